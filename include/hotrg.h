@@ -1,0 +1,169 @@
+/*
+ * hotrg.h - C ABI of the GB300 (sm_103a) HOTRG library for the 4D Ising model.
+ *
+ * What it computes (arXiv:1911.12954, Sec. 2, Fig. 1; impure-tensor observables of
+ * Sec. 3.1): the higher-order tensor renormalisation group. A site tensor
+ * T[x,x',y,y',z,z',t,t'] (unprimed leg of direction nu points to -nu, primed to +nu)
+ * is coarse-grained along a direction mu by merging two neighbouring tensors; every
+ * transverse direction nu gets an isometry U^nu (D_nu^2 -> chi_nu = min(D_nu^2, D_cut))
+ * from the HOSVD of the pair, and the O(D^15) block-spin contraction produces the new
+ * tensor, which is normalised by its Frobenius norm c. After k steps the lattice has
+ * V = 2^k sites and ln Z / V = sum_i ln(c_i) / 2^i + ln(Tr T_k) / 2^k.
+ *
+ * Conventions shared by every call:
+ *  - A context holds `batch` independent runs (one per temperature); everything is per
+ *    batch element b in [0, batch).
+ *  - Device memory and the CUDA stream belong to the caller. The library never calls
+ *    cudaMalloc; it carves the caller's workspace (hotrg_set_workspace) and launches
+ *    on the caller's stream (hotrg_set_stream; default: the legacy default stream).
+ *  - Every call returns a hotrg_status and never aborts. Calls that return host values
+ *    synchronise the stream and report device-side errors (eigensolver not converged,
+ *    non-finite norm, timeout) raised by earlier asynchronous steps. After an error the
+ *    context is sticky (HOTRG_ESTATE) until hotrg_init_tensor or hotrg_set_tensor.
+ *  - Host arrays passed in are read before the call returns; host arrays passed out
+ *    are written before it returns. Layout of a tensor on the host: row-major FP64
+ *    over legs [x, x', y, y', z, z', t, t'] with sizes (Dx, Dx, Dy, Dy, Dz, Dz, Dt, Dt).
+ */
+#ifndef HOTRG_H
+#define HOTRG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hotrg_ctx hotrg_ctx; /* opaque, created by hotrg_create, host-owned */
+
+typedef enum {
+  HOTRG_OK = 0,
+  HOTRG_EINVAL = -1,      /* bad argument (null pointer, dir, dcut, batch index, sizes) */
+  HOTRG_EWORKSPACE = -2,  /* no workspace set, or too small for the requested step      */
+  HOTRG_ECUDA = -3,       /* a CUDA runtime call failed (message: hotrg_last_error)     */
+  HOTRG_ENOCONV = -4,     /* Jacobi eigensolver hit its sweep limit                     */
+  HOTRG_ENONFINITE = -5,  /* a norm or trace was not finite / not positive             */
+  HOTRG_ETIMEOUT = -6,    /* a bounded device-side wait gave up                         */
+  HOTRG_ESTATE = -7,      /* call out of order, or context sticky after an error        */
+  HOTRG_EUNSUPPORTED = -8 /* precision or size not built into this library              */
+} hotrg_status;
+
+/* Arithmetic of the block-spin contraction and the Gram build.
+ * HOTRG_FP64  : FP64 everywhere (DFMA).                                     reference
+ * HOTRG_FP32  : FP32 SIMT FMA, FP32 accumulation; tensors stored in FP32.
+ * HOTRG_TF32X3: tcgen05 tensor cores, each FP32 operand split into tf32 hi + lo,
+ *               products hi*hi + hi*lo + lo*hi accumulated in FP32 (TMEM).
+ * In every mode the Gram matrices are accumulated in FP64, and the eigensolver, the
+ * isometries, the norm and ln Z / V are FP64. */
+typedef enum { HOTRG_FP64 = 0, HOTRG_FP32 = 1, HOTRG_TF32X3 = 2 } hotrg_precision;
+
+/* Impure tensors propagated with the pure one (same isometries, same c):
+ * SIGMA: S (one sigma inserted) -> magnetisation <sigma> = Tr S / Tr T.
+ * SIGMASIGMA: M (sigma_n sigma_{n+mu0}, mu0 = first step's direction) -> <sigma sigma>;
+ * requires SIGMA. */
+enum { HOTRG_IMPURE_NONE = 0, HOTRG_IMPURE_SIGMA = 1, HOTRG_IMPURE_SIGMASIGMA = 2 };
+
+/* Per-step record kept for every batch element (FP64). */
+typedef struct {
+  int mu;            /* direction of the step: 0..3 = x, y, z, t                      */
+  int dims[4];       /* bond dimensions after the step                               */
+  int primed[4];     /* per transverse nu: 1 if the nu' side of the HOSVD was taken    */
+  double eps[4][2];  /* per transverse nu: discarded eigenvalue sum, nu and nu' side   */
+  double ln_c;       /* ln of the Frobenius norm of the new tensor before normalising */
+  int degenerate[4]; /* per transverse nu: the cut fell inside an eigenvalue cluster   */
+} hotrg_step_record;
+
+/* Create a context for `batch` runs with bond dimensions up to `dcut_max`
+ * (2 <= dcut_max <= 16), precision `prec` and impure mask. No device memory is
+ * touched. Errors: EINVAL. */
+hotrg_status hotrg_create(hotrg_ctx** out, int batch, int dcut_max, int prec, int impure_mask);
+
+/* Release the context (not the caller's workspace). Accepts NULL. */
+hotrg_status hotrg_destroy(hotrg_ctx* ctx);
+
+/* Plan a run and return the bytes of device workspace it needs: the steps `dirs[i]`,
+ * `dcuts[i]` (i < nsteps) from the 2x2x2x2 initial tensor or, when dims0 != NULL, from a
+ * tensor of bond dimensions dims0[4] given to hotrg_set_tensor. With nsteps == 0 the
+ * bound covers any step whose bond dimensions are all <= dcut_max. The plan fixes the
+ * per-tensor capacity used by the next hotrg_set_workspace. The returned size lets every
+ * step contract unsliced; a smaller workspace (at least the persistent part plus one
+ * X slice) makes hotrg_step slice the new a-leg instead. Errors: EINVAL. */
+hotrg_status hotrg_workspace_size(hotrg_ctx* ctx, int nsteps, const int* dirs, const int* dcuts,
+                                  const int* dims0, size_t* bytes);
+
+/* Give the library `bytes` bytes of device memory at `dev_ptr` (256-byte aligned),
+ * owned by the caller, kept until the next call of this function or hotrg_destroy.
+ * Errors: EINVAL (null or misaligned pointer). */
+hotrg_status hotrg_set_workspace(hotrg_ctx* ctx, void* dev_ptr, size_t bytes);
+
+/* Launch all later work on `cuda_stream` (a cudaStream_t, caller-owned; NULL =
+ * legacy default stream). */
+hotrg_status hotrg_set_stream(hotrg_ctx* ctx, void* cuda_stream);
+
+/* Site tensors of the 4D Ising model (Fig. 1A; H = -sum s s' - h sum s):
+ * T[i1..i8] = sum_s e^{beta h s} prod_j W[s, i_j], W = [[sqrt(cosh b), sqrt(sinh b)],
+ * [sqrt(cosh b), -sqrt(sinh b)]]; S the same with an extra factor s. beta[b], h[b] are
+ * host arrays of length batch (beta >= 0). Resets the step counter, ln Z accumulator,
+ * records and sticky error. Asynchronous. Errors: EINVAL, EWORKSPACE, ECUDA. */
+hotrg_status hotrg_init_tensor(hotrg_ctx* ctx, const double* beta, const double* h);
+
+/* Replace the pure tensor of batch element b by the host tensor `T_host` with bond
+ * dimensions dims[4] (each <= dcut_max; layout in the header comment); the stored
+ * tensor is T_host / ||T_host||_F and ln ||T_host|| starts the accumulator. Disables
+ * impure tensors for the context. For kernel-level tests. Synchronous. */
+hotrg_status hotrg_set_tensor(hotrg_ctx* ctx, int b, const int dims[4], const double* T_host);
+
+/* One coarse-graining step along `dir` (0..3) with cut `dcut` (>= 1, <= dcut_max),
+ * for every batch element: Gram matrices on both sides of the three transverse bond
+ * pairs (FP64 accumulation), Jacobi eigendecomposition (FP64, on the GPU), isometries
+ * from the side with the smaller discarded eigenvalue sum, the block-spin contraction
+ * in the context's precision, normalisation by ||T'||_F and ln c / 2^k accumulated in
+ * FP64. Impure tensors follow with the same isometries and c. Asynchronous on the
+ * stream; device-side failures are reported by the next synchronising call.
+ * Errors: EINVAL, EWORKSPACE, ESTATE, ECUDA. */
+hotrg_status hotrg_step(hotrg_ctx* ctx, int dir, int dcut);
+
+/* ln Z / V of the 2^k-site periodic lattice after the k steps done so far, per batch
+ * element (host array of length batch). Synchronises. */
+hotrg_status hotrg_lnZ(hotrg_ctx* ctx, double* lnZ_over_V);
+
+/* <sigma> = Tr S_k / Tr T_k per batch element. Needs HOTRG_IMPURE_SIGMA. */
+hotrg_status hotrg_impure_magnetization(hotrg_ctx* ctx, double* m);
+
+/* <sigma_n sigma_{n+mu0}> = Tr M_k / Tr T_k and E/V = -4 <sigma sigma> - h <sigma>
+ * per batch element (k >= 1). Needs HOTRG_IMPURE_SIGMASIGMA. Either pointer may be
+ * NULL. */
+hotrg_status hotrg_impure_energy(hotrg_ctx* ctx, double* e, double* sigma_sigma);
+
+/* Record of step `step` (1-based, <= steps done) of batch element b. Synchronises. */
+hotrg_status hotrg_step_info(hotrg_ctx* ctx, int b, int step, hotrg_step_record* rec);
+
+/* Number of steps done since the last init/set_tensor; current bond dimensions. */
+hotrg_status hotrg_state(const hotrg_ctx* ctx, int* steps_done, int dims[4]);
+
+/* Copy tensor `which` (0 = T, 1 = S, 2 = M) of batch element b to the host as FP64,
+ * normalised as stored; `n` = capacity of `host` in elements (must be >= Dx^2 Dy^2
+ * Dz^2 Dt^2). Synchronises. */
+hotrg_status hotrg_copy_tensor(hotrg_ctx* ctx, int which, int b, double* host, size_t n);
+
+/* Copy the isometry U^nu of the last step (b, nu transverse) to the host as FP64,
+ * row-major [(i1*D_nu + i2)][chi_nu]; `n` = capacity. Synchronises. */
+hotrg_status hotrg_copy_isometry(hotrg_ctx* ctx, int b, int nu, double* host, size_t n);
+
+/* Algorithmic floating-point operations of the next step along `dir` with `dcut` from
+ * the current bond dimensions D, per batch element and per tensor product (2 flops per
+ * multiply-add). main = 2 (chi_a chi_b D_c^2 D_mu)^2 (D_a^2 D_b^2 D_mu), the block-spin
+ * contraction (2 D^15 when every dimension is D), with c the transverse direction that
+ * makes it smallest; total adds the isometry applications, the closing contractions and
+ * the Gram build. Host-only, no device access. */
+hotrg_status hotrg_step_flops(const hotrg_ctx* ctx, int dir, int dcut, double* main_flops,
+                              double* total_flops);
+
+/* Text of a status code, and the last CUDA error message seen by this thread. */
+const char* hotrg_status_string(int status);
+const char* hotrg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HOTRG_H */

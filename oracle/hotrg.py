@@ -281,7 +281,7 @@ class StepRecord:
     primed: dict             # nu -> side taken
     ln_c: float
     degenerate_cut: bool
-    lnZ: float               # ln Z / V after this step (V = 2**k)
+    lnZ: float               # ln Z / V after this step (V = 2**k); nan if Tr T <= 0
 
 
 @dataclass
@@ -359,7 +359,7 @@ class HOTRG:
             chi=tuple(self.T.shape[2 * n] for n in range(d)),
             eps={n: isos[n].eps for n in isos}, primed={n: isos[n].primed for n in isos},
             ln_c=math.log(c), degenerate_cut=any(i.degenerate_cut for i in isos.values()),
-            lnZ=self.lnZ())
+            lnZ=self.lnZ() if trace(self.T) > 0 else float("nan"))
         self.history.append(rec)
         return rec
 

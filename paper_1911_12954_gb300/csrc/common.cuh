@@ -1,0 +1,127 @@
+// common.cuh - shared types of the HOTRG CUDA library (internal header).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+
+namespace hotrg {
+
+constexpr int kMaxRank = 10;      // legs of the largest intermediate (D^10 operands)
+constexpr int kMaxLeg = 16;       // largest bond dimension (dcut_max)
+constexpr int kMaxGramN = kMaxLeg * kMaxLeg;  // largest Gram matrix side (D_nu^2)
+constexpr int kMaxSteps = 64;     // steps recorded per batch element
+constexpr int kJacobiMaxSweeps = 60;
+
+// Device-side status words (in the caller's workspace), read back at sync points.
+enum StatusWord { kStNoConv = 0, kStNonFinite = 1, kStTimeout = 2, kStWords = 4 };
+
+// Tensor-times-matrix descriptor: out[o] = alpha * sum_{j1<J1, j2<J2}
+//   U[u(o) + j1*u_sj1 + j2*u_sj2] * in[i(o) + j1*in_sj1 + j2*in_sj2]  (+ beta * out[o])
+// where o runs over `rank` output dims (iteration order: dims[0] outermost); the last
+// `rin` dims form the inner loop of one block. i(o), u(o), out offset are linear in the
+// output multi-index with the given strides. U == nullptr means U = 1 (a permutation).
+struct TTMArgs {
+  int rank;
+  int rin;
+  int J1, J2;
+  int64_t dims[kMaxRank];
+  int64_t in_st[kMaxRank];
+  int64_t u_st[kMaxRank];
+  int64_t out_st[kMaxRank];
+  int64_t in_sj1, in_sj2, u_sj1, u_sj2;
+  int64_t outer, inner;
+  double alpha, beta;
+};
+
+enum TTMMode { kTTMStore = 0, kTTMSplitTF32 = 1, kTTMAccumulate = 2 };
+
+// One half-Gram job: A[(i1 i2), (j1 j2)] = sum_rest T[i1@l1, i2@l2, rest] T[j1, j2, rest].
+struct GramJob {
+  const void* T;
+  int D1, D2;               // sizes of the two row legs
+  int64_t s1, s2;           // their strides in T
+  int nrest;                // number of summed legs (6 for a rank-8 tensor)
+  int64_t rdims[8];         // summed leg sizes (outermost first)
+  int64_t rst[8];           // summed leg strides
+  int64_t K;                // product of rdims
+  double* partial;          // [nchunks][R][R]
+};
+
+// One symmetric eigenproblem for the Jacobi kernel.
+struct EigJob {
+  const double* G;          // n x n, row-major, symmetric
+  double* work;             // 2 n^2 doubles of global scratch (used when n is large)
+  double* lam;              // n eigenvalues, descending
+  double* U;                // n x chi, first chi eigenvectors in canonical gauge
+  double* eps;              // sum of the discarded eigenvalues (index >= chi)
+  int* degenerate;          // 1 if the cut at chi falls inside a cluster
+  int n, chi;
+};
+
+// Side choice for one transverse direction: candidates from the nu and nu' Gram matrices.
+struct SelectJob {
+  const double* U[2];      // candidate isometries (n x chi), nu side and nu' side
+  const double* lam0;      // spectrum of the nu side (absolute tie floor)
+  const double* eps[2];    // discarded eigenvalue sums
+  const int* degen[2];     // cut inside a cluster
+  double* U64;             // chosen isometry, FP64, n x chi (after Gram-Schmidt)
+  void* Ur;                // chosen isometry in the storage precision
+  int n, chi;
+  double* rec_eps;         // step record: eps of both sides
+  int* rec_primed;         // step record: side taken
+  int* rec_degen;          // step record: degenerate cut on the side taken
+};
+
+// Step record as kept on the device for each batch element and step.
+struct DevRecord {
+  double eps[4][2];
+  double ln_c;
+  int primed[4];
+  int degen[4];
+};
+
+// Job packs passed to kernels by value (kernel parameter space), so a step needs no
+// host-to-device copies of job descriptors and can be captured in a CUDA graph.
+constexpr int kMaxGramJobs = 12;
+constexpr int kMaxEigJobs = 6;
+constexpr int kMaxSelectJobs = 3;
+struct GramPack { GramJob j[kMaxGramJobs]; };
+struct EigPack { EigJob j[kMaxEigJobs]; };
+struct SelectPack { SelectJob j[kMaxSelectJobs]; };
+
+// Host-side launchers (defined in the .cu files, called by the orchestrator).
+template <typename TI, typename TU, typename TO>
+cudaError_t launch_ttm(const TI* in, const TU* U, TO* out, TO* out_lo, const TTMArgs& a, int mode,
+                       cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_gram(const GramPack& jobs, int njobs, int Rmax, int nchunks, cudaStream_t st);
+cudaError_t launch_gram_reduce(const double* partial, int nchunks, int64_t RR, double* out,
+                               cudaStream_t st);
+cudaError_t launch_gram_merge(const double* A1, const double* A2, int Dn, int Dk, double* G,
+                              cudaStream_t st);
+cudaError_t launch_jacobi(const EigPack& jobs, int njobs, int nmax, double cluster_tau, int* status,
+                          cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_select(const SelectPack& jobs, int njobs, double side_rel, cudaStream_t st);
+template <typename R>
+cudaError_t launch_init(const double* beta, const double* h, R* T, R* S, int64_t slot, double* lnz_acc,
+                        int batch, cudaStream_t st);
+template <typename R>
+cudaError_t launch_norm(const R* x, int64_t n, double* partial, double weight, double* c_out, double* lnz_acc,
+                        double* ln_c_rec, int* status, cudaStream_t st);
+template <typename R>
+cudaError_t launch_scale(R* x, int64_t n, const double* c, cudaStream_t st);
+template <typename R>
+cudaError_t launch_trace(const R* T, int64_t slot, const int* dims, int batch, double* out, cudaStream_t st);
+constexpr int kNormPartials = 2 * 152;
+
+template <typename R>
+cudaError_t launch_gemm_simt(const R* A, int64_t lda, const R* B, int64_t ldb, R* C, int64_t ldc,
+                             int64_t M, int64_t N, int64_t K, double alpha, double beta,
+                             cudaStream_t st);
+
+}  // namespace hotrg

@@ -1,0 +1,403 @@
+// gemm_tc.cu - tcgen05 / TMEM / TMA GEMM for the block-spin contraction (TF32x3 mode).
+//
+// C[m][n] = alpha * sum_k (Ahi Bhi + Ahi Blo + Alo Bhi)[m,n,k] + beta * C[m][n]
+// with A = Ahi + Alo and B = Bhi + Blo, each part a tf32 value stored in an FP32 word,
+// both operands K-major ([rows][ld] with ld % 4 == 0). This is the O(D^15) block-spin
+// contraction of the HOTRG step, where Sec. 2 of arXiv:1911.12954 places the D^(4d-1)
+// cost of the method, carried out on the 5th-generation tensor cores with FP32
+// accumulation; the dropped Alo Blo term is below 2^-21 of each product.
+//
+// The tensor cores add each MMA's products into the FP32 accumulator with truncation,
+// so an accumulator that runs over the whole K picks up a bias that grows linearly with
+// K (measured 2.5e-4 relative at K = 32768). The kernel therefore promotes the partial
+// sum of every k-block of 32 (12 MMAs) from TMEM into FP32 registers, where the sums
+// are rounded to nearest: the truncation bias is bounded by one k-block's worth.
+//
+// Structure: persistent kernel, one CTA per SM, 10 warps.
+//   warp 0 lane 0 : TMA producer. Per k-block of 32 (one 128-byte swizzle row), four
+//                   tiles (Ahi, Alo: 128x32; Bhi, Blo: 256x32) land in one pipeline stage
+//                   through cp.async.bulk.tensor with 128-byte swizzle.
+//   warp 1 lane 0 : MMA issuer. Per k-block, 4 k-steps x 3 products of
+//                   tcgen05.mma.cta_group::1.kind::tf32 (M=128, N=256, K=8) into one of
+//                   two TMEM chunk accumulators (2 x 256 of the 512 columns); commits free
+//                   the stage and hand the chunk to the epilogue.
+//   warps 2..9    : promotion + epilogue. Warp w reads TMEM lane quarter w % 4 and column
+//                   half (w - 2) / 4 with tcgen05.ld 32x32b, adds the chunk into 128 FP32
+//                   registers per thread, and after the last k-block of the tile writes
+//                   alpha * acc + beta * C with guarded stores.
+// Tiles are visited in groups of 16 M-tiles so the CTAs running at the same time share
+// A and B k-blocks through L2.
+// Every mbarrier wait is bounded (globaltimer, 4 s): on expiry the thread raises the
+// timeout status word and leaves its loop; teardown still drains the copies and MMAs in
+// flight (bounded) and frees TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+
+namespace hotrg {
+
+namespace tc {
+
+constexpr int BM = 128;
+constexpr int BN = 256;
+constexpr int BK = 32;                                  // fp32 elements per 128-byte row
+constexpr int STAGES = 2;
+constexpr int A_BYTES = BM * BK * 4;                    // 16 KB
+constexpr int B_BYTES = BN * BK * 4;                    // 32 KB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 96 KB
+constexpr int TMEM_COLS = 2 * BN;                       // two chunk accumulators
+constexpr int GROUP_M = 16;
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+constexpr unsigned long long kWaitNs = 4000000000ull;
+
+// instruction descriptor: D = F32, A = B = TF32, both K-major, N = 256, M = 128
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false (and the timeout status raised) when it gives up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* status) {
+  if (mbar_try(b, parity)) return true;
+  const unsigned long long t0 = now_ns();
+  while (true) {
+    if (mbar_try(b, parity)) return true;
+    if (now_ns() - t0 > kWaitNs) {
+      atomicAdd(&status[kStTimeout], 1);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
+          "r"(su32(dst)),
+      "l"((uint64_t)map), "r"(su32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                            // leading byte offset (unused for SW128 K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;                  // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                            // descriptor version (tcgen05)
+  d |= (uint64_t)2 << 61;                            // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& tm, int& tn) {
+  const int per_group = GROUP_M * tiles_n;
+  const int g = t / per_group;
+  const int first_m = g * GROUP_M;
+  const int gm = min(GROUP_M, tiles_m - first_m);
+  const int r = t - g * per_group;
+  tm = first_m + r % gm;
+  tn = r / gm;
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+                       const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
+                       float* __restrict__ C, int64_t ldc, int M, int N, int K, float alpha, float beta,
+                       int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* full = bars;                 // [STAGES]
+  uint64_t* empty = bars + STAGES;       // [STAGES]
+  uint64_t* cfull = bars + 2 * STAGES;   // [2] chunk accumulator written
+  uint64_t* cempty = cfull + 2;          // [2] chunk accumulator drained
+  uint64_t* drain = cempty + 2;          // [1]
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
+  const int ntiles = tiles_m * tiles_n;
+  const int nkb = (K + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&cfull[a], 1);
+      mbar_init(&cempty[a], 32 * EPI_WARPS);
+    }
+    mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ TMA producer
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mAhi) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mAlo) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mBhi) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mBlo) : "memory");
+    int s = 0;
+    uint32_t ph = 0;
+    int issued[STAGES] = {};
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int tm, tn;
+      tile_coords(t, tiles_m, tiles_n, tm, tn);
+      for (int kb = 0; kb < nkb; ++kb) {
+        if (!mbar_wait(&empty[s], ph ^ 1, status)) {
+          ok = false;
+          break;
+        }
+        uint8_t* st = smem + s * STAGE_BYTES;
+        mbar_expect_tx(&full[s], STAGE_BYTES);
+        tma_load(&mAhi, &full[s], st, kb * BK, tm * BM);
+        tma_load(&mAlo, &full[s], st + A_BYTES, kb * BK, tm * BM);
+        tma_load(&mBhi, &full[s], st + 2 * A_BYTES, kb * BK, tn * BN);
+        tma_load(&mBlo, &full[s], st + 2 * A_BYTES + B_BYTES, kb * BK, tn * BN);
+        ++issued[s];
+        if (++s == STAGES) {
+          s = 0;
+          ph ^= 1;
+        }
+      }
+    }
+    // make sure every copy issued has landed before the CTA can exit
+    for (int q = 0; q < STAGES; ++q)
+      if (issued[q] > 0) mbar_wait(&full[q], (uint32_t)((issued[q] - 1) & 1), status);
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    int s = 0, cb = 0;
+    uint32_t ph = 0, cph = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int kb = 0; kb < nkb; ++kb) {
+        if (!mbar_wait(&cempty[cb], cph ^ 1, status) || !mbar_wait(&full[s], ph, status)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t d = tmem + (uint32_t)(cb * BN);
+        const uint32_t base = su32(smem + s * STAGE_BYTES);
+        const uint64_t ahi = sw128_desc(base), alo = sw128_desc(base + A_BYTES);
+        const uint64_t bhi = sw128_desc(base + 2 * A_BYTES), blo = sw128_desc(base + 2 * A_BYTES + B_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < BK / 8; ++kk) {
+          const uint64_t off = (uint64_t)(kk * 32) >> 4;   // 8 tf32 = 32 bytes along the swizzled row
+          mma_tf32(d, alo + off, bhi + off, kk != 0);
+          mma_tf32(d, ahi + off, blo + off, 1);
+          mma_tf32(d, ahi + off, bhi + off, 1);
+        }
+        mma_commit(&empty[s]);
+        mma_commit(&cfull[cb]);
+        if (++s == STAGES) {
+          s = 0;
+          ph ^= 1;
+        }
+        if (++cb == 2) {
+          cb = 0;
+          cph ^= 1;
+        }
+      }
+    }
+    // every MMA issued has completed once this commit arrives
+    mma_commit(drain);
+    mbar_wait(drain, 0, status);
+  } else if (warp >= 2) {
+    // ------------------------------------------------------------ promotion + epilogue
+    const int q = warp & 3;                 // TMEM lane quarter this warp may access
+    const int h = (warp - 2) >> 2;          // column half of the tile
+    const int row = q * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    int cb = 0;
+    uint32_t cph = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int tm, tn;
+      tile_coords(t, tiles_m, tiles_n, tm, tn);
+      float acc[BN / 2];
+#pragma unroll
+      for (int j = 0; j < BN / 2; ++j) acc[j] = 0.f;
+      for (int kb = 0; kb < nkb; ++kb) {
+        // warp-uniform outcome: tcgen05.ld below must be executed by all 32 lanes
+        if (!__all_sync(0xffffffffu, mbar_wait(&cfull[cb], cph, status))) {
+          ok = false;
+          break;
+        }
+        fence_after();
+#pragma unroll
+        for (int c = 0; c < BN / 64; ++c) {
+          float v[32];
+          tmem_ld32(tmem + lane_base + (uint32_t)(cb * BN + h * (BN / 2) + c * 32), v);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc[c * 32 + j] += v[j];
+        }
+        fence_before();
+        mbar_arrive(&cempty[cb]);
+        if (++cb == 2) {
+          cb = 0;
+          cph ^= 1;
+        }
+      }
+      if (!ok) break;
+      const int64_t m = (int64_t)tm * BM + row;
+      const int n0 = tn * BN + h * (BN / 2);
+      if (m < M) {
+        float* crow = C + m * ldc + n0;
+        if (n0 + BN / 2 <= N && ((((uintptr_t)crow) & 15) == 0)) {
+#pragma unroll
+          for (int j = 0; j < BN / 2; j += 4) {
+            float4 o = make_float4(alpha * acc[j], alpha * acc[j + 1], alpha * acc[j + 2], alpha * acc[j + 3]);
+            if (beta != 0.f) {
+              const float4 old = *(const float4*)(crow + j);
+              o.x += beta * old.x;
+              o.y += beta * old.y;
+              o.z += beta * old.z;
+              o.w += beta * old.w;
+            }
+            *(float4*)(crow + j) = o;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < BN / 2; ++j)
+            if (n0 + j < N) crow[j] = alpha * acc[j] + (beta != 0.f ? beta * crow[j] : 0.f);
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, const float* ptr, int64_t rows, int64_t K, int64_t ld, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)ptr, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace tc
+
+cudaError_t launch_gemm_tf32x3(const float* Ahi, const float* Alo, int64_t lda, const float* Bhi, const float* Blo,
+                               int64_t ldb, float* C, int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha,
+                               float beta, int* status, cudaStream_t st) {
+  using namespace tc;
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (K <= 0 || M > 0x7fffffff || N > 0x7fffffff || K > 0x7fffffff) return cudaErrorInvalidValue;
+  if ((lda & 3) || (ldb & 3) || lda < K || ldb < K) return cudaErrorInvalidValue;
+  if ((((uintptr_t)Ahi) | ((uintptr_t)Alo) | ((uintptr_t)Bhi) | ((uintptr_t)Blo)) & 15) return cudaErrorInvalidValue;
+  CUtensorMap mAhi, mAlo, mBhi, mBlo;
+  if (!make_map(&mAhi, Ahi, M, K, lda, BM) || !make_map(&mAlo, Alo, M, K, lda, BM) ||
+      !make_map(&mBhi, Bhi, N, K, ldb, BN) || !make_map(&mBlo, Blo, N, K, ldb, BN))
+    return cudaErrorInvalidValue;
+  static int sms = 0;
+  static bool attr = false;
+  if (!attr) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(gemm_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  const int grid = (int)(tiles < sms ? tiles : sms);
+  gemm_tf32x3_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(mAhi, mAlo, mBhi, mBlo, C, ldc, (int)M, (int)N, (int)K,
+                                                        alpha, beta, status);
+  return cudaGetLastError();
+}
+
+}  // namespace hotrg

@@ -1,0 +1,1105 @@
+// hotrg.cu - C ABI and step orchestration of the HOTRG library (include/hotrg.h).
+//
+// One coarse-graining step along mu (Fig. 1 of arXiv:1911.12954), for each batch
+// element, as a fixed sequence of stream-ordered launches with no host synchronisation:
+//   1. Gram halves on both sides of the three transverse legs (12 split-K jobs, one
+//      launch), chunk reduction, merge into six D_nu^2 x D_nu^2 FP64 Gram matrices.
+//   2. Jacobi eigensolver on the six matrices (one launch), canonical gauge, then the
+//      side choice + Gram-Schmidt per direction (one launch).
+//   3. Block-spin contraction (the O(D^15) part, Sec. 2): the transverse direction whose
+//      closing is cheapest is c, the others a and b. For each slice of X (new a leg):
+//        A[(X Y c1 c1' mu1), (a2 b2 a1' b1' k)] = T1 x_{a1} U^a x_{b1} U^b   (two passes)
+//        B[(X' Y' c2 c2' mu2'), (a2 b2 a1' b1' k)] = T2 x_{a2'} U^a x_{b2'} U^b
+//        C = A B^T                                                        (the GEMM)
+//        T'[X, X', Y, Y', Z, Z', mu1, mu2'] = C x_{(c1 c2)} U^c x_{(c1' c2')} U^c
+//      Impure tensors: S' = (C(S,T) + C(T,S)) / 2, M_1 = C(S,S), M' = (C(M,T) + C(T,M)) / 2.
+//   4. c = ||T'||_F (FP64), ln c / 2^k accumulated, T', S', M' divided by c.
+// Tensors are stored row-major over legs [x, x', y, y', z, z', t, t'].
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "hotrg.h"
+
+namespace hotrg {
+cudaError_t launch_gemm_tf32x3(const float* Ahi, const float* Alo, int64_t lda, const float* Bhi, const float* Blo,
+                               int64_t ldb, float* C, int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha,
+                               float beta, int* status, cudaStream_t st);
+}
+
+using namespace hotrg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Sizes of one step (elements), derived from the bond dimensions before the step.
+struct StepPlan {
+  int mu, a, b, c;
+  int D[4];
+  int chi[4];
+  int newD[4];
+  int64_t E, Enew;        // tensor elements before / after
+  int64_t rowsA_full;     // xs = chi_a
+  int64_t rowsB;          // chi_a chi_b Dc^2 Dmu
+  int64_t K, ldk;         // Da^2 Db^2 Dmu, padded to 4
+  int xs;                 // X values per slice
+  // Gram
+  int R[4];               // rows of the half-Gram per direction = D_nu D_mu
+  int Rmax, nmax, nchunks;
+  double main_flops, total_flops;
+};
+
+struct Layout {
+  // persistent
+  size_t status, lnz, cval, trace, rec, beta, hfield, U64, Ur, tensors;
+  int64_t cap;            // elements per tensor slot
+  size_t persistent_end;
+};
+
+}  // namespace
+
+struct hotrg_ctx {
+  int batch = 1, dcut_max = 2, prec = HOTRG_FP64, impure = 0;
+  int impure_active = 0;
+  size_t rsize = 8;
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  int64_t cap_planned = 0;
+  Layout L{};
+  bool ready = false;        // workspace laid out
+  bool initialised = false;  // tensors exist
+  int sticky = 0;
+  int k = 0;
+  int dims[4] = {2, 2, 2, 2};
+  int mu_hist[kMaxSteps];
+  int dims_hist[kMaxSteps][4];
+  int cur = 0;               // which tensor buffer holds the current tensors
+  int last_chi[4] = {0, 0, 0, 0};
+  int last_Dold[4] = {0, 0, 0, 0};
+  int last_mu = -1;
+  std::vector<double> h_host;
+};
+
+namespace {
+
+hotrg_status cuda_fail(hotrg_ctx* ctx, cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  if (ctx) ctx->sticky = HOTRG_ECUDA;
+  return HOTRG_ECUDA;
+}
+
+#define CK(call, where)                                   \
+  do {                                                    \
+    cudaError_t e__ = (call);                             \
+    if (e__ != cudaSuccess) return cuda_fail(ctx, e__, where); \
+  } while (0)
+
+// Largest element offset a TTM launch touches in its input, isometry and output (all
+// strides are non-negative); launches that would leave their buffers are refused.
+struct Extent {
+  int64_t in, u, out;
+};
+Extent ttm_extent(const TTMArgs& a) {
+  Extent e{0, 0, 0};
+  for (int i = 0; i < a.rank; ++i) {
+    e.in += (a.dims[i] - 1) * a.in_st[i];
+    e.u += (a.dims[i] - 1) * a.u_st[i];
+    e.out += (a.dims[i] - 1) * a.out_st[i];
+  }
+  e.in += (a.J1 - 1) * a.in_sj1 + (a.J2 - 1) * a.in_sj2;
+  e.u += (a.J1 - 1) * a.u_sj1 + (a.J2 - 1) * a.u_sj2;
+  return e;
+}
+
+thread_local int64_t g_lim_in = -1, g_lim_u = -1, g_lim_out = -1;  // elements available
+
+template <typename R>
+inline cudaError_t launch_ttm_r(const R* in, const R* U, R* out, R* lo, const TTMArgs& a, int mode, cudaStream_t st) {
+  const Extent e = ttm_extent(a);
+  for (int i = 0; i < a.rank; ++i)
+    if (a.in_st[i] < 0 || a.u_st[i] < 0 || a.out_st[i] < 0) return cudaErrorInvalidValue;
+  if (e.in >= g_lim_in || (U && e.u >= g_lim_u) || e.out >= g_lim_out) {
+    g_last_error = "TTM launch refused: extent outside its buffer";
+    return cudaErrorInvalidValue;
+  }
+  return launch_ttm<R, R, R>(in, U, out, lo, a, mode, st);
+}
+inline void ttm_limits(int64_t in, int64_t u, int64_t out) {
+  g_lim_in = in;
+  g_lim_u = u;
+  g_lim_out = out;
+}
+
+int64_t tensor_elems(const int D[4]) {
+  int64_t e = 1;
+  for (int n = 0; n < 4; ++n) e *= (int64_t)D[n] * D[n];
+  return e;
+}
+
+double plan_main_flops(const int D[4], const int chi[4], int mu, int a, int b, int c) {
+  const double rows = (double)chi[a] * chi[b] * D[c] * D[c] * D[mu];
+  const double K = (double)D[a] * D[a] * D[b] * D[b] * D[mu];
+  return 2.0 * rows * rows * K;
+}
+
+StepPlan make_plan(const int D[4], int mu, int dcut) {
+  StepPlan p{};
+  p.mu = mu;
+  for (int n = 0; n < 4; ++n) {
+    p.D[n] = D[n];
+    p.chi[n] = (n == mu) ? D[n] : std::min(D[n] * D[n], dcut);
+    p.newD[n] = p.chi[n];
+  }
+  int tr[3], t = 0;
+  for (int n = 0; n < 4; ++n)
+    if (n != mu) tr[t++] = n;
+  // closing direction: the one that minimises the main contraction (ties: last)
+  double best = -1;
+  int bc = tr[2];
+  for (int i = 0; i < 3; ++i) {
+    const int c = tr[i];
+    int ab[2], q = 0;
+    for (int j = 0; j < 3; ++j)
+      if (j != i) ab[q++] = tr[j];
+    const double f = plan_main_flops(D, p.chi, mu, ab[0], ab[1], c);
+    if (best < 0 || f <= best) {
+      best = f;
+      bc = c;
+    }
+  }
+  p.c = bc;
+  int q = 0, ab[2];
+  for (int i = 0; i < 3; ++i)
+    if (tr[i] != bc) ab[q++] = tr[i];
+  p.a = ab[0];
+  p.b = ab[1];
+  p.E = tensor_elems(D);
+  p.Enew = tensor_elems(p.newD);
+  const int Da = D[p.a], Db = D[p.b], Dc = D[p.c], Dm = D[mu];
+  p.rowsB = (int64_t)p.chi[p.a] * p.chi[p.b] * Dc * Dc * Dm;
+  p.rowsA_full = p.rowsB;
+  p.K = (int64_t)Da * Da * Db * Db * Dm;
+  p.ldk = (p.K + 3) / 4 * 4;
+  p.xs = p.chi[p.a];
+  p.Rmax = 0;
+  p.nmax = 0;
+  for (int n = 0; n < 4; ++n) {
+    p.R[n] = D[n] * Dm;
+    if (n != mu) {
+      p.Rmax = std::max(p.Rmax, p.R[n]);
+      p.nmax = std::max(p.nmax, D[n] * D[n]);
+    }
+  }
+  const int64_t Kg = p.E / p.Rmax;
+  int64_t nc = (Kg + 511) / 512;
+  if (nc > 256) nc = 256;
+  if (nc < 1) nc = 1;
+  // keep the split-K partials under 256 MB
+  const int64_t per = (int64_t)kMaxGramJobs * p.Rmax * p.Rmax * 8;
+  while (nc > 1 && nc * per > (256LL << 20)) nc /= 2;
+  p.nchunks = (int)nc;
+  p.main_flops = best;
+  // every other product of the step, counted as 2 flops per multiply-add
+  const double Ed = (double)p.E, rA = (double)p.rowsA_full, rB = (double)p.rowsB, Kd = (double)p.K;
+  double f = best;
+  f += 2.0 * Da * p.chi[p.a] * Ed + 2.0 * Db * rA * Kd;            // A = T x U^a x U^b
+  f += 2.0 * Da * p.chi[p.a] * Ed + 2.0 * Db * rB * Kd;            // B = T x U^a x U^b
+  f += 2.0 * p.chi[p.c] * rA * rB + 2.0 * Dc * Dc * (double)p.Enew; // closing with U^c twice
+  for (int n = 0; n < 4; ++n)
+    if (n != mu) f += 8.0 * p.R[n] * Ed + 2.0 * 2.0 * pow((double)D[n], 4) * Dm * Dm;  // Gram
+  p.total_flops = f;
+  return p;
+}
+
+int ntensors(int impure) { return (impure & HOTRG_IMPURE_SIGMASIGMA) ? 3 : ((impure & HOTRG_IMPURE_SIGMA) ? 2 : 1); }
+
+// Scratch bytes of one step with slice size xs.
+struct Scratch {
+  size_t gpart, npart, gA, G, jwork, lam, eps, degen, Uside;
+  size_t O1A, A, Alo, O1B, B, Blo, C, O3;
+  size_t total;
+};
+
+Scratch scratch_layout(const StepPlan& p, int xs, int prec, int impure, size_t rs) {
+  Scratch s{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  const int nt = ntensors(impure);
+  s.gpart = take((size_t)kMaxGramJobs * p.nchunks * p.Rmax * p.Rmax * 8);
+  s.npart = take((size_t)kNormPartials * 8);
+  s.gA = take((size_t)kMaxGramJobs * p.Rmax * p.Rmax * 8);
+  s.G = take((size_t)6 * p.nmax * p.nmax * 8);
+  s.jwork = take((size_t)6 * 2 * p.nmax * p.nmax * 8);
+  s.lam = take((size_t)6 * p.nmax * 8);
+  s.eps = take(6 * 8);
+  s.degen = take(6 * 4);
+  s.Uside = take((size_t)6 * p.nmax * kMaxLeg * 8);
+  const int64_t rowsA = (int64_t)xs * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[p.mu];
+  const bool split = prec == HOTRG_TF32X3;
+  s.O1A = take((size_t)xs * p.E * rs);
+  s.A = take((size_t)nt * rowsA * p.ldk * rs);
+  s.Alo = split ? take((size_t)nt * rowsA * p.ldk * rs) : 0;
+  s.O1B = take((size_t)p.chi[p.a] * p.E * rs);
+  s.B = take((size_t)nt * p.rowsB * p.ldk * rs);
+  s.Blo = split ? take((size_t)nt * p.rowsB * p.ldk * rs) : 0;
+  s.C = take((size_t)nt * rowsA * p.rowsB * rs);
+  s.O3 = take((size_t)rowsA * p.rowsB / (p.D[p.c] * p.D[p.c]) * p.chi[p.c] * rs);
+  s.total = off;
+  return s;
+}
+
+Layout persistent_layout(int batch, int64_t cap, int impure, size_t rs) {
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  L.status = take(kStWords * 4);
+  L.lnz = take(batch * 8);
+  L.cval = take(batch * 8);
+  L.trace = take(3 * batch * 8);
+  L.rec = take((size_t)batch * kMaxSteps * sizeof(DevRecord));
+  L.beta = take(batch * 8);
+  L.hfield = take(batch * 8);
+  L.U64 = take((size_t)batch * 4 * kMaxGramN * kMaxLeg * 8);
+  L.Ur = take((size_t)batch * 4 * kMaxGramN * kMaxLeg * rs);
+  L.cap = cap;
+  L.tensors = take((size_t)ntensors(impure) * 2 * batch * cap * rs);
+  L.persistent_end = off;
+  return L;
+}
+
+// canonical row-major strides of a rank-8 tensor with bond dims D
+void canon_strides(const int D[4], int64_t st[8]) {
+  int64_t s = 1;
+  for (int leg = 7; leg >= 0; --leg) {
+    st[leg] = s;
+    s *= D[leg / 2];
+  }
+}
+
+template <typename R>
+R* tensor_ptr(hotrg_ctx* ctx, int which, int buf, int b) {
+  R* base = (R*)(ctx->ws + ctx->L.tensors);
+  return base + (((int64_t)which * 2 + buf) * ctx->batch + b) * ctx->L.cap;
+}
+
+// Build a TTMArgs. `dims` in output iteration order, with per-dim strides.
+struct Dim {
+  int64_t n, in, u, out;
+};
+TTMArgs make_ttm(const std::vector<Dim>& d, int J1, int64_t in_sj1, int64_t u_sj1, int J2, int64_t in_sj2,
+                 int64_t u_sj2, double alpha, double beta) {
+  TTMArgs a{};
+  a.rank = (int)d.size();
+  a.J1 = J1;
+  a.J2 = J2;
+  a.in_sj1 = in_sj1;
+  a.u_sj1 = u_sj1;
+  a.in_sj2 = in_sj2;
+  a.u_sj2 = u_sj2;
+  a.alpha = alpha;
+  a.beta = beta;
+  for (int i = 0; i < a.rank; ++i) {
+    a.dims[i] = d[i].n;
+    a.in_st[i] = d[i].in;
+    a.u_st[i] = d[i].u;
+    a.out_st[i] = d[i].out;
+  }
+  // inner part: trailing dims while the product stays <= 2^16 (at least one dim)
+  int64_t inner = 1;
+  int rin = 0;
+  for (int i = a.rank - 1; i >= 0; --i) {
+    if (rin > 0 && inner * d[i].n > 65536) break;
+    inner *= d[i].n;
+    ++rin;
+  }
+  a.rin = rin;
+  a.inner = inner;
+  int64_t outer = 1;
+  for (int i = 0; i < a.rank - rin; ++i) outer *= d[i].n;
+  a.outer = outer;
+  return a;
+}
+
+// Row-major strides of a list of sizes.
+std::vector<int64_t> rm_strides(const std::vector<int64_t>& n) {
+  std::vector<int64_t> s(n.size());
+  int64_t acc = 1;
+  for (int i = (int)n.size() - 1; i >= 0; --i) {
+    s[i] = acc;
+    acc *= n[i];
+  }
+  return s;
+}
+
+template <typename R>
+hotrg_status build_A(hotrg_ctx* ctx, const StepPlan& p, const R* P, const R* Ua, const R* Ub, int x0, int xs,
+                     R* O1, R* A, R* Alo, cudaStream_t st) {
+  const int mu = p.mu, a = p.a, b = p.b, c = p.c;
+  const int Da = p.D[a], Db = p.D[b], Dc = p.D[c], Dm = p.D[mu];
+  const int ca = p.chi[a], cb = p.chi[b];
+  int64_t ts[8];
+  canon_strides(p.D, ts);
+  // O1[X, b1, c1, c1', mu1, a2, a1', b1', k] = sum_a1 U^a[a1, a2, X] P[...]
+  const std::vector<int64_t> on = {xs, Db, Dc, Dc, Dm, Da, Da, Db, Dm};
+  const std::vector<int64_t> os = rm_strides(on);
+  {
+    std::vector<Dim> d = {
+        {xs, 0, 1, os[0]},                       // X   (U col X, offset x0 on U)
+        {Db, ts[2 * b], 0, os[1]},               // b1
+        {Dc, ts[2 * c], 0, os[2]},               // c1
+        {Dc, ts[2 * c + 1], 0, os[3]},           // c1'
+        {Dm, ts[2 * mu], 0, os[4]},              // mu1
+        {Da, 0, ca, os[5]},                      // a2
+        {Da, ts[2 * a + 1], 0, os[6]},           // a1'
+        {Db, ts[2 * b + 1], 0, os[7]},           // b1'
+        {Dm, ts[2 * mu + 1], 0, os[8]},          // k = T1.mu'
+    };
+    TTMArgs t = make_ttm(d, Da, ts[2 * a], (int64_t)Da * ca, 1, 0, 0, 1.0, 0.0);
+    ttm_limits(p.E, (int64_t)Da * Da * ca - x0, (int64_t)xs * p.E);
+    CK(launch_ttm_r<R>(P, Ua + x0, O1, nullptr, t, kTTMStore, st), "ttm A1");
+  }
+  // A[(X Y c1 c1' mu1), (a2 b2 a1' b1' k)] = sum_b1 U^b[b1, b2, Y] O1[X, b1, ...]
+  {
+    const int64_t Kk = (int64_t)Da * Db * Da * Db * Dm;
+    (void)Kk;
+    const int64_t ld = p.ldk;
+    const std::vector<int64_t> rn = {xs, cb, Dc, Dc, Dm};
+    const std::vector<int64_t> rs = rm_strides(rn);
+    const std::vector<int64_t> kn = {Da, Db, Da, Db, Dm};
+    const std::vector<int64_t> ks = rm_strides(kn);
+    std::vector<Dim> d = {
+        {xs, os[0], 0, rs[0] * ld},   // X
+        {cb, 0, 1, rs[1] * ld},       // Y
+        {Dc, os[2], 0, rs[2] * ld},   // c1
+        {Dc, os[3], 0, rs[3] * ld},   // c1'
+        {Dm, os[4], 0, rs[4] * ld},   // mu1
+        {Da, os[5], 0, ks[0]},        // a2
+        {Db, 0, cb, ks[1]},           // b2
+        {Da, os[6], 0, ks[2]},        // a1'
+        {Db, os[7], 0, ks[3]},        // b1'
+        {Dm, os[8], 0, ks[4]},        // k
+    };
+    TTMArgs t = make_ttm(d, Db, os[1], (int64_t)Db * cb, 1, 0, 0, 1.0, 0.0);
+    const int mode = Alo ? kTTMSplitTF32 : kTTMStore;
+    ttm_limits((int64_t)xs * p.E, (int64_t)Db * Db * cb, (int64_t)xs * cb * Dc * Dc * Dm * ld);
+    CK(launch_ttm_r<R>(O1, Ub, A, Alo, t, mode, st), "ttm A2");
+  }
+  return HOTRG_OK;
+}
+
+template <typename R>
+hotrg_status build_B(hotrg_ctx* ctx, const StepPlan& p, const R* Q, const R* Ua, const R* Ub, R* O1, R* B, R* Blo,
+                     cudaStream_t st) {
+  const int mu = p.mu, a = p.a, b = p.b, c = p.c;
+  const int Da = p.D[a], Db = p.D[b], Dc = p.D[c], Dm = p.D[mu];
+  const int ca = p.chi[a], cb = p.chi[b];
+  int64_t ts[8];
+  canon_strides(p.D, ts);
+  // O1[X', b2', c2, c2', mu2', a2, b2, a1', k] = sum_a2' U^a[a1', a2', X'] Q[...]
+  const std::vector<int64_t> on = {ca, Db, Dc, Dc, Dm, Da, Db, Da, Dm};
+  const std::vector<int64_t> os = rm_strides(on);
+  {
+    std::vector<Dim> d = {
+        {ca, 0, 1, os[0]},                       // X'
+        {Db, ts[2 * b + 1], 0, os[1]},           // b2'
+        {Dc, ts[2 * c], 0, os[2]},               // c2
+        {Dc, ts[2 * c + 1], 0, os[3]},           // c2'
+        {Dm, ts[2 * mu + 1], 0, os[4]},          // mu2'
+        {Da, ts[2 * a], 0, os[5]},               // a2
+        {Db, ts[2 * b], 0, os[6]},               // b2
+        {Da, 0, (int64_t)Da * ca, os[7]},        // a1'
+        {Dm, ts[2 * mu], 0, os[8]},              // k = T2.mu
+    };
+    TTMArgs t = make_ttm(d, Da, ts[2 * a + 1], ca, 1, 0, 0, 1.0, 0.0);
+    ttm_limits(p.E, (int64_t)Da * Da * ca, (int64_t)ca * p.E);
+    CK(launch_ttm_r<R>(Q, Ua, O1, nullptr, t, kTTMStore, st), "ttm B1");
+  }
+  {
+    const int64_t ld = p.ldk;
+    const std::vector<int64_t> rn = {ca, cb, Dc, Dc, Dm};
+    const std::vector<int64_t> rs = rm_strides(rn);
+    const std::vector<int64_t> kn = {Da, Db, Da, Db, Dm};
+    const std::vector<int64_t> ks = rm_strides(kn);
+    std::vector<Dim> d = {
+        {ca, os[0], 0, rs[0] * ld},             // X'
+        {cb, 0, 1, rs[1] * ld},                 // Y'
+        {Dc, os[2], 0, rs[2] * ld},             // c2
+        {Dc, os[3], 0, rs[3] * ld},             // c2'
+        {Dm, os[4], 0, rs[4] * ld},             // mu2'
+        {Da, os[5], 0, ks[0]},                  // a2
+        {Db, os[6], 0, ks[1]},                  // b2
+        {Da, os[7], 0, ks[2]},                  // a1'
+        {Db, 0, (int64_t)Db * cb, ks[3]},       // b1'
+        {Dm, os[8], 0, ks[4]},                  // k
+    };
+    TTMArgs t = make_ttm(d, Db, os[1], cb, 1, 0, 0, 1.0, 0.0);
+    const int mode = Blo ? kTTMSplitTF32 : kTTMStore;
+    ttm_limits((int64_t)ca * p.E, (int64_t)Db * Db * cb, p.rowsB * ld);
+    CK(launch_ttm_r<R>(O1, Ub, B, Blo, t, mode, st), "ttm B2");
+  }
+  return HOTRG_OK;
+}
+
+// T'[slice] = C x_{(c1 c2)} U^c x_{(c1' c2')} U^c, written into the canonical layout.
+template <typename R>
+hotrg_status close_C(hotrg_ctx* ctx, const StepPlan& p, const R* C, const R* Uc, int x0, int xs, R* O3, R* Tn,
+                     cudaStream_t st) {
+  const int mu = p.mu, a = p.a, b = p.b, c = p.c;
+  const int Dc = p.D[c], Dm = p.D[mu];
+  const int ca = p.chi[a], cb = p.chi[b], cc = p.chi[c];
+  const int64_t N = p.rowsB;
+  // C row m = (X, Y, c1, c1', mu1), col n = (X', Y', c2, c2', mu2')
+  const std::vector<int64_t> mn = {xs, cb, Dc, Dc, Dm};
+  const std::vector<int64_t> ms = rm_strides(mn);
+  const std::vector<int64_t> nn = {ca, cb, Dc, Dc, Dm};
+  const std::vector<int64_t> ns = rm_strides(nn);
+  // O3[Z, X, Y, c1', mu1, X', Y', c2', mu2']
+  const std::vector<int64_t> on = {cc, xs, cb, Dc, Dm, ca, cb, Dc, Dm};
+  const std::vector<int64_t> os = rm_strides(on);
+  {
+    std::vector<Dim> d = {
+        {cc, 0, 1, os[0]},              // Z
+        {xs, ms[0] * N, 0, os[1]},      // X
+        {cb, ms[1] * N, 0, os[2]},      // Y
+        {Dc, ms[3] * N, 0, os[3]},      // c1'
+        {Dm, ms[4] * N, 0, os[4]},      // mu1
+        {ca, ns[0], 0, os[5]},          // X'
+        {cb, ns[1], 0, os[6]},          // Y'
+        {Dc, ns[3], 0, os[7]},          // c2'
+        {Dm, ns[4], 0, os[8]},          // mu2'
+    };
+    TTMArgs t = make_ttm(d, Dc, ms[2] * N, (int64_t)Dc * cc, Dc, ns[2], cc, 1.0, 0.0);
+    ttm_limits((int64_t)xs * cb * Dc * Dc * Dm * N, (int64_t)Dc * Dc * cc, on[0] * os[0]);
+    CK(launch_ttm_r<R>(C, Uc, O3, nullptr, t, kTTMStore, st), "ttm close1");
+  }
+  {
+    int64_t tn[8];
+    canon_strides(p.newD, tn);
+    // output iteration in canonical order of the new tensor, restricted to the X slice
+    int64_t sizes[8], in_st[8], u_st[8];
+    for (int n = 0; n < 4; ++n) {
+      for (int pr = 0; pr < 2; ++pr) {
+        const int leg = 2 * n + pr;
+        int64_t sz = p.newD[n], in = 0, u = 0;
+        if (n == a) {
+          if (pr == 0) {
+            sz = xs;
+            in = os[1];
+          } else {
+            in = os[5];
+          }
+        } else if (n == b) {
+          in = pr == 0 ? os[2] : os[6];
+        } else if (n == c) {
+          if (pr == 0) in = os[0];
+          else u = 1;                       // Z' from U^c column
+        } else {                            // mu
+          in = pr == 0 ? os[4] : os[8];
+        }
+        sizes[leg] = sz;
+        in_st[leg] = in;
+        u_st[leg] = u;
+      }
+    }
+    std::vector<Dim> d;
+    for (int leg = 0; leg < 8; ++leg) d.push_back({sizes[leg], in_st[leg], u_st[leg], tn[leg]});
+    TTMArgs t = make_ttm(d, Dc, os[3], (int64_t)Dc * cc, Dc, os[7], cc, 1.0, 0.0);
+    R* out = Tn + (int64_t)x0 * tn[2 * a];
+    ttm_limits(on[0] * os[0], (int64_t)Dc * Dc * cc, p.Enew - (int64_t)x0 * tn[2 * a]);
+    CK(launch_ttm_r<R>(O3, Uc, out, nullptr, t, kTTMStore, st), "ttm close2");
+  }
+  return HOTRG_OK;
+}
+
+template <typename R>
+hotrg_status gemm(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R* Blo, int64_t ld, R* C, int64_t M,
+                  int64_t N, int64_t K, double alpha, double beta, cudaStream_t st) {
+  if (ctx->prec == HOTRG_TF32X3) {
+    CK(launch_gemm_tf32x3((const float*)A, (const float*)Alo, ld, (const float*)B, (const float*)Blo, ld, (float*)C,
+                          N, M, N, K, (float)alpha, (float)beta, (int*)(ctx->ws + ctx->L.status), st),
+       "gemm tf32x3");
+  } else {
+    CK(launch_gemm_simt<R>(A, ld, B, ld, C, N, M, N, K, alpha, beta, st), "gemm simt");
+  }
+  return HOTRG_OK;
+}
+
+template <typename R>
+hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
+  cudaStream_t st = ctx->stream;
+  const Scratch sc = scratch_layout(p, p.xs, ctx->prec, ctx->impure_active, ctx->rsize);
+  char* sb = ctx->ws + ctx->L.persistent_end;
+  const int mu = p.mu;
+  const int kstep = ctx->k;  // steps done before this one
+  int* status = (int*)(ctx->ws + ctx->L.status);
+  const int nt = ntensors(ctx->impure_active);
+  const bool split = ctx->prec == HOTRG_TF32X3;
+  const int64_t rowsA = (int64_t)p.xs * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[mu];
+
+  for (int bidx = 0; bidx < ctx->batch; ++bidx) {
+    const R* T = tensor_ptr<R>(ctx, 0, ctx->cur, bidx);
+    DevRecord* rec = (DevRecord*)(ctx->ws + ctx->L.rec) + (int64_t)bidx * kMaxSteps + kstep;
+    // ---------------------------------------------------------------- 1. Gram
+    int64_t ts[8];
+    canon_strides(p.D, ts);
+    GramPack gp{};
+    int nj = 0;
+    int dirs[3], nd = 0;
+    for (int n = 0; n < 4; ++n)
+      if (n != mu) dirs[nd++] = n;
+    double* gpart = (double*)(sb + sc.gpart);
+    double* gA = (double*)(sb + sc.gA);
+    for (int i = 0; i < 3; ++i) {
+      const int n = dirs[i];
+      for (int side = 0; side < 2; ++side) {
+        for (int half = 0; half < 2; ++half) {   // half 0: k on mu' (T1), 1: k on mu (T2)
+          GramJob& j = gp.j[nj];
+          j.T = T;
+          const int leg = 2 * n + side;
+          const int kleg = half == 0 ? 2 * mu + 1 : 2 * mu;
+          j.D1 = p.D[n];
+          j.D2 = p.D[mu];
+          j.s1 = ts[leg];
+          j.s2 = ts[kleg];
+          j.nrest = 0;
+          j.K = 1;
+          for (int l = 0; l < 8; ++l) {
+            if (l == leg || l == kleg) continue;
+            j.rdims[j.nrest] = p.D[l / 2];
+            j.rst[j.nrest] = ts[l];
+            j.K *= p.D[l / 2];
+            ++j.nrest;
+          }
+          j.partial = gpart + (int64_t)nj * p.nchunks * p.Rmax * p.Rmax;
+          ++nj;
+        }
+      }
+    }
+    CK(launch_gram<R>(gp, nj, p.Rmax, p.nchunks, st), "gram");
+    for (int i = 0; i < nj; ++i) {
+      const int R2 = gp.j[i].D1 * gp.j[i].D2;
+      CK(launch_gram_reduce(gp.j[i].partial, p.nchunks, (int64_t)R2 * R2, gA + (int64_t)i * p.Rmax * p.Rmax, st),
+         "gram reduce");
+    }
+    double* G = (double*)(sb + sc.G);
+    for (int i = 0; i < 3; ++i) {
+      for (int side = 0; side < 2; ++side) {
+        const int j1 = (i * 2 + side) * 2;
+        CK(launch_gram_merge(gA + (int64_t)j1 * p.Rmax * p.Rmax, gA + (int64_t)(j1 + 1) * p.Rmax * p.Rmax,
+                             p.D[dirs[i]], p.D[mu], G + (int64_t)(i * 2 + side) * p.nmax * p.nmax, st),
+           "gram merge");
+      }
+    }
+    // ---------------------------------------------------------------- 2. eigen + side
+    EigPack ep{};
+    double* lam = (double*)(sb + sc.lam);
+    double* eps = (double*)(sb + sc.eps);
+    int* degen = (int*)(sb + sc.degen);
+    double* Uside = (double*)(sb + sc.Uside);
+    double* jwork = (double*)(sb + sc.jwork);
+    int nmax = 0;
+    for (int i = 0; i < 3; ++i) {
+      for (int side = 0; side < 2; ++side) {
+        const int e = i * 2 + side;
+        EigJob& j = ep.j[e];
+        j.n = p.D[dirs[i]] * p.D[dirs[i]];
+        j.chi = p.chi[dirs[i]];
+        j.G = G + (int64_t)e * p.nmax * p.nmax;
+        j.work = jwork + (int64_t)e * 2 * p.nmax * p.nmax;
+        j.lam = lam + (int64_t)e * p.nmax;
+        j.eps = eps + e;
+        j.degenerate = degen + e;
+        j.U = Uside + (int64_t)e * p.nmax * kMaxLeg;
+        nmax = std::max(nmax, j.n);
+      }
+    }
+    const bool fp64 = ctx->prec == HOTRG_FP64;
+    CK(launch_jacobi(ep, 6, nmax, fp64 ? 1e-10 : 1e-6, status, st), "jacobi");
+    SelectPack sp{};
+    double* U64 = (double*)(ctx->ws + ctx->L.U64) + (int64_t)bidx * 4 * kMaxGramN * kMaxLeg;
+    R* Ur = (R*)(ctx->ws + ctx->L.Ur) + (int64_t)bidx * 4 * kMaxGramN * kMaxLeg;
+    for (int i = 0; i < 3; ++i) {
+      const int n = dirs[i];
+      SelectJob& j = sp.j[i];
+      j.U[0] = ep.j[i * 2].U;
+      j.U[1] = ep.j[i * 2 + 1].U;
+      j.lam0 = ep.j[i * 2].lam;
+      j.eps[0] = ep.j[i * 2].eps;
+      j.eps[1] = ep.j[i * 2 + 1].eps;
+      j.degen[0] = ep.j[i * 2].degenerate;
+      j.degen[1] = ep.j[i * 2 + 1].degenerate;
+      j.U64 = U64 + (int64_t)n * kMaxGramN * kMaxLeg;
+      j.Ur = Ur + (int64_t)n * kMaxGramN * kMaxLeg;
+      j.n = ep.j[i * 2].n;
+      j.chi = ep.j[i * 2].chi;
+      j.rec_eps = rec->eps[n];
+      j.rec_primed = &rec->primed[n];
+      j.rec_degen = &rec->degen[n];
+    }
+    CK(launch_select<R>(sp, 3, fp64 ? 1e-9 : 1e-6, st), "select");
+    const R* Ua = Ur + (int64_t)p.a * kMaxGramN * kMaxLeg;
+    const R* Ub = Ur + (int64_t)p.b * kMaxGramN * kMaxLeg;
+    const R* Uc = Ur + (int64_t)p.c * kMaxGramN * kMaxLeg;
+    // ---------------------------------------------------------------- 3. contraction
+    R* O1A = (R*)(sb + sc.O1A);
+    R* O1B = (R*)(sb + sc.O1B);
+    R* Abuf = (R*)(sb + sc.A);
+    R* Alob = split ? (R*)(sb + sc.Alo) : nullptr;
+    R* Bbuf = (R*)(sb + sc.B);
+    R* Blob = split ? (R*)(sb + sc.Blo) : nullptr;
+    R* Cbuf = (R*)(sb + sc.C);
+    R* O3 = (R*)(sb + sc.O3);
+    const int64_t Asz = rowsA * p.ldk, Bsz = p.rowsB * p.ldk, Csz = rowsA * p.rowsB;
+    const R* src[3];
+    R* dst[3];
+    for (int w = 0; w < nt; ++w) {
+      src[w] = tensor_ptr<R>(ctx, w, ctx->cur, bidx);
+      dst[w] = tensor_ptr<R>(ctx, w, 1 - ctx->cur, bidx);
+    }
+    // zero the padding columns of A and B (read by nothing when ldk == K)
+    if (p.ldk != p.K) {
+      CK(cudaMemsetAsync(Abuf, 0, (size_t)nt * Asz * ctx->rsize, st), "memset A");
+      CK(cudaMemsetAsync(Bbuf, 0, (size_t)nt * Bsz * ctx->rsize, st), "memset B");
+      if (split) {
+        CK(cudaMemsetAsync(Alob, 0, (size_t)nt * Asz * ctx->rsize, st), "memset Alo");
+        CK(cudaMemsetAsync(Blob, 0, (size_t)nt * Bsz * ctx->rsize, st), "memset Blo");
+      }
+    }
+    for (int w = 0; w < nt; ++w) {
+      hotrg_status s = build_B<R>(ctx, p, src[w], Ua, Ub, O1B, Bbuf + w * Bsz, split ? Blob + w * Bsz : nullptr, st);
+      if (s != HOTRG_OK) return s;
+    }
+    for (int x0 = 0; x0 < p.chi[p.a]; x0 += p.xs) {
+      const int xs = std::min(p.xs, p.chi[p.a] - x0);
+      const int64_t rA = (int64_t)xs * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[mu];
+      for (int w = 0; w < nt; ++w) {
+        hotrg_status s = build_A<R>(ctx, p, src[w], Ua, Ub, x0, xs, O1A, Abuf + w * Asz,
+                                    split ? Alob + w * Asz : nullptr, st);
+        if (s != HOTRG_OK) return s;
+      }
+      auto Ap = [&](int w) { return Abuf + w * Asz; };
+      auto Alp = [&](int w) { return split ? Alob + w * Asz : nullptr; };
+      auto Bp = [&](int w) { return Bbuf + w * Bsz; };
+      auto Blp = [&](int w) { return split ? Blob + w * Bsz : nullptr; };
+      hotrg_status s;
+      // C_T = A(T) B(T)^T
+      s = gemm<R>(ctx, Ap(0), Alp(0), Bp(0), Blp(0), p.ldk, Cbuf, rA, p.rowsB, p.K, 1.0, 0.0, st);
+      if (s != HOTRG_OK) return s;
+      if (nt >= 2) {  // C_S = (A(S) B(T)^T + A(T) B(S)^T) / 2
+        s = gemm<R>(ctx, Ap(1), Alp(1), Bp(0), Blp(0), p.ldk, Cbuf + Csz, rA, p.rowsB, p.K, 0.5, 0.0, st);
+        if (s != HOTRG_OK) return s;
+        s = gemm<R>(ctx, Ap(0), Alp(0), Bp(1), Blp(1), p.ldk, Cbuf + Csz, rA, p.rowsB, p.K, 0.5, 1.0, st);
+        if (s != HOTRG_OK) return s;
+      }
+      if (nt >= 3) {
+        if (kstep == 0) {  // M_1 = A(S) B(S)^T: the nearest-neighbour pair inside the first block
+          s = gemm<R>(ctx, Ap(1), Alp(1), Bp(1), Blp(1), p.ldk, Cbuf + 2 * Csz, rA, p.rowsB, p.K, 1.0, 0.0, st);
+          if (s != HOTRG_OK) return s;
+        } else {           // M' = (A(M) B(T)^T + A(T) B(M)^T) / 2
+          s = gemm<R>(ctx, Ap(2), Alp(2), Bp(0), Blp(0), p.ldk, Cbuf + 2 * Csz, rA, p.rowsB, p.K, 0.5, 0.0, st);
+          if (s != HOTRG_OK) return s;
+          s = gemm<R>(ctx, Ap(0), Alp(0), Bp(2), Blp(2), p.ldk, Cbuf + 2 * Csz, rA, p.rowsB, p.K, 0.5, 1.0, st);
+          if (s != HOTRG_OK) return s;
+        }
+      }
+      for (int w = 0; w < nt; ++w) {
+        s = close_C<R>(ctx, p, Cbuf + w * Csz, Uc, x0, xs, O3, dst[w], st);
+        if (s != HOTRG_OK) return s;
+      }
+    }
+    // ---------------------------------------------------------------- 4. normalise
+    double* lnz = (double*)(ctx->ws + ctx->L.lnz) + bidx;
+    double* cval = (double*)(ctx->ws + ctx->L.cval) + bidx;
+    const double weight = ldexp(1.0, -(kstep + 1));
+    CK(launch_norm<R>(dst[0], p.Enew, (double*)(sb + sc.npart), weight, cval, lnz, &rec->ln_c, status, st),
+       "norm");
+    for (int w = 0; w < nt; ++w) CK(launch_scale<R>(dst[w], p.Enew, cval, st), "scale");
+  }
+  return HOTRG_OK;
+}
+
+hotrg_status check_ready(hotrg_ctx* ctx) {
+  if (!ctx) return HOTRG_EINVAL;
+  if (!ctx->ready) return HOTRG_EWORKSPACE;
+  return HOTRG_OK;
+}
+
+hotrg_status sync_and_status(hotrg_ctx* ctx) {
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "stream sync");
+  int st[kStWords];
+  e = cudaMemcpy(st, ctx->ws + ctx->L.status, sizeof(st), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "status read");
+  if (st[kStTimeout]) ctx->sticky = HOTRG_ETIMEOUT;
+  else if (st[kStNonFinite]) ctx->sticky = HOTRG_ENONFINITE;
+  else if (st[kStNoConv]) ctx->sticky = HOTRG_ENOCONV;
+  return ctx->sticky ? (hotrg_status)ctx->sticky : HOTRG_OK;
+}
+
+size_t persistent_bytes(const hotrg_ctx* ctx, int64_t cap) {
+  return persistent_layout(ctx->batch, cap, ctx->impure, ctx->rsize).persistent_end;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hotrg_status_string(int s) {
+  switch (s) {
+    case HOTRG_OK: return "ok";
+    case HOTRG_EINVAL: return "invalid argument";
+    case HOTRG_EWORKSPACE: return "workspace missing or too small";
+    case HOTRG_ECUDA: return "CUDA error";
+    case HOTRG_ENOCONV: return "eigensolver did not converge";
+    case HOTRG_ENONFINITE: return "non-finite or non-positive norm";
+    case HOTRG_ETIMEOUT: return "device-side wait timed out";
+    case HOTRG_ESTATE: return "call out of order or context in error state";
+    case HOTRG_EUNSUPPORTED: return "unsupported precision or size";
+    default: return "unknown status";
+  }
+}
+
+const char* hotrg_last_error(void) { return g_last_error.c_str(); }
+
+hotrg_status hotrg_create(hotrg_ctx** out, int batch, int dcut_max, int prec, int impure_mask) {
+  if (!out || batch < 1 || batch > 4096 || dcut_max < 2 || dcut_max > kMaxLeg) return HOTRG_EINVAL;
+  if (prec != HOTRG_FP64 && prec != HOTRG_FP32 && prec != HOTRG_TF32X3) return HOTRG_EINVAL;
+  if (impure_mask < 0 || impure_mask > 3 || impure_mask == HOTRG_IMPURE_SIGMASIGMA) return HOTRG_EINVAL;
+  hotrg_ctx* c = new hotrg_ctx();
+  c->batch = batch;
+  c->dcut_max = dcut_max;
+  c->prec = prec;
+  c->impure = impure_mask;
+  c->impure_active = impure_mask;
+  c->rsize = prec == HOTRG_FP64 ? 8 : 4;
+  *out = c;
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_destroy(hotrg_ctx* ctx) {
+  delete ctx;
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_workspace_size(hotrg_ctx* ctx, int nsteps, const int* dirs, const int* dcuts, const int* dims0,
+                                  size_t* bytes) {
+  if (!ctx || !bytes || nsteps < 0 || (nsteps > 0 && (!dirs || !dcuts))) return HOTRG_EINVAL;
+  int D[4] = {2, 2, 2, 2};
+  if (dims0)
+    for (int n = 0; n < 4; ++n) {
+      if (dims0[n] < 1 || dims0[n] > kMaxLeg) return HOTRG_EINVAL;
+      D[n] = dims0[n];
+    }
+  size_t scratch = 0;
+  int64_t cap = tensor_elems(D);
+  if (nsteps == 0) {
+    int Dm[4] = {ctx->dcut_max, ctx->dcut_max, ctx->dcut_max, ctx->dcut_max};
+    StepPlan p = make_plan(Dm, 0, ctx->dcut_max);
+    scratch = scratch_layout(p, p.xs, ctx->prec, ctx->impure, ctx->rsize).total;
+    cap = std::max(cap, tensor_elems(Dm));
+  } else {
+    for (int i = 0; i < nsteps; ++i) {
+      if (dirs[i] < 0 || dirs[i] > 3 || dcuts[i] < 1 || dcuts[i] > ctx->dcut_max) return HOTRG_EINVAL;
+      StepPlan p = make_plan(D, dirs[i], dcuts[i]);
+      scratch = std::max(scratch, scratch_layout(p, p.xs, ctx->prec, ctx->impure, ctx->rsize).total);
+      for (int n = 0; n < 4; ++n) {
+        D[n] = p.newD[n];
+        if (D[n] > kMaxLeg) return HOTRG_EINVAL;
+      }
+      cap = std::max(cap, tensor_elems(D));
+    }
+  }
+  ctx->cap_planned = cap;
+  *bytes = persistent_bytes(ctx, cap) + scratch;
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_set_workspace(hotrg_ctx* ctx, void* dev_ptr, size_t bytes) {
+  if (!ctx || !dev_ptr || ((uintptr_t)dev_ptr & 255)) return HOTRG_EINVAL;
+  int64_t cap = ctx->cap_planned;
+  if (cap == 0) {
+    int64_t d = ctx->dcut_max;
+    cap = d * d * d * d * d * d * d * d;
+  }
+  Layout L = persistent_layout(ctx->batch, cap, ctx->impure, ctx->rsize);
+  if (L.persistent_end > bytes) return HOTRG_EWORKSPACE;
+  ctx->ws = (char*)dev_ptr;
+  ctx->ws_bytes = bytes;
+  ctx->L = L;
+  ctx->ready = true;
+  ctx->initialised = false;
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_set_stream(hotrg_ctx* ctx, void* s) {
+  if (!ctx) return HOTRG_EINVAL;
+  ctx->stream = (cudaStream_t)s;
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_init_tensor(hotrg_ctx* ctx, const double* beta, const double* h) {
+  hotrg_status r = check_ready(ctx);
+  if (r != HOTRG_OK) return r;
+  if (!beta || !h) return HOTRG_EINVAL;
+  for (int b = 0; b < ctx->batch; ++b)
+    if (!(beta[b] >= 0.0) || !isfinite(beta[b]) || !isfinite(h[b])) return HOTRG_EINVAL;
+  if (ctx->L.cap < 256) return HOTRG_EWORKSPACE;
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemsetAsync(ctx->ws + ctx->L.status, 0, kStWords * 4, st), "init status");
+  CK(cudaMemsetAsync(ctx->ws + ctx->L.rec, 0, (size_t)ctx->batch * kMaxSteps * sizeof(DevRecord), st), "init rec");
+  CK(cudaMemcpyAsync(ctx->ws + ctx->L.beta, beta, ctx->batch * 8, cudaMemcpyHostToDevice, st), "beta");
+  CK(cudaMemcpyAsync(ctx->ws + ctx->L.hfield, h, ctx->batch * 8, cudaMemcpyHostToDevice, st), "h");
+  ctx->impure_active = ctx->impure;
+  ctx->cur = 0;
+  const double* db = (const double*)(ctx->ws + ctx->L.beta);
+  const double* dh = (const double*)(ctx->ws + ctx->L.hfield);
+  double* lnz = (double*)(ctx->ws + ctx->L.lnz);
+  if (ctx->prec == HOTRG_FP64)
+    CK(launch_init<double>(db, dh, tensor_ptr<double>(ctx, 0, 0, 0),
+                           ctx->impure ? tensor_ptr<double>(ctx, 1, 0, 0) : nullptr, ctx->L.cap, lnz, ctx->batch, st),
+       "init");
+  else
+    CK(launch_init<float>(db, dh, tensor_ptr<float>(ctx, 0, 0, 0),
+                          ctx->impure ? tensor_ptr<float>(ctx, 1, 0, 0) : nullptr, ctx->L.cap, lnz, ctx->batch, st),
+       "init");
+  // the beta/h uploads read host memory that may go away: make them complete now
+  CK(cudaStreamSynchronize(st), "init sync");
+  ctx->h_host.assign(h, h + ctx->batch);
+  for (int n = 0; n < 4; ++n) ctx->dims[n] = 2;
+  ctx->k = 0;
+  ctx->sticky = 0;
+  ctx->initialised = true;
+  ctx->last_mu = -1;
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_set_tensor(hotrg_ctx* ctx, int b, const int dims[4], const double* T_host) {
+  hotrg_status r = check_ready(ctx);
+  if (r != HOTRG_OK) return r;
+  if (!dims || !T_host || b < 0 || b >= ctx->batch) return HOTRG_EINVAL;
+  for (int n = 0; n < 4; ++n)
+    if (dims[n] < 1 || dims[n] > ctx->dcut_max) return HOTRG_EINVAL;
+  const int64_t E = tensor_elems(dims);
+  if (E > ctx->L.cap) return HOTRG_EWORKSPACE;
+  if (ctx->initialised && ctx->k > 0 && b > 0) return HOTRG_ESTATE;
+  if (b > 0 && ctx->initialised)
+    for (int n = 0; n < 4; ++n)
+      if (dims[n] != ctx->dims[n]) return HOTRG_EINVAL;
+  double nrm2 = 0;
+  for (int64_t i = 0; i < E; ++i) nrm2 += T_host[i] * T_host[i];
+  const double c = sqrt(nrm2);
+  if (!(c > 0) || !isfinite(c)) return HOTRG_EINVAL;
+  cudaStream_t st = ctx->stream;
+  CK(cudaStreamSynchronize(st), "set_tensor sync");
+  if (b == 0) {
+    CK(cudaMemset(ctx->ws + ctx->L.status, 0, kStWords * 4), "status");
+    CK(cudaMemset(ctx->ws + ctx->L.rec, 0, (size_t)ctx->batch * kMaxSteps * sizeof(DevRecord)), "rec");
+    ctx->cur = 0;
+  }
+  if (ctx->prec == HOTRG_FP64) {
+    std::vector<double> tmp(E);
+    for (int64_t i = 0; i < E; ++i) tmp[i] = T_host[i] / c;
+    CK(cudaMemcpy(tensor_ptr<double>(ctx, 0, ctx->cur, b), tmp.data(), E * 8, cudaMemcpyHostToDevice), "upload");
+  } else {
+    std::vector<float> tmp(E);
+    for (int64_t i = 0; i < E; ++i) tmp[i] = (float)(T_host[i] / c);
+    CK(cudaMemcpy(tensor_ptr<float>(ctx, 0, ctx->cur, b), tmp.data(), E * 4, cudaMemcpyHostToDevice), "upload");
+  }
+  const double lc = log(c);
+  CK(cudaMemcpy((double*)(ctx->ws + ctx->L.lnz) + b, &lc, 8, cudaMemcpyHostToDevice), "lnz");
+  ctx->impure_active = 0;
+  for (int n = 0; n < 4; ++n) ctx->dims[n] = dims[n];
+  ctx->k = 0;
+  ctx->sticky = 0;
+  ctx->initialised = true;
+  ctx->last_mu = -1;
+  ctx->h_host.assign(ctx->batch, 0.0);
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_step(hotrg_ctx* ctx, int dir, int dcut) {
+  hotrg_status r = check_ready(ctx);
+  if (r != HOTRG_OK) return r;
+  if (dir < 0 || dir > 3 || dcut < 1 || dcut > ctx->dcut_max) return HOTRG_EINVAL;
+  if (!ctx->initialised || ctx->sticky) return HOTRG_ESTATE;
+  if (ctx->k >= kMaxSteps) return HOTRG_ESTATE;
+  StepPlan p = make_plan(ctx->dims, dir, dcut);
+  for (int n = 0; n < 4; ++n)
+    if (p.newD[n] > kMaxLeg) return HOTRG_EINVAL;
+  if (p.Enew > ctx->L.cap) return HOTRG_EWORKSPACE;
+  // largest X slice whose scratch fits
+  const size_t avail = ctx->ws_bytes - ctx->L.persistent_end;
+  int xs = p.chi[p.a];
+  while (xs > 1 && scratch_layout(p, xs, ctx->prec, ctx->impure_active, ctx->rsize).total > avail) --xs;
+  if (scratch_layout(p, xs, ctx->prec, ctx->impure_active, ctx->rsize).total > avail) return HOTRG_EWORKSPACE;
+  p.xs = xs;
+  hotrg_status s = ctx->prec == HOTRG_FP64 ? do_step<double>(ctx, p) : do_step<float>(ctx, p);
+  if (s != HOTRG_OK) return s;
+  ctx->mu_hist[ctx->k] = dir;
+  for (int n = 0; n < 4; ++n) {
+    ctx->dims_hist[ctx->k][n] = p.newD[n];
+    ctx->dims[n] = p.newD[n];
+    ctx->last_chi[n] = p.chi[n];
+    ctx->last_Dold[n] = p.D[n];
+  }
+  ctx->last_mu = dir;
+  ctx->cur = 1 - ctx->cur;
+  ctx->k += 1;
+  return HOTRG_OK;
+}
+
+static hotrg_status traces(hotrg_ctx* ctx, int which, std::vector<double>& out) {
+  const double* dtr = (const double*)(ctx->ws + ctx->L.trace);
+  if (ctx->prec == HOTRG_FP64)
+    CK(launch_trace<double>(tensor_ptr<double>(ctx, which, ctx->cur, 0), ctx->L.cap, ctx->dims, ctx->batch,
+                            (double*)dtr + which * ctx->batch, ctx->stream),
+       "trace");
+  else
+    CK(launch_trace<float>(tensor_ptr<float>(ctx, which, ctx->cur, 0), ctx->L.cap, ctx->dims, ctx->batch,
+                           (double*)dtr + which * ctx->batch, ctx->stream),
+       "trace");
+  hotrg_status s = sync_and_status(ctx);
+  if (s != HOTRG_OK) return s;
+  out.resize(ctx->batch);
+  CK(cudaMemcpy(out.data(), dtr + which * ctx->batch, ctx->batch * 8, cudaMemcpyDeviceToHost), "trace read");
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_lnZ(hotrg_ctx* ctx, double* out) {
+  hotrg_status r = check_ready(ctx);
+  if (r != HOTRG_OK) return r;
+  if (!out) return HOTRG_EINVAL;
+  if (!ctx->initialised) return HOTRG_ESTATE;
+  std::vector<double> tr, acc(ctx->batch);
+  r = traces(ctx, 0, tr);
+  if (r != HOTRG_OK) return r;
+  CK(cudaMemcpy(acc.data(), ctx->ws + ctx->L.lnz, ctx->batch * 8, cudaMemcpyDeviceToHost), "lnz read");
+  hotrg_status res = HOTRG_OK;
+  for (int b = 0; b < ctx->batch; ++b) {
+    if (!(tr[b] > 0) || !isfinite(tr[b])) {
+      out[b] = nan("");
+      res = HOTRG_ENONFINITE;
+    } else {
+      out[b] = acc[b] + log(tr[b]) * ldexp(1.0, -ctx->k);
+    }
+  }
+  return res;
+}
+
+hotrg_status hotrg_impure_magnetization(hotrg_ctx* ctx, double* m) {
+  hotrg_status r = check_ready(ctx);
+  if (r != HOTRG_OK) return r;
+  if (!m) return HOTRG_EINVAL;
+  if (!ctx->initialised || !(ctx->impure_active & HOTRG_IMPURE_SIGMA)) return HOTRG_ESTATE;
+  std::vector<double> t, s;
+  if ((r = traces(ctx, 0, t)) != HOTRG_OK) return r;
+  if ((r = traces(ctx, 1, s)) != HOTRG_OK) return r;
+  for (int b = 0; b < ctx->batch; ++b) m[b] = s[b] / t[b];
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_impure_energy(hotrg_ctx* ctx, double* e, double* ss) {
+  hotrg_status r = check_ready(ctx);
+  if (r != HOTRG_OK) return r;
+  if (!ctx->initialised || !(ctx->impure_active & HOTRG_IMPURE_SIGMASIGMA) || ctx->k < 1) return HOTRG_ESTATE;
+  std::vector<double> t, s, mm;
+  if ((r = traces(ctx, 0, t)) != HOTRG_OK) return r;
+  if ((r = traces(ctx, 1, s)) != HOTRG_OK) return r;
+  if ((r = traces(ctx, 2, mm)) != HOTRG_OK) return r;
+  for (int b = 0; b < ctx->batch; ++b) {
+    const double sig2 = mm[b] / t[b];
+    if (ss) ss[b] = sig2;
+    if (e) e[b] = -4.0 * sig2 - ctx->h_host[b] * s[b] / t[b];
+  }
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_step_info(hotrg_ctx* ctx, int b, int step, hotrg_step_record* rec) {
+  hotrg_status r = check_ready(ctx);
+  if (r != HOTRG_OK) return r;
+  if (!rec || b < 0 || b >= ctx->batch || step < 1 || step > ctx->k) return HOTRG_EINVAL;
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  DevRecord d;
+  CK(cudaMemcpy(&d, (DevRecord*)(ctx->ws + ctx->L.rec) + (int64_t)b * kMaxSteps + (step - 1), sizeof(d),
+                cudaMemcpyDeviceToHost),
+     "record read");
+  memset(rec, 0, sizeof(*rec));
+  rec->mu = ctx->mu_hist[step - 1];
+  for (int n = 0; n < 4; ++n) {
+    rec->dims[n] = ctx->dims_hist[step - 1][n];
+    rec->primed[n] = d.primed[n];
+    rec->degenerate[n] = d.degen[n];
+    rec->eps[n][0] = d.eps[n][0];
+    rec->eps[n][1] = d.eps[n][1];
+  }
+  rec->ln_c = d.ln_c;
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_state(const hotrg_ctx* ctx, int* steps_done, int dims[4]) {
+  if (!ctx) return HOTRG_EINVAL;
+  if (steps_done) *steps_done = ctx->k;
+  if (dims)
+    for (int n = 0; n < 4; ++n) dims[n] = ctx->dims[n];
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_copy_tensor(hotrg_ctx* ctx, int which, int b, double* host, size_t n) {
+  hotrg_status r = check_ready(ctx);
+  if (r != HOTRG_OK) return r;
+  if (!host || b < 0 || b >= ctx->batch || which < 0 || which > 2) return HOTRG_EINVAL;
+  if (which >= ntensors(ctx->impure_active)) return HOTRG_ESTATE;
+  if (which == 2 && ctx->k < 1) return HOTRG_ESTATE;
+  const int64_t E = tensor_elems(ctx->dims);
+  if ((int64_t)n < E) return HOTRG_EINVAL;
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  if (ctx->prec == HOTRG_FP64) {
+    CK(cudaMemcpy(host, tensor_ptr<double>(ctx, which, ctx->cur, b), E * 8, cudaMemcpyDeviceToHost), "copy");
+  } else {
+    std::vector<float> tmp(E);
+    CK(cudaMemcpy(tmp.data(), tensor_ptr<float>(ctx, which, ctx->cur, b), E * 4, cudaMemcpyDeviceToHost), "copy");
+    for (int64_t i = 0; i < E; ++i) host[i] = tmp[i];
+  }
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_copy_isometry(hotrg_ctx* ctx, int b, int nu, double* host, size_t n) {
+  hotrg_status r = check_ready(ctx);
+  if (r != HOTRG_OK) return r;
+  if (!host || b < 0 || b >= ctx->batch || nu < 0 || nu > 3 || ctx->last_mu < 0 || nu == ctx->last_mu)
+    return HOTRG_EINVAL;
+  const int chi = ctx->last_chi[nu];
+  const int Dold = ctx->last_Dold[nu];
+  const int64_t cnt = (int64_t)Dold * Dold * chi;
+  if ((int64_t)n < cnt) return HOTRG_EINVAL;
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  const double* U64 = (const double*)(ctx->ws + ctx->L.U64) + ((int64_t)b * 4 + nu) * kMaxGramN * kMaxLeg;
+  CK(cudaMemcpy(host, U64, cnt * 8, cudaMemcpyDeviceToHost), "copy U");
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_step_flops(const hotrg_ctx* ctx, int dir, int dcut, double* main_flops, double* total_flops) {
+  if (!ctx || dir < 0 || dir > 3 || dcut < 1) return HOTRG_EINVAL;
+  StepPlan p = make_plan(ctx->dims, dir, dcut);
+  if (main_flops) *main_flops = p.main_flops;
+  if (total_flops) *total_flops = p.total_flops;
+  return HOTRG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,305 @@
+// jacobi.cu - FP64 symmetric eigensolver for the HOSVD Gram matrices (Fig. 1B) and the
+// choice of the truncating isometry.
+//
+// jacobi_kernel: one CTA per matrix. Cyclic two-sided Jacobi in round-robin (tournament)
+// order: each round rotates n/2 disjoint index pairs at once, so every 2x2 block of A is
+// updated by exactly one thread and the rounds need only block barriers. A pair is
+// rotated when |a_pq| > max(1e-18 ||G||_F, 2^-52 sqrt|a_pp a_qq|); a sweep without
+// rotations ends the loop, and kJacobiMaxSweeps sweeps raise the no-convergence status
+// (results are still written). Then: eigenvalues sorted descending, the discarded sum
+// eps = sum_{j >= chi} lambda_j, and the first chi eigenvectors in the canonical gauge:
+// eigenvalues closer than cluster_tau * lambda_0 form a cluster (cluster_tau is set
+// above the rounding noise of the Gram matrix: 1e-10 when the tensors are FP64, 1e-6
+// when they are stored in FP32); inside a cluster the
+// basis is built by repeatedly taking the unit vector e_i with the longest projection on
+// the not-yet-covered part of the cluster's eigenspace (lowest i within a relative 1e-8
+// of the longest) and normalising that projection. This gauge depends only on the
+// eigenspaces, so it does not depend on the eigensolver.
+//
+// select_kernel: per transverse direction, the side (nu or nu') with the smaller
+// discarded sum (a difference within side_rel (eps + eps') + 1e-13 lambda_0 is a tie and
+// goes to nu; side_rel = 1e-9 for FP64 tensors, 1e-6 for FP32 ones), then modified Gram-Schmidt in FP64 on the kept vectors, and copies of U in
+// FP64 and in the storage precision.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace hotrg {
+
+constexpr double kTieRel = 1e-8;
+constexpr int kJT = 256;            // threads per Jacobi CTA
+constexpr int kSmemJacobiN = 96;    // A and V in shared memory up to this n
+
+__device__ __forceinline__ void rr_pair(int r, int i, int m, int& p, int& q) {
+  if (i == 0) {
+    p = r;
+    q = m - 1;
+  } else {
+    p = (r + i) % (m - 1);
+    q = (r - i + (m - 1)) % (m - 1);
+  }
+  if (p > q) {
+    const int t = p;
+    p = q;
+    q = t;
+  }
+}
+
+__device__ double block_sum(double v, double* red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+__global__ void __launch_bounds__(kJT) jacobi_kernel(const __grid_constant__ EigPack jobs, int use_smem,
+                                                     double cluster_tau, int* status) {
+  extern __shared__ double dyn[];
+  __shared__ double cs[kMaxGramN / 2 + 1], sn[kMaxGramN / 2 + 1];
+  __shared__ int pp[kMaxGramN / 2 + 1], qq[kMaxGramN / 2 + 1];
+  __shared__ double lam[kMaxGramN], nrm[kMaxGramN];
+  __shared__ int perm[kMaxGramN], cstart[kMaxGramN + 1];
+  __shared__ double red[kJT / 32];
+  __shared__ int rotated, ncl, pivot;
+  __shared__ double pivval;
+
+  const EigJob& jb = jobs.j[blockIdx.x];
+  const int n = jb.n, chi = jb.chi;
+  const int tid = threadIdx.x;
+  double* A = use_smem ? dyn : jb.work;   // use_smem: every job of the launch has n <= kSmemJacobiN
+  double* V = A + (int64_t)n * n;
+
+  double fro = 0;
+  for (int e = tid; e < n * n; e += kJT) {
+    const double g = jb.G[e];
+    A[e] = g;
+    V[e] = (e / n == e % n) ? 1.0 : 0.0;
+    fro += g * g;
+  }
+  fro = sqrt(block_sum(fro, red));
+  const double tol_abs = 1e-18 * fro;
+  const double tol_rel = 2.220446049250313e-16;
+  const int m = (n % 2 == 0) ? n : n + 1;
+  const int half = m / 2;
+
+  int sweep = 0;
+  for (; sweep < kJacobiMaxSweeps && n > 1; ++sweep) {
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < m - 1; ++r) {
+      for (int i = tid; i < half; i += kJT) {
+        int p, q;
+        rr_pair(r, i, m, p, q);
+        double c = 1.0, s = 0.0;
+        if (q < n) {
+          const double apq = A[p * n + q], app = A[p * n + p], aqq = A[q * n + q];
+          if (fabs(apq) > fmax(tol_abs, tol_rel * sqrt(fabs(app * aqq)))) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+            rotated = 1;
+          }
+        }
+        cs[i] = c;
+        sn[i] = s;
+        pp[i] = p;
+        qq[i] = q;
+      }
+      __syncthreads();
+      // A <- J^T A J, one 2x2 block (pair P rows, pair Q columns) per thread iteration
+      for (int e = tid; e < half * half; e += kJT) {
+        const int P = e / half, Q = e % half;
+        const double c1 = cs[P], s1 = sn[P], c2 = cs[Q], s2 = sn[Q];
+        if (s1 == 0.0 && s2 == 0.0) continue;
+        const int p1 = pp[P], q1 = qq[P], p2 = pp[Q], q2 = qq[Q];
+        const bool hq1 = q1 < n, hq2 = q2 < n;
+        const double a = A[p1 * n + p2];
+        const double b = hq2 ? A[p1 * n + q2] : 0.0;
+        const double cc = hq1 ? A[q1 * n + p2] : 0.0;
+        const double d = (hq1 && hq2) ? A[q1 * n + q2] : 0.0;
+        // rows
+        const double ra = c1 * a - s1 * cc, rb = c1 * b - s1 * d;
+        const double rc = s1 * a + c1 * cc, rd = s1 * b + c1 * d;
+        // columns
+        double na = c2 * ra - s2 * rb, nb = s2 * ra + c2 * rb;
+        double nc = c2 * rc - s2 * rd, nd = s2 * rc + c2 * rd;
+        if (P == Q && s1 != 0.0) {
+          nb = 0.0;
+          nc = 0.0;
+        }
+        A[p1 * n + p2] = na;
+        if (hq2) A[p1 * n + q2] = nb;
+        if (hq1) A[q1 * n + p2] = nc;
+        if (hq1 && hq2) A[q1 * n + q2] = nd;
+      }
+      // V <- V J
+      for (int e = tid; e < n * half; e += kJT) {
+        const int row = e / half, Q = e % half;
+        const double s = sn[Q];
+        if (s == 0.0) continue;
+        const double c = cs[Q];
+        const int p = pp[Q], q = qq[Q];
+        const double vp = V[row * n + p], vq = V[row * n + q];
+        V[row * n + p] = c * vp - s * vq;
+        V[row * n + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+    if (rotated == 0) break;
+    __syncthreads();
+  }
+  if (tid == 0 && sweep >= kJacobiMaxSweeps) atomicAdd(&status[kStNoConv], 1);
+
+  // ---- sort descending (rank = number of larger eigenvalues, ties by index)
+  for (int i = tid; i < n; i += kJT) nrm[i] = A[i * n + i];
+  __syncthreads();
+  for (int i = tid; i < n; i += kJT) {
+    const double li = nrm[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const double lj = nrm[j];
+      rank += (lj > li) || (lj == li && j < i);
+    }
+    perm[rank] = i;
+    lam[rank] = li;
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += kJT) jb.lam[i] = lam[i];
+  if (tid == 0) {
+    double e = 0;
+    for (int j = chi; j < n; ++j) e += lam[j];
+    *jb.eps = e;
+    int nc = 0;
+    cstart[nc++] = 0;
+    for (int j = 1; j < n; ++j)
+      if (lam[j - 1] - lam[j] > cluster_tau * fabs(lam[0])) cstart[nc++] = j;
+    cstart[nc] = n;
+    ncl = nc;
+    int deg = 0;
+    for (int c = 0; c < nc; ++c)
+      if (cstart[c] < chi && chi < cstart[c + 1]) deg = 1;
+    *jb.degenerate = deg;
+  }
+  __syncthreads();
+
+  // ---- canonical gauge for the first chi columns, written to U (n x chi)
+  for (int c = 0; c < ncl; ++c) {
+    const int s0 = cstart[c], e0 = cstart[c + 1];
+    if (s0 >= chi) break;
+    for (int i = tid; i < n; i += kJT) {   // |P_cluster e_i|^2
+      double b = 0;
+      for (int j = s0; j < e0; ++j) {
+        const double v = V[i * n + perm[j]];
+        b = fma(v, v, b);
+      }
+      nrm[i] = b;
+    }
+    __syncthreads();
+    const int tend = min(e0, chi);
+    for (int t = s0; t < tend; ++t) {
+      double mx = 0;
+      for (int i = tid; i < n; i += kJT) mx = fmax(mx, nrm[i]);
+      for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
+      if ((tid & 31) == 0) red[tid >> 5] = mx;
+      __syncthreads();
+      if (tid == 0) {
+        double m2 = 0;
+        for (int w = 0; w < kJT / 32; ++w) m2 = fmax(m2, red[w]);
+        int ip = 0;
+        for (int i = 0; i < n; ++i)
+          if (nrm[i] >= (1.0 - kTieRel) * m2) {
+            ip = i;
+            break;
+          }
+        pivot = ip;
+        pivval = nrm[ip];
+      }
+      __syncthreads();
+      const int ip = pivot;
+      const double inv = 1.0 / sqrt(pivval);
+      for (int i = tid; i < n; i += kJT) {
+        double g = 0;
+        for (int j = s0; j < e0; ++j) g = fma(V[i * n + perm[j]], V[ip * n + perm[j]], g);
+        for (int u = s0; u < t; ++u) g -= jb.U[i * chi + u] * jb.U[ip * chi + u];
+        jb.U[i * chi + t] = g * inv;
+      }
+      __threadfence_block();
+      __syncthreads();
+      for (int i = tid; i < n; i += kJT) {
+        const double g = jb.U[i * chi + t];
+        nrm[i] -= g * g;
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_jacobi(const EigPack& jobs, int njobs, int nmax, double cluster_tau, int* status,
+                          cudaStream_t st) {
+  const int smem_n = nmax <= kSmemJacobiN ? nmax : 0;
+  const size_t smem = (size_t)2 * smem_n * smem_n * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         2 * kSmemJacobiN * kSmemJacobiN * (int)sizeof(double));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  jacobi_kernel<<<njobs, kJT, smem, st>>>(jobs, smem_n > 0 ? 1 : 0, cluster_tau, status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- side choice
+template <typename R>
+__global__ void __launch_bounds__(256) select_kernel(const __grid_constant__ SelectPack jobs, double side_rel) {
+  const SelectJob& jb = jobs.j[blockIdx.x];
+  __shared__ double red[8];
+  __shared__ int side;
+  const int n = jb.n, chi = jb.chi, tid = threadIdx.x;
+  if (tid == 0) {
+    const double e0 = *jb.eps[0], e1 = *jb.eps[1];
+    side = (e0 - e1 > side_rel * (fabs(e0) + fabs(e1)) + 1e-13 * fabs(jb.lam0[0])) ? 1 : 0;
+    jb.rec_eps[0] = e0;
+    jb.rec_eps[1] = e1;
+    *jb.rec_primed = side;
+    *jb.rec_degen = *jb.degen[side];
+  }
+  __syncthreads();
+  const double* src = jb.U[side];
+  for (int e = tid; e < n * chi; e += blockDim.x) jb.U64[e] = src[e];
+  __syncthreads();
+  // modified Gram-Schmidt, FP64
+  for (int j = 0; j < chi; ++j) {
+    for (int i = 0; i < j; ++i) {
+      double d = 0;
+      for (int r = tid; r < n; r += blockDim.x) d = fma(jb.U64[r * chi + i], jb.U64[r * chi + j], d);
+      d = block_sum(d, red);
+      for (int r = tid; r < n; r += blockDim.x) jb.U64[r * chi + j] -= d * jb.U64[r * chi + i];
+      __syncthreads();
+    }
+    double q = 0;
+    for (int r = tid; r < n; r += blockDim.x) q = fma(jb.U64[r * chi + j], jb.U64[r * chi + j], q);
+    q = block_sum(q, red);
+    const double inv = 1.0 / sqrt(q);
+    for (int r = tid; r < n; r += blockDim.x) jb.U64[r * chi + j] *= inv;
+    __syncthreads();
+  }
+  R* ur = (R*)jb.Ur;
+  for (int e = tid; e < n * chi; e += blockDim.x) ur[e] = (R)jb.U64[e];
+}
+
+template <typename R>
+cudaError_t launch_select(const SelectPack& jobs, int njobs, double side_rel, cudaStream_t st) {
+  select_kernel<R><<<njobs, 256, 0, st>>>(jobs, side_rel);
+  return cudaGetLastError();
+}
+template cudaError_t launch_select<double>(const SelectPack&, int, double, cudaStream_t);
+template cudaError_t launch_select<float>(const SelectPack&, int, double, cudaStream_t);
+
+}  // namespace hotrg

@@ -1,0 +1,267 @@
+// tensor_ops.cu - memory-bound tensor kernels of the HOTRG step.
+//
+//  * ttm_kernel     : contraction of one or two legs of a tensor with an isometry
+//                     (the half contractions T x U^a x U^b that build the operands of
+//                     the block-spin GEMM, and the closing contractions with U^c,
+//                     Fig. 1C), writing any output leg order, optionally split into
+//                     tf32 hi + lo for the tensor-core path.
+//  * init_kernel    : the 4D Ising site tensors T and S (Fig. 1A) and ln c_0.
+//  * sumsq/normalise: c = ||T'||_F in FP64, ln c / 2^k accumulated (ln Z / V), T' /= c.
+//  * trace_kernel   : Tr T (each leg joined to its primed partner), FP64.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace hotrg {
+
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+template <typename TI, typename TU, typename TO, int MODE>
+__global__ void __launch_bounds__(256) ttm_kernel(const TI* __restrict__ in, const TU* __restrict__ U,
+                                                  TO* __restrict__ out, TO* __restrict__ out_lo,
+                                                  TTMArgs a) {
+  using Acc = typename std::conditional<sizeof(TI) == 8, double, float>::type;
+  const int outer_dims = a.rank - a.rin;
+  for (int64_t row = blockIdx.x; row < a.outer; row += gridDim.x) {
+    int64_t r = row, in0 = 0, u0 = 0, o0 = 0;
+    for (int d = outer_dims - 1; d >= 0; --d) {
+      const int64_t n = a.dims[d];
+      const int64_t i = r % n;
+      r /= n;
+      in0 += i * a.in_st[d];
+      u0 += i * a.u_st[d];
+      o0 += i * a.out_st[d];
+    }
+    for (int64_t e = threadIdx.x; e < a.inner; e += blockDim.x) {
+      uint32_t q = (uint32_t)e;
+      int64_t i1 = in0, u1 = u0, o1 = o0;
+      for (int d = a.rank - 1; d >= outer_dims; --d) {
+        const uint32_t n = (uint32_t)a.dims[d];
+        const uint32_t i = q % n;
+        q /= n;
+        i1 += (int64_t)i * a.in_st[d];
+        u1 += (int64_t)i * a.u_st[d];
+        o1 += (int64_t)i * a.out_st[d];
+      }
+      Acc acc = 0;
+      if (U == nullptr) {
+        acc = (Acc)in[i1];
+      } else {
+        for (int j1 = 0; j1 < a.J1; ++j1) {
+          const int64_t ib = i1 + j1 * a.in_sj1;
+          const int64_t ub = u1 + j1 * a.u_sj1;
+          for (int j2 = 0; j2 < a.J2; ++j2)
+            acc = fma((Acc)U[ub + j2 * a.u_sj2], (Acc)in[ib + j2 * a.in_sj2], acc);
+        }
+      }
+      acc *= (Acc)a.alpha;
+      if (MODE == kTTMSplitTF32) {
+        const float v = (float)acc;
+        const float hi = tf32_round(v);
+        out[o1] = (TO)hi;
+        out_lo[o1] = (TO)tf32_round(v - hi);
+      } else if (MODE == kTTMAccumulate) {
+        out[o1] = (TO)(acc + (Acc)a.beta * (Acc)out[o1]);
+      } else {
+        out[o1] = (TO)acc;
+      }
+    }
+  }
+}
+
+template <typename TI, typename TU, typename TO>
+cudaError_t launch_ttm(const TI* in, const TU* U, TO* out, TO* out_lo, const TTMArgs& a, int mode,
+                       cudaStream_t st) {
+  if (a.outer <= 0 || a.inner <= 0) return cudaSuccess;
+  if (a.inner > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const int64_t blocks = a.outer < 152 * 64 ? a.outer : 152 * 64;
+  const int threads = a.inner >= 256 ? 256 : (int)((a.inner + 31) / 32 * 32);
+  switch (mode) {
+    case kTTMStore:
+      ttm_kernel<TI, TU, TO, kTTMStore><<<(unsigned)blocks, threads, 0, st>>>(in, U, out, out_lo, a);
+      break;
+    case kTTMSplitTF32:
+      ttm_kernel<TI, TU, TO, kTTMSplitTF32><<<(unsigned)blocks, threads, 0, st>>>(in, U, out, out_lo, a);
+      break;
+    default:
+      ttm_kernel<TI, TU, TO, kTTMAccumulate><<<(unsigned)blocks, threads, 0, st>>>(in, U, out, out_lo, a);
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_ttm<double, double, double>(const double*, const double*, double*, double*,
+                                                        const TTMArgs&, int, cudaStream_t);
+template cudaError_t launch_ttm<float, float, float>(const float*, const float*, float*, float*,
+                                                     const TTMArgs&, int, cudaStream_t);
+template cudaError_t launch_ttm<double, double, float>(const double*, const double*, float*, float*,
+                                                       const TTMArgs&, int, cudaStream_t);
+template cudaError_t launch_ttm<float, double, double>(const float*, const double*, double*, double*,
+                                                       const TTMArgs&, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------- site tensors
+// T[i1..i8] = sum_s w_s prod_j W[s][i_j], S = sum_s sigma_s w_s prod_j W[s][i_j];
+// w_s = exp(beta h sigma_s), sigma = (+1, -1), W as in Fig. 1A's tensor network of the
+// Ising model. One block per batch element, 256 threads = 256 entries. Writes the
+// normalised tensors and ln c_0 = ln ||T||_F.
+template <typename R>
+__global__ void __launch_bounds__(256) init_kernel(const double* __restrict__ beta, const double* __restrict__ h,
+                                                   R* T, R* S, int64_t slot, double* lnz_acc) {
+  const int b = blockIdx.x;
+  const double be = beta[b], hb = h[b];
+  const double ch = sqrt(cosh(be)), sh = sqrt(sinh(be));
+  const int i = threadIdx.x;
+  double t = 0, s = 0;
+  for (int sp = 0; sp < 2; ++sp) {
+    const double sig = sp == 0 ? 1.0 : -1.0;
+    const double w = exp(be * hb * sig);
+    double p = 1.0;
+    for (int leg = 0; leg < 8; ++leg) {
+      const int bit = (i >> (7 - leg)) & 1;          // leg 0 is the slowest index
+      p *= bit == 0 ? ch : sig * sh;
+    }
+    t += w * p;
+    s += sig * w * p;
+  }
+  __shared__ double red[256];
+  red[i] = t * t;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if (i < off) red[i] += red[i + off];
+    __syncthreads();
+  }
+  const double c = sqrt(red[0]);
+  T[b * slot + i] = (R)(t / c);
+  if (S != nullptr) S[b * slot + i] = (R)(s / c);
+  if (i == 0) lnz_acc[b] = log(c);
+}
+
+template <typename R>
+cudaError_t launch_init(const double* beta, const double* h, R* T, R* S, int64_t slot, double* lnz_acc,
+                        int batch, cudaStream_t st) {
+  init_kernel<R><<<batch, 256, 0, st>>>(beta, h, T, S, slot, lnz_acc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_init<double>(const double*, const double*, double*, double*, int64_t, double*,
+                                         int, cudaStream_t);
+template cudaError_t launch_init<float>(const double*, const double*, float*, float*, int64_t, double*, int,
+                                        cudaStream_t);
+
+// ---------------------------------------------------------------------------- norm
+// Pass 1: each block writes the FP64 sum of squares of its grid-stride share.
+constexpr int kNormBlocks = kNormPartials;
+
+template <typename R>
+__global__ void __launch_bounds__(256) sumsq_kernel(const R* __restrict__ x, int64_t n, double* partial) {
+  double acc = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)x[i];
+    acc = fma(v, v, acc);
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  __shared__ double w[8];
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int j = 0; j < 8; ++j) s += w[j];
+    partial[blockIdx.x] = s;
+  }
+}
+
+// Pass 2 (one block): c = sqrt(sum), ln Z accumulator += ln(c) / 2^k, record ln c.
+__global__ void norm_finish_kernel(const double* __restrict__ partial, int np, double weight, double* c_out,
+                                   double* lnz_acc, double* ln_c_rec, int* status) {
+  __shared__ double red[256];
+  double s = 0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += partial[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double c = sqrt(red[0]);
+    if (!(c > 0.0) || !isfinite(c)) {
+      atomicAdd(&status[kStNonFinite], 1);
+      *c_out = 1.0;
+      *ln_c_rec = nan("");
+    } else {
+      *c_out = c;
+      *lnz_acc += log(c) * weight;
+      *ln_c_rec = log(c);
+    }
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) scale_kernel(R* __restrict__ x, int64_t n, const double* __restrict__ c) {
+  const R inv = (R)(1.0 / *c);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] *= inv;
+}
+
+template <typename R>
+cudaError_t launch_norm(const R* x, int64_t n, double* partial, double weight, double* c_out, double* lnz_acc,
+                        double* ln_c_rec, int* status, cudaStream_t st) {
+  sumsq_kernel<R><<<kNormBlocks, 256, 0, st>>>(x, n, partial);
+  norm_finish_kernel<<<1, 256, 0, st>>>(partial, kNormBlocks, weight, c_out, lnz_acc, ln_c_rec, status);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t launch_scale(R* x, int64_t n, const double* c, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  scale_kernel<R><<<(unsigned)blocks, 256, 0, st>>>(x, n, c);
+  return cudaGetLastError();
+}
+template cudaError_t launch_norm<double>(const double*, int64_t, double*, double, double*, double*, double*, int*,
+                                         cudaStream_t);
+template cudaError_t launch_norm<float>(const float*, int64_t, double*, double, double*, double*, double*, int*,
+                                        cudaStream_t);
+template cudaError_t launch_scale<double>(double*, int64_t, const double*, cudaStream_t);
+template cudaError_t launch_scale<float>(float*, int64_t, const double*, cudaStream_t);
+
+// ---------------------------------------------------------------------------- trace
+// Tr T = sum_{x,y,z,t} T[x,x,y,y,z,z,t,t] in FP64; one block per batch element.
+template <typename R>
+__global__ void __launch_bounds__(256) trace_kernel(const R* __restrict__ T, int64_t slot, int Dx, int Dy, int Dz,
+                                                    int Dt, double* out) {
+  const R* t = T + blockIdx.x * slot;
+  // strides of the primed legs; the unprimed leg of direction nu has D_nu times that
+  const int64_t szp = (int64_t)Dt * Dt, syp = (int64_t)Dz * Dz * szp, sxp = (int64_t)Dy * Dy * syp;
+  const int64_t n = (int64_t)Dx * Dy * Dz * Dt;
+  double acc = 0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    int64_t r = i;
+    const int64_t it = r % Dt; r /= Dt;
+    const int64_t iz = r % Dz; r /= Dz;
+    const int64_t iy = r % Dy; r /= Dy;
+    const int64_t ix = r;
+    const int64_t off = ix * (Dx + 1) * sxp + iy * (Dy + 1) * syp + iz * (Dz + 1) * szp + it * (Dt + 1);
+    acc += (double)t[off];
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+template <typename R>
+cudaError_t launch_trace(const R* T, int64_t slot, const int* dims, int batch, double* out, cudaStream_t st) {
+  trace_kernel<R><<<batch, 256, 0, st>>>(T, slot, dims[0], dims[1], dims[2], dims[3], out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_trace<double>(const double*, int64_t, const int*, int, double*, cudaStream_t);
+template cudaError_t launch_trace<float>(const float*, int64_t, const int*, int, double*, cudaStream_t);
+
+}  // namespace hotrg

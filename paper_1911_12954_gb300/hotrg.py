@@ -1,0 +1,217 @@
+"""Thin ctypes binding of libhotrg.so (include/hotrg.h).
+
+Argument marshalling only: every step of the HOTRG coarse-graining runs in the
+library's CUDA kernels. PyTorch supplies the device workspace (one uint8 tensor) and
+the stream. There is no CPU path: if the library or a CUDA device is missing, the
+constructor raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FP64, FP32, TF32X3 = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32x3": TF32X3}
+IMPURE_NONE, IMPURE_SIGMA, IMPURE_SIGMASIGMA = 0, 1, 2
+
+STATUS = {0: "ok", -1: "EINVAL", -2: "EWORKSPACE", -3: "ECUDA", -4: "ENOCONV", -5: "ENONFINITE",
+          -6: "ETIMEOUT", -7: "ESTATE", -8: "EUNSUPPORTED"}
+
+
+class HotrgError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = f"{where}: {STATUS.get(status, status)}"
+        if status == -3:
+            msg += " (" + _lib().hotrg_last_error().decode() + ")"
+        super().__init__(msg)
+
+
+class StepRecord(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_int), ("dims", ctypes.c_int * 4), ("primed", ctypes.c_int * 4),
+                ("eps", (ctypes.c_double * 2) * 4), ("ln_c", ctypes.c_double),
+                ("degenerate", ctypes.c_int * 4)]
+
+
+_LIB = None
+SYMBOLS = ["hotrg_create", "hotrg_destroy", "hotrg_workspace_size", "hotrg_set_workspace", "hotrg_set_stream",
+           "hotrg_init_tensor", "hotrg_set_tensor", "hotrg_step", "hotrg_lnZ", "hotrg_impure_magnetization",
+           "hotrg_impure_energy", "hotrg_step_info", "hotrg_state", "hotrg_copy_tensor", "hotrg_copy_isometry",
+           "hotrg_step_flops", "hotrg_status_string", "hotrg_last_error"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _lib():
+    """Load (building first if needed) libhotrg.so and declare its signatures."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.build() if not os.path.exists(_build.LIB) else _build.LIB
+    L = ctypes.CDLL(path)
+    c_int, c_double, c_size_t, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_void_p
+    P = ctypes.POINTER
+    sig = {
+        "hotrg_create": (c_int, [P(c_void_p), c_int, c_int, c_int, c_int]),
+        "hotrg_destroy": (c_int, [c_void_p]),
+        "hotrg_workspace_size": (c_int, [c_void_p, c_int, P(c_int), P(c_int), P(c_int), P(c_size_t)]),
+        "hotrg_set_workspace": (c_int, [c_void_p, c_void_p, c_size_t]),
+        "hotrg_set_stream": (c_int, [c_void_p, c_void_p]),
+        "hotrg_init_tensor": (c_int, [c_void_p, P(c_double), P(c_double)]),
+        "hotrg_set_tensor": (c_int, [c_void_p, c_int, P(c_int), P(c_double)]),
+        "hotrg_step": (c_int, [c_void_p, c_int, c_int]),
+        "hotrg_lnZ": (c_int, [c_void_p, P(c_double)]),
+        "hotrg_impure_magnetization": (c_int, [c_void_p, P(c_double)]),
+        "hotrg_impure_energy": (c_int, [c_void_p, P(c_double), P(c_double)]),
+        "hotrg_step_info": (c_int, [c_void_p, c_int, c_int, P(StepRecord)]),
+        "hotrg_state": (c_int, [c_void_p, P(c_int), P(c_int)]),
+        "hotrg_copy_tensor": (c_int, [c_void_p, c_int, c_int, P(c_double), c_size_t]),
+        "hotrg_copy_isometry": (c_int, [c_void_p, c_int, c_int, P(c_double), c_size_t]),
+        "hotrg_step_flops": (c_int, [c_void_p, c_int, c_int, P(c_double), P(c_double)]),
+        "hotrg_status_string": (ctypes.c_char_p, [c_int]),
+        "hotrg_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = L
+    return L
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _iptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _check(st, where):
+    if st != 0:
+        raise HotrgError(st, where)
+
+
+class HOTRG:
+    """A batch of HOTRG runs of the 4D Ising model on one CUDA device.
+
+    Parameters
+    ----------
+    batch : number of independent runs (temperatures).
+    dcut_max : largest bond dimension (2..16).
+    precision : "fp64", "fp32" or "tf32x3".
+    impure : 0, IMPURE_SIGMA or IMPURE_SIGMA | IMPURE_SIGMASIGMA.
+    schedule : list of (dir, dcut) used to size the workspace (None: steady state at
+        dcut_max), dims0 : starting bond dimensions for set_tensor runs.
+    workspace_bytes : override of the workspace size (smaller makes steps slice).
+    """
+
+    def __init__(self, batch=1, dcut_max=4, precision="fp64", impure=0, schedule=None, dims0=None,
+                 workspace_bytes=None, device=None, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libhotrg needs a CUDA device; there is no CPU path")
+        self.torch = torch
+        self.lib = _lib()
+        self.device = torch.device(device or "cuda")
+        self.batch = batch
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else precision
+        self.impure = impure
+        ctx = ctypes.c_void_p()
+        _check(self.lib.hotrg_create(ctypes.byref(ctx), batch, dcut_max, self.precision, impure), "create")
+        self.ctx = ctx
+        nbytes = self.workspace_size(schedule, dims0)
+        if workspace_bytes is not None:
+            nbytes = int(workspace_bytes)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        _check(self.lib.hotrg_set_workspace(self.ctx, ctypes.c_void_p(self.workspace.data_ptr()), nbytes),
+               "set_workspace")
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        _check(self.lib.hotrg_set_stream(self.ctx, ctypes.c_void_p(self.stream.cuda_stream)), "set_stream")
+
+    def workspace_size(self, schedule=None, dims0=None) -> int:
+        n = 0 if schedule is None else len(schedule)
+        dirs = np.array([s[0] for s in schedule] if n else [0], dtype=np.int32)
+        dcuts = np.array([s[1] for s in schedule] if n else [0], dtype=np.int32)
+        d0 = None if dims0 is None else np.array(dims0, dtype=np.int32)
+        out = ctypes.c_size_t()
+        _check(self.lib.hotrg_workspace_size(self.ctx, n, _iptr(dirs), _iptr(dcuts),
+                                             None if d0 is None else _iptr(d0), ctypes.byref(out)),
+               "workspace_size")
+        return out.value
+
+    def __del__(self):
+        try:
+            if getattr(self, "ctx", None):
+                self.lib.hotrg_destroy(self.ctx)
+                self.ctx = None
+        except Exception:
+            pass
+
+    # -------------------------------------------------------------- calls
+    def init_tensor(self, beta, h):
+        b = np.ascontiguousarray(np.broadcast_to(np.asarray(beta, dtype=np.float64), (self.batch,)))
+        hh = np.ascontiguousarray(np.broadcast_to(np.asarray(h, dtype=np.float64), (self.batch,)))
+        _check(self.lib.hotrg_init_tensor(self.ctx, _dptr(b), _dptr(hh)), "init_tensor")
+
+    def set_tensor(self, T: np.ndarray, b: int = 0):
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        dims = np.array([T.shape[2 * n] for n in range(4)], dtype=np.int32)
+        _check(self.lib.hotrg_set_tensor(self.ctx, b, _iptr(dims), _dptr(T)), "set_tensor")
+
+    def step(self, direction: int, dcut: int):
+        _check(self.lib.hotrg_step(self.ctx, direction, dcut), "step")
+
+    def lnZ(self) -> np.ndarray:
+        out = np.zeros(self.batch)
+        _check(self.lib.hotrg_lnZ(self.ctx, _dptr(out)), "lnZ")
+        return out
+
+    def magnetization(self) -> np.ndarray:
+        out = np.zeros(self.batch)
+        _check(self.lib.hotrg_impure_magnetization(self.ctx, _dptr(out)), "magnetization")
+        return out
+
+    def energy(self):
+        e = np.zeros(self.batch)
+        ss = np.zeros(self.batch)
+        _check(self.lib.hotrg_impure_energy(self.ctx, _dptr(e), _dptr(ss)), "energy")
+        return e, ss
+
+    def state(self):
+        k = ctypes.c_int()
+        dims = np.zeros(4, dtype=np.int32)
+        _check(self.lib.hotrg_state(self.ctx, ctypes.byref(k), _iptr(dims)), "state")
+        return k.value, tuple(int(x) for x in dims)
+
+    def step_info(self, step: int, b: int = 0) -> dict:
+        r = StepRecord()
+        _check(self.lib.hotrg_step_info(self.ctx, b, step, ctypes.byref(r)), "step_info")
+        return dict(mu=r.mu, dims=tuple(r.dims), primed=tuple(r.primed),
+                    eps=tuple(tuple(r.eps[n]) for n in range(4)), ln_c=r.ln_c,
+                    degenerate=tuple(r.degenerate))
+
+    def tensor(self, which: int = 0, b: int = 0) -> np.ndarray:
+        _, dims = self.state()
+        shape = tuple(x for D in dims for x in (D, D))
+        out = np.zeros(int(np.prod(shape)))
+        _check(self.lib.hotrg_copy_tensor(self.ctx, which, b, _dptr(out), out.size), "copy_tensor")
+        return out.reshape(shape)
+
+    def isometry(self, nu: int, b: int = 0, dold: int = None, chi: int = None) -> np.ndarray:
+        out = np.zeros(16 * 16 * 16)
+        _check(self.lib.hotrg_copy_isometry(self.ctx, b, nu, _dptr(out), out.size), "copy_isometry")
+        return out[: dold * dold * chi].reshape(dold, dold, chi)
+
+    def step_flops(self, direction: int, dcut: int):
+        m, t = ctypes.c_double(), ctypes.c_double()
+        _check(self.lib.hotrg_step_flops(self.ctx, direction, dcut, ctypes.byref(m), ctypes.byref(t)), "step_flops")
+        return m.value, t.value

@@ -1,0 +1,211 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+FP64 mode must agree with the oracle to rounding (1e-10 relative on ln Z / V, the bar
+for the FP64 path); FP32 and TF32x3 modes within the error their arithmetic allows,
+stated per test. Inputs are the Ising site tensors (any T, h) and seeded random
+tensors from ``workloads`` with non-uniform and odd bond dimensions; single steps are
+compared element by element (tensors and isometries in the canonical gauge), runs on
+gauge-invariant quantities (ln Z / V, <sigma>, <sigma sigma>, discarded sums).
+"""
+
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import hotrg as H
+from workloads import random_tensor
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _gpu(**kw):
+    from paper_1911_12954_gb300 import HOTRG
+    return HOTRG(**kw)
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name + ".json")) as f:
+        return json.load(f)
+
+
+# ------------------------------------------------------------------ site tensor, k = 0
+def test_init_tensor_lnz_and_magnetization():
+    betas = np.array([0.0, 0.1, 1 / 6.65, 0.7])
+    hs = np.array([0.0, 0.3, 1e-5, -0.2])
+    g = _gpu(batch=4, dcut_max=4, precision="fp64", impure=3, schedule=[(0, 4)])
+    g.init_tensor(betas, hs)
+    lnz = g.lnZ()
+    m = g.magnetization()
+    for i in range(4):
+        st = H.HOTRG.start(4, betas[i], hs[i], impure=True)
+        assert lnz[i] == pytest.approx(st.lnZ(), abs=1e-14)
+        assert m[i] == pytest.approx(st.magnetization(), abs=1e-14)
+        assert g.tensor(0, i) == pytest.approx(st.T, abs=1e-15)
+
+
+# ------------------------------------------------------------------ single steps on random tensors
+CASES = [
+    # dims (Dx, Dy, Dz, Dt), mu, dcut
+    ((2, 3, 2, 3), 1, 5),
+    ((3, 2, 2, 2), 0, 4),
+    ((2, 2, 3, 2), 3, 9),       # no truncation: chi = D^2 everywhere
+    ((4, 3, 2, 3), 2, 7),
+    ((3, 3, 3, 3), 3, 1),       # chi = 1
+    ((2, 4, 3, 2), 1, 6),
+]
+
+
+@pytest.mark.parametrize("dims,mu,dcut", CASES)
+def test_single_step_random_tensor_fp64(dims, mu, dcut):
+    T = random_tensor(1000 + sum(dims) * 7 + mu, dims)
+    ref = H.HOTRG.from_tensor(T)
+    trans = [n for n in range(4) if n != mu]
+    isos = {n: H.isometry(ref.T, ref.T, mu, n, dcut) for n in trans}
+    ref.step(mu, dcut)
+    g = _gpu(batch=1, dcut_max=max(max(dims), dcut, 2), precision="fp64", schedule=[(mu, dcut)], dims0=dims)
+    g.set_tensor(T)
+    g.step(mu, dcut)
+    k, newdims = g.state()
+    assert k == 1 and newdims == ref.history[0].dims_out
+    Tg = g.tensor()
+    scale = np.abs(ref.T).max()
+    assert np.allclose(Tg, ref.T, rtol=0, atol=1e-12 * scale)
+    info = g.step_info(1)
+    assert info["ln_c"] == pytest.approx(ref.history[0].ln_c, abs=1e-12)
+    for n in trans:
+        Ug = g.isometry(n, dold=dims[n], chi=isos[n].chi)
+        assert np.allclose(Ug, isos[n].U, atol=1e-11), n
+        assert info["primed"][n] == int(isos[n].primed)
+        assert info["eps"][n] == pytest.approx(isos[n].eps, rel=1e-9, abs=1e-13)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 3e-5), ("tf32x3", 3e-5)])
+@pytest.mark.parametrize("dims,mu,dcut", [CASES[0], CASES[3], CASES[5]])
+def test_single_step_random_tensor_mixed(prec, tol, dims, mu, dcut):
+    T = random_tensor(2000 + sum(dims) * 7 + mu, dims)
+    ref = H.HOTRG.from_tensor(T)
+    ref.step(mu, dcut)
+    g = _gpu(batch=1, dcut_max=max(max(dims), dcut, 2), precision=prec, schedule=[(mu, dcut)], dims0=dims)
+    g.set_tensor(T)
+    g.step(mu, dcut)
+    Tg = g.tensor()
+    scale = np.abs(ref.T).max()
+    err = np.abs(Tg - ref.T).max() / scale
+    assert err < tol, err
+    assert g.step_info(1)["ln_c"] == pytest.approx(ref.history[0].ln_c, abs=tol)
+
+
+def test_sliced_contraction_matches_unsliced():
+    """A workspace too small for the unsliced contraction makes the step slice the new
+    a-leg; the result is the same to rounding."""
+    dims, mu, dcut = (3, 3, 3, 3), 0, 6
+    T = random_tensor(77, dims)
+    full = _gpu(batch=1, dcut_max=6, precision="fp64", schedule=[(mu, dcut)], dims0=dims)
+    full.set_tensor(T)
+    full.step(mu, dcut)
+    need = full.workspace_size([(mu, dcut)], dims)
+    small = _gpu(batch=1, dcut_max=6, precision="fp64", schedule=[(mu, dcut)], dims0=dims,
+                 workspace_bytes=int(need * 0.55))
+    small.set_tensor(T)
+    small.step(mu, dcut)
+    assert np.allclose(small.tensor(), full.tensor(), atol=1e-14)
+
+
+# ------------------------------------------------------------------ Ising runs
+def test_untruncated_two_steps_impure_vs_oracle():
+    """Two untruncated steps (dims 4,4,16,16) = the exactly enumerable 2x2x1x1 lattice."""
+    betas, hs = [1 / 6.65, 0.6], [0.1, 0.03]
+    g = _gpu(batch=2, dcut_max=16, precision="fp64", impure=3, schedule=[(0, 16), (1, 16)])
+    g.init_tensor(betas, hs)
+    g.step(0, 16)
+    g.step(1, 16)
+    lnz, m = g.lnZ(), g.magnetization()
+    e, ss = g.energy()
+    for i in range(2):
+        st = H.run(4, betas[i], hs[i], 10 ** 6, 2, impure=True)
+        assert lnz[i] == pytest.approx(st.lnZ(), abs=1e-12)
+        assert m[i] == pytest.approx(st.magnetization(), abs=1e-12)
+        assert ss[i] == pytest.approx(st.sigma_sigma(), abs=1e-12)
+        assert e[i] == pytest.approx(-4 * st.sigma_sigma() - hs[i] * st.magnetization(), abs=1e-12)
+
+
+@pytest.mark.parametrize("name", ["ising4d_T6.65_h0_dcut4_16steps", "ising4d_T6.65_h0_dcut5_8steps"])
+def test_fp64_run_vs_golden(name):
+    gd = _golden(name)
+    cfg = gd["config"]
+    sched = [(s["mu"], cfg["dcut"]) for s in gd["steps"]]
+    g = _gpu(batch=1, dcut_max=cfg["dcut"], precision="fp64", schedule=sched)
+    g.init_tensor(gd["beta"], cfg["h"])
+    for i, (mu, dc) in enumerate(sched):
+        g.step(mu, dc)
+        ref = gd["steps"][i]
+        got = g.lnZ()[0]
+        assert got == pytest.approx(ref["lnZ"], rel=1e-10), (i + 1, got, ref["lnZ"])
+        info = g.step_info(i + 1)
+        assert list(info["dims"]) == ref["dims"]
+        for n, (e0, e1) in ref["eps"].items():
+            assert info["eps"][int(n)] == pytest.approx((e0, e1), rel=1e-7, abs=1e-12)
+
+
+def test_fp64_impure_run_vs_golden():
+    gd = _golden("ising4d_T6.65_h1e-5_dcut4_impure_12steps")
+    cfg = gd["config"]
+    sched = [(s["mu"], cfg["dcut"]) for s in gd["steps"]]
+    g = _gpu(batch=1, dcut_max=cfg["dcut"], precision="fp64", impure=3, schedule=sched)
+    g.init_tensor(gd["beta"], cfg["h"])
+    for i, (mu, dc) in enumerate(sched):
+        g.step(mu, dc)
+        ref = gd["steps"][i]
+        assert g.lnZ()[0] == pytest.approx(ref["lnZ"], rel=1e-10)
+        assert g.magnetization()[0] == pytest.approx(ref["m"], rel=1e-8, abs=1e-12)
+        e, ss = g.energy()
+        assert ss[0] == pytest.approx(ref["sigma_sigma"], rel=1e-9)
+        assert e[0] == pytest.approx(ref["energy"], rel=1e-9)
+
+
+def test_batch_of_temperatures_matches_single_runs():
+    temps = [6.60, 6.65, 6.72]
+    g = _gpu(batch=3, dcut_max=4, precision="fp64", schedule=[(i % 4, 4) for i in range(6)])
+    g.init_tensor([1 / T for T in temps], 0.0)
+    for i in range(6):
+        g.step(i % 4, 4)
+    lnz = g.lnZ()
+    for j, T in enumerate(temps):
+        assert lnz[j] == pytest.approx(H.run(4, 1 / T, 0.0, 4, 6).lnZ(), rel=1e-10)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("tf32x3", 2e-6)])
+def test_mixed_run_vs_golden(prec, tol):
+    """|Delta ln Z/V| of the FP32-storage modes against the FP64 oracle, D_cut = 4, 16^4."""
+    gd = _golden("ising4d_T6.65_h0_dcut4_16steps")
+    cfg = gd["config"]
+    sched = [(s["mu"], cfg["dcut"]) for s in gd["steps"]]
+    g = _gpu(batch=1, dcut_max=cfg["dcut"], precision=prec, schedule=sched)
+    g.init_tensor(gd["beta"], cfg["h"])
+    worst = 0.0
+    for i, (mu, dc) in enumerate(sched):
+        g.step(mu, dc)
+        worst = max(worst, abs(g.lnZ()[0] - gd["steps"][i]["lnZ"]))
+    assert worst < tol, worst
+
+
+# ------------------------------------------------------------------ error handling
+def test_errors_are_reported_not_raised_on_device():
+    from paper_1911_12954_gb300 import HotrgError
+    g = _gpu(batch=1, dcut_max=4, precision="fp64", schedule=[(0, 4)])
+    with pytest.raises(HotrgError, match="ESTATE"):
+        g.step(0, 4)                      # before init
+    g.init_tensor(0.2, 0.0)
+    with pytest.raises(HotrgError, match="EINVAL"):
+        g.step(4, 4)                      # bad direction
+    with pytest.raises(HotrgError, match="EINVAL"):
+        g.step(0, 5)                      # dcut > dcut_max
+    with pytest.raises(HotrgError, match="EINVAL"):
+        g.init_tensor(-1.0, 0.0)          # beta < 0
+    g.step(0, 4)
+    assert math.isfinite(g.lnZ()[0])
