@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Throughput of the 4D Ising HOTRG coarse-graining step on GB300.
+
+Workload (synthetic, deterministic): the 4D Ising site tensor at T = 6.65, h = 0,
+D_cut = 8, directions cycled x, y, z, t towards the 1024^4 lattice (40 steps). A
+benchmark "step" is one HOTRG coarse-graining step: Gram matrices on both sides of the
+three transverse bond pairs, FP64 Jacobi eigensolves and isometries, the block-spin
+contraction (2 D^15 flops, tcgen05 TF32x3), normalisation and ln Z accumulation. The
+W warm-up steps are steps 1..W of the run (bond dimensions reach 8 at step 3), the K
+timed steps are the steady-state steps W+1..W+K.
+
+Printed (rank 0, one JSON line): algorithmic TFLOP/s of the timed steps (value), the
+block-spin GEMM against its tensor-core roofline, the FP64 GPU path on one
+steady-state step, |Delta ln Z/V| of the mixed path against FP64, the FP64 NumPy oracle
+timed on a bounded sample (cpu_baseline), and an end-to-end figure for the whole
+40-step job through the public API with host inputs and outputs.
+
+--impl reference times the FP64 NumPy oracle itself (the reference arm) on the host.
+Multi-GPU: replicas only (each rank runs its own temperature); value = all ranks' flops
+/ the slowest rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "4D HOTRG step TFLOP/s (% peak), mixed vs FP64, D_cut 8–13, |Δ lnZ/V|≤1e-6"
+T_WORK = 6.65
+H_WORK = 0.0
+LATTICE_STEPS = 40
+GOLDEN_D8 = os.path.join(ROOT, "tests", "golden", "ising4d_T6.65_h0_dcut8_8steps.json")
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=8)
+    p.add_argument("--warmup", type=int, default=4)
+    p.add_argument("--dcut", type=int, default=8)
+    p.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    p.add_argument("--fp64", type=int, default=1, help="time one FP64 GPU step for the mixed-vs-FP64 ratio")
+    p.add_argument("--e2e", type=int, default=1, help="time the whole 40-step job through the public API")
+    p.add_argument("--cpu", type=int, default=1, help="time the FP64 oracle on a bounded sample (rank 0, N=1)")
+    return p.parse_args()
+
+
+# --------------------------------------------------------------------------- helpers
+def tf32_peak():
+    """Dense TF32 tensor peak: the measured BF16 burst peak x the nominal TF32/BF16 ratio
+    (1.1 / 2.25 PFLOP/s); the profiling recipe's fallback when no measurement exists."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            mp = json.load(f)
+        return mp["bf16_tflops"] * 1.1 / 2.25, "measured bf16 x nominal tf32/bf16 (1.1/2.25)"
+    except Exception:
+        return 1900.0 * 1.1 / 2.25, "fallback bf16 1.9 PF x nominal tf32/bf16 (1.1/2.25)"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.tmp.flush()
+
+    def summary(self):
+        try:
+            with open(self.tmp.name) as f:
+                rows = [r.strip().split(", ") for r in f if r.strip()]
+            os.unlink(self.tmp.name)
+        except Exception:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- CPU oracle sample
+def oracle_sample(dcut: int, seed: int = 8):
+    """One steady-state step of the FP64 oracle on a seeded tensor of the steady-state
+    shape: the HOSVD of all three transverse directions (both sides) and the block-spin
+    contraction restricted to the new x legs X = X' = 0 (isometry U^x cut to its first
+    column), i.e. 1/D_cut^2 of the D^15 product. Returns (flops, seconds)."""
+    import numpy as np
+
+    from oracle import hotrg as H
+    from workloads import random_tensor
+
+    D = dcut
+    mu = 0
+    T = random_tensor(seed, (D, D, D, D))
+    T = T / np.linalg.norm(T)
+    t0 = time.perf_counter()
+    isos = {n: H.isometry(T, T, mu, n, dcut) for n in (1, 2, 3)}
+    U = {n: isos[n].U for n in (1, 2, 3)}
+    U[1] = U[1][:, :, :1].copy()
+    H.coarse_grain(T, T, U, mu)
+    dt = time.perf_counter() - t0
+    # flops of what ran (2 per multiply-add): 12 half-Grams + the restricted contraction
+    E = float(D) ** 8
+    R = D * D
+    gram = 3 * 4 * 2.0 * R * E
+    rows = 1 * D * D * D * D          # X (1) * Y (chi) * c1 c1' (D^2) * mu1 (D)
+    K = float(D) ** 5
+    main = 2.0 * rows * rows * K
+    builds = 2 * (2.0 * D * 1 * E) + 2 * (2.0 * D * rows * K)     # T x U^x (1 col), x U^y, both sides
+    close = 2.0 * D * rows * rows + 2.0 * D * D * rows * rows / (D * D) * D
+    return gram + main + builds + close, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    cores = os.cpu_count()
+    for _ in range(args.warmup):
+        oracle_sample(args.dcut)
+    fl, secs = 0.0, 0.0
+    for i in range(args.steps):
+        f, s = oracle_sample(args.dcut, seed=100 + i)
+        fl += f
+        secs += s
+    value = fl / secs / 1e12
+    sample = (f"per step: one steady-state D_cut={args.dcut} HOTRG step of the FP64 NumPy oracle on a seeded "
+              f"N(0,1) tensor of shape ({args.dcut},)*8: full HOSVD of the 3 transverse directions + the "
+              f"block-spin contraction restricted to X = X' = 0 (1/{args.dcut ** 2} of the D^15 product)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"4D Ising HOTRG step, D_cut={args.dcut}, steady state (1024^4 schedule)",
+                       "dcut": args.dcut, "sample": "bounded oracle sample, see cpu_baseline"},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    from paper_1911_12954_gb300 import HOTRG
+
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def allmax(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def allsum(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    D = args.dcut
+    temp = T_WORK + 0.001 * rank           # replicas: one temperature per rank
+    beta = 1.0 / temp
+    nsteps = args.warmup + args.steps
+    sched = [(i % 4, D) for i in range(max(nsteps, 8))]
+
+    # ---------------------------------------------------------------- mixed precision, timed
+    run = HOTRG(batch=1, dcut_max=D, precision="tf32x3", schedule=sched)
+    run.init_tensor(beta, H_WORK)
+    for i in range(args.warmup):
+        run.step(*sched[i])
+    barrier()
+    flops = 0.0
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        run.profile(True)
+        start.record(run.stream)
+        for i in range(args.warmup, nsteps):
+            flops += run.step_flops(*sched[i])[1]
+            run.step(*sched[i])
+        stop.record(run.stream)
+        barrier()
+    prof = run.profile_read()
+    run.profile(False)
+    ms = start.elapsed_time(stop)
+    ms_max = allmax(ms)
+    flops_all = allsum(flops)
+    value = flops_all / (ms_max * 1e-3) / 1e12
+    lnz_run = float(run.lnZ()[0])
+    del run
+    torch.cuda.empty_cache()
+
+    # ---------------------------------------------------------------- accuracy vs FP64 oracle
+    accuracy = {}
+    ver = HOTRG(batch=1, dcut_max=D, precision="tf32x3", schedule=sched[:8])
+    ver.init_tensor(beta, H_WORK)
+    mixed_lnz = []
+    for i in range(8):
+        ver.step(*sched[i])
+        mixed_lnz.append(float(ver.lnZ()[0]))
+    del ver
+    torch.cuda.empty_cache()
+    if rank == 0 and D == 8 and os.path.exists(GOLDEN_D8):
+        with open(GOLDEN_D8) as f:
+            gd = json.load(f)
+        diffs = [abs(mixed_lnz[i] - s["lnZ"]) for i, s in enumerate(gd["steps"][:8])]
+        accuracy["max_abs_dlnZ_vs_fp64_oracle_steps1to8"] = max(diffs)
+        accuracy["dlnZ_per_step"] = diffs
+
+    # ---------------------------------------------------------------- FP64 GPU path, one step
+    fp64 = None
+    if args.fp64:
+        r64 = HOTRG(batch=1, dcut_max=D, precision="fp64", schedule=sched[:4])
+        r64.init_tensor(beta, H_WORK)
+        for i in range(3):
+            r64.step(*sched[i])
+        barrier()
+        f64 = r64.step_flops(*sched[3])[1]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(r64.stream)
+        r64.step(*sched[3])
+        e1.record(r64.stream)
+        barrier()
+        ms64 = allmax(e0.elapsed_time(e1))
+        lnz64 = float(r64.lnZ()[0])
+        fp64 = {"value": allsum(f64) / (ms64 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms64,
+                "steps": 1, "warmup": 3, "timed_step": 4,
+                "speedup_mixed_vs_fp64": ms64 / (ms_max / args.steps)}
+        accuracy["abs_dlnZ_mixed_vs_fp64_gpu_step4"] = abs(mixed_lnz[3] - lnz64)
+        del r64
+        torch.cuda.empty_cache()
+
+    # ---------------------------------------------------------------- end to end, public API
+    e2e = None
+    if args.e2e:
+        full = [(i % 4, D) for i in range(LATTICE_STEPS)]
+        job = HOTRG(batch=1, dcut_max=D, precision="tf32x3", schedule=full)
+        bh = torch.tensor([beta], dtype=torch.float64).pin_memory()
+        hh = torch.tensor([H_WORK], dtype=torch.float64).pin_memory()
+        job.init_tensor(bh.numpy(), hh.numpy())           # warm the job once
+        job.step(*full[0])
+        job.lnZ()
+        barrier()
+        t0 = time.perf_counter()
+        job.init_tensor(bh.numpy(), hh.numpy())
+        fl = 0.0
+        for s in full:
+            fl += job.step_flops(*s)[1]
+            job.step(*s)
+        lnz40 = float(job.lnZ()[0])
+        t1 = time.perf_counter()
+        barrier()
+        secs = allmax(t1 - t0)
+        e2e = {"value": allsum(fl) / secs / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 16,
+               "d2h_bytes_per_step": 32, "step": f"whole {LATTICE_STEPS}-step job (1024^4 sites): init from host "
+               "beta, h (pinned) -> 40 steps -> ln Z/V read back", "seconds": secs, "lnZ_over_V": lnz40}
+        del job
+        torch.cuda.empty_cache()
+
+    # ---------------------------------------------------------------- CPU oracle baseline
+    cpu = None
+    if args.cpu and rank == 0 and world == 1:
+        f, s = oracle_sample(D)
+        cpu = {"value": f / s / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"one steady-state D_cut={D} step of the FP64 NumPy oracle on a seeded N(0,1) tensor of "
+                         f"shape ({D},)*8: full HOSVD + the block-spin contraction restricted to X = X' = 0 "
+                         f"(1/{D * D} of the D^15 product); {s:.1f} s"}
+
+    peak, peak_src = tf32_peak()
+    achieved = prof["gemm_flops"] / (prof["gemm_ms"] * 1e-3) / 1e12 if prof["gemm_ms"] > 0 else None
+    traffic = None
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "tf32x3", "data": "synthetic",
+        "config": {"workload": f"4D Ising HOTRG, T={T_WORK}, h={H_WORK}, D_cut={D}, 1024^4 lattice schedule "
+                               f"(x,y,z,t cycled); timed steps {args.warmup + 1}..{nsteps} (steady state)",
+                   "dcut": D, "temperatures_per_gpu": 1, "lattice": "1024^4", "precision": "tf32x3 (fp32 storage)",
+                   "l2": "operands larger than L2 (GEMM A and B: 2 x 4.3 GB per step, hi + lo)"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "kernel": "gemm_tf32x3_kernel (block-spin contraction, 2 M N K algorithmic flops per launch)",
+                     "peak_source": peak_src, "launches": prof["gemm_launches"],
+                     "avg_launch_ms": prof["gemm_ms"] / max(1, prof["gemm_launches"]),
+                     "tensor_pipe_flops_frac": (3 * achieved / peak) if achieved else None},
+        "gpu_launches": prof["launches"],
+        "clocks": clk.summary(),
+        "fp64": fp64, "accuracy": accuracy, "lnZ_over_V_after_timed_steps": lnz_run,
+        "cpu_baseline": cpu, "e2e": e2e,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

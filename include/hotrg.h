@@ -159,6 +159,21 @@ hotrg_status hotrg_copy_isometry(hotrg_ctx* ctx, int b, int nu, double* host, si
 hotrg_status hotrg_step_flops(const hotrg_ctx* ctx, int dir, int dcut, double* main_flops,
                               double* total_flops);
 
+/* Launch accounting of one context, for benchmarks. */
+typedef struct {
+  uint64_t launches;      /* CUDA kernels this context launched since the last reset         */
+  uint64_t gemm_launches; /* launches of the block-spin GEMM (the O(D^15) product)            */
+  double gemm_ms;         /* their summed device time, CUDA events on the context's stream   */
+  double gemm_flops;      /* their summed algorithmic flops, 2 M N K each                    */
+} hotrg_profile;
+
+/* enable != 0: from now on record a CUDA event pair around every GEMM launch (host-side
+ * events, no device memory); any call resets the counters. */
+hotrg_status hotrg_profile_enable(hotrg_ctx* ctx, int enable);
+
+/* Counters since the last hotrg_profile_enable. Synchronises the stream. */
+hotrg_status hotrg_profile_read(hotrg_ctx* ctx, hotrg_profile* out);
+
 /* Text of a status code, and the last CUDA error message seen by this thread. */
 const char* hotrg_status_string(int status);
 const char* hotrg_last_error(void);

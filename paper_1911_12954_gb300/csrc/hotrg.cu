@@ -86,6 +86,16 @@ struct hotrg_ctx {
   int last_Dold[4] = {0, 0, 0, 0};
   int last_mu = -1;
   std::vector<double> h_host;
+  // launch accounting
+  uint64_t launches = 0;
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;   // pairs (start, stop) of timed GEMM launches
+  size_t ev_used = 0;
+  uint64_t gemm_launches = 0;
+  double gemm_flops = 0;
+  ~hotrg_ctx() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
 };
 
 namespace {
@@ -100,6 +110,17 @@ hotrg_status cuda_fail(hotrg_ctx* ctx, cudaError_t e, const char* where) {
   do {                                                    \
     cudaError_t e__ = (call);                             \
     if (e__ != cudaSuccess) return cuda_fail(ctx, e__, where); \
+  } while (0)
+
+template <typename R>
+hotrg_status gemm_launch(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R* Blo, int64_t ld, R* C,
+                         int64_t M, int64_t N, int64_t K, double alpha, double beta, cudaStream_t st);
+
+// A launcher call that issues `n` kernels.
+#define LK(n, call, where)                                \
+  do {                                                    \
+    CK(call, where);                                      \
+    ctx->launches += (n);                                 \
   } while (0)
 
 // Largest element offset a TTM launch touches in its input, isometry and output (all
@@ -372,7 +393,7 @@ hotrg_status build_A(hotrg_ctx* ctx, const StepPlan& p, const R* P, const R* Ua,
     };
     TTMArgs t = make_ttm(d, Da, ts[2 * a], (int64_t)Da * ca, 1, 0, 0, 1.0, 0.0);
     ttm_limits(p.E, (int64_t)Da * Da * ca - x0, (int64_t)xs * p.E);
-    CK(launch_ttm_r<R>(P, Ua + x0, O1, nullptr, t, kTTMStore, st), "ttm A1");
+    LK(1, launch_ttm_r<R>(P, Ua + x0, O1, nullptr, t, kTTMStore, st), "ttm A1");
   }
   // A[(X Y c1 c1' mu1), (a2 b2 a1' b1' k)] = sum_b1 U^b[b1, b2, Y] O1[X, b1, ...]
   {
@@ -398,7 +419,7 @@ hotrg_status build_A(hotrg_ctx* ctx, const StepPlan& p, const R* P, const R* Ua,
     TTMArgs t = make_ttm(d, Db, os[1], (int64_t)Db * cb, 1, 0, 0, 1.0, 0.0);
     const int mode = Alo ? kTTMSplitTF32 : kTTMStore;
     ttm_limits((int64_t)xs * p.E, (int64_t)Db * Db * cb, (int64_t)xs * cb * Dc * Dc * Dm * ld);
-    CK(launch_ttm_r<R>(O1, Ub, A, Alo, t, mode, st), "ttm A2");
+    LK(1, launch_ttm_r<R>(O1, Ub, A, Alo, t, mode, st), "ttm A2");
   }
   return HOTRG_OK;
 }
@@ -428,7 +449,7 @@ hotrg_status build_B(hotrg_ctx* ctx, const StepPlan& p, const R* Q, const R* Ua,
     };
     TTMArgs t = make_ttm(d, Da, ts[2 * a + 1], ca, 1, 0, 0, 1.0, 0.0);
     ttm_limits(p.E, (int64_t)Da * Da * ca, (int64_t)ca * p.E);
-    CK(launch_ttm_r<R>(Q, Ua, O1, nullptr, t, kTTMStore, st), "ttm B1");
+    LK(1, launch_ttm_r<R>(Q, Ua, O1, nullptr, t, kTTMStore, st), "ttm B1");
   }
   {
     const int64_t ld = p.ldk;
@@ -451,7 +472,7 @@ hotrg_status build_B(hotrg_ctx* ctx, const StepPlan& p, const R* Q, const R* Ua,
     TTMArgs t = make_ttm(d, Db, os[1], cb, 1, 0, 0, 1.0, 0.0);
     const int mode = Blo ? kTTMSplitTF32 : kTTMStore;
     ttm_limits((int64_t)ca * p.E, (int64_t)Db * Db * cb, p.rowsB * ld);
-    CK(launch_ttm_r<R>(O1, Ub, B, Blo, t, mode, st), "ttm B2");
+    LK(1, launch_ttm_r<R>(O1, Ub, B, Blo, t, mode, st), "ttm B2");
   }
   return HOTRG_OK;
 }
@@ -486,7 +507,7 @@ hotrg_status close_C(hotrg_ctx* ctx, const StepPlan& p, const R* C, const R* Uc,
     };
     TTMArgs t = make_ttm(d, Dc, ms[2] * N, (int64_t)Dc * cc, Dc, ns[2], cc, 1.0, 0.0);
     ttm_limits((int64_t)xs * cb * Dc * Dc * Dm * N, (int64_t)Dc * Dc * cc, on[0] * os[0]);
-    CK(launch_ttm_r<R>(C, Uc, O3, nullptr, t, kTTMStore, st), "ttm close1");
+    LK(1, launch_ttm_r<R>(C, Uc, O3, nullptr, t, kTTMStore, st), "ttm close1");
   }
   {
     int64_t tn[8];
@@ -522,7 +543,7 @@ hotrg_status close_C(hotrg_ctx* ctx, const StepPlan& p, const R* C, const R* Uc,
     TTMArgs t = make_ttm(d, Dc, os[3], (int64_t)Dc * cc, Dc, os[7], cc, 1.0, 0.0);
     R* out = Tn + (int64_t)x0 * tn[2 * a];
     ttm_limits(on[0] * os[0], (int64_t)Dc * Dc * cc, p.Enew - (int64_t)x0 * tn[2 * a]);
-    CK(launch_ttm_r<R>(O3, Uc, out, nullptr, t, kTTMStore, st), "ttm close2");
+    LK(1, launch_ttm_r<R>(O3, Uc, out, nullptr, t, kTTMStore, st), "ttm close2");
   }
   return HOTRG_OK;
 }
@@ -530,6 +551,32 @@ hotrg_status close_C(hotrg_ctx* ctx, const StepPlan& p, const R* C, const R* Uc,
 template <typename R>
 hotrg_status gemm(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R* Blo, int64_t ld, R* C, int64_t M,
                   int64_t N, int64_t K, double alpha, double beta, cudaStream_t st) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ctx->profiling) {
+    while (ctx->ev.size() < ctx->ev_used + 2) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e), "event create");
+      ctx->ev.push_back(e);
+    }
+    e0 = ctx->ev[ctx->ev_used];
+    e1 = ctx->ev[ctx->ev_used + 1];
+    ctx->ev_used += 2;
+    CK(cudaEventRecord(e0, st), "event record");
+  }
+  hotrg_status r = gemm_launch<R>(ctx, A, Alo, B, Blo, ld, C, M, N, K, alpha, beta, st);
+  if (r != HOTRG_OK) return r;
+  ctx->launches += 1;
+  if (ctx->profiling) {
+    CK(cudaEventRecord(e1, st), "event record");
+    ctx->gemm_launches += 1;
+    ctx->gemm_flops += 2.0 * (double)M * (double)N * (double)K;
+  }
+  return HOTRG_OK;
+}
+
+template <typename R>
+hotrg_status gemm_launch(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R* Blo, int64_t ld, R* C,
+                         int64_t M, int64_t N, int64_t K, double alpha, double beta, cudaStream_t st) {
   if (ctx->prec == HOTRG_TF32X3) {
     CK(launch_gemm_tf32x3((const float*)A, (const float*)Alo, ld, (const float*)B, (const float*)Blo, ld, (float*)C,
                           N, M, N, K, (float)alpha, (float)beta, (int*)(ctx->ws + ctx->L.status), st),
@@ -591,17 +638,17 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
         }
       }
     }
-    CK(launch_gram<R>(gp, nj, p.Rmax, p.nchunks, st), "gram");
+    LK(1, launch_gram<R>(gp, nj, p.Rmax, p.nchunks, st), "gram");
     for (int i = 0; i < nj; ++i) {
       const int R2 = gp.j[i].D1 * gp.j[i].D2;
-      CK(launch_gram_reduce(gp.j[i].partial, p.nchunks, (int64_t)R2 * R2, gA + (int64_t)i * p.Rmax * p.Rmax, st),
+      LK(1, launch_gram_reduce(gp.j[i].partial, p.nchunks, (int64_t)R2 * R2, gA + (int64_t)i * p.Rmax * p.Rmax, st),
          "gram reduce");
     }
     double* G = (double*)(sb + sc.G);
     for (int i = 0; i < 3; ++i) {
       for (int side = 0; side < 2; ++side) {
         const int j1 = (i * 2 + side) * 2;
-        CK(launch_gram_merge(gA + (int64_t)j1 * p.Rmax * p.Rmax, gA + (int64_t)(j1 + 1) * p.Rmax * p.Rmax,
+        LK(1, launch_gram_merge(gA + (int64_t)j1 * p.Rmax * p.Rmax, gA + (int64_t)(j1 + 1) * p.Rmax * p.Rmax,
                              p.D[dirs[i]], p.D[mu], G + (int64_t)(i * 2 + side) * p.nmax * p.nmax, st),
            "gram merge");
       }
@@ -630,7 +677,7 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
       }
     }
     const bool fp64 = ctx->prec == HOTRG_FP64;
-    CK(launch_jacobi(ep, 6, nmax, fp64 ? 1e-10 : 1e-6, status, st), "jacobi");
+    LK(1, launch_jacobi(ep, 6, nmax, fp64 ? 1e-10 : 1e-6, status, st), "jacobi");
     SelectPack sp{};
     double* U64 = (double*)(ctx->ws + ctx->L.U64) + (int64_t)bidx * 4 * kMaxGramN * kMaxLeg;
     R* Ur = (R*)(ctx->ws + ctx->L.Ur) + (int64_t)bidx * 4 * kMaxGramN * kMaxLeg;
@@ -652,7 +699,7 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
       j.rec_primed = &rec->primed[n];
       j.rec_degen = &rec->degen[n];
     }
-    CK(launch_select<R>(sp, 3, fp64 ? 1e-9 : 1e-6, st), "select");
+    LK(1, launch_select<R>(sp, 3, fp64 ? 1e-9 : 1e-6, st), "select");
     const R* Ua = Ur + (int64_t)p.a * kMaxGramN * kMaxLeg;
     const R* Ub = Ur + (int64_t)p.b * kMaxGramN * kMaxLeg;
     const R* Uc = Ur + (int64_t)p.c * kMaxGramN * kMaxLeg;
@@ -727,9 +774,9 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
     double* lnz = (double*)(ctx->ws + ctx->L.lnz) + bidx;
     double* cval = (double*)(ctx->ws + ctx->L.cval) + bidx;
     const double weight = ldexp(1.0, -(kstep + 1));
-    CK(launch_norm<R>(dst[0], p.Enew, (double*)(sb + sc.npart), weight, cval, lnz, &rec->ln_c, status, st),
+    LK(2, launch_norm<R>(dst[0], p.Enew, (double*)(sb + sc.npart), weight, cval, lnz, &rec->ln_c, status, st),
        "norm");
-    for (int w = 0; w < nt; ++w) CK(launch_scale<R>(dst[w], p.Enew, cval, st), "scale");
+    for (int w = 0; w < nt; ++w) LK(1, launch_scale<R>(dst[w], p.Enew, cval, st), "scale");
   }
   return HOTRG_OK;
 }
@@ -871,11 +918,11 @@ hotrg_status hotrg_init_tensor(hotrg_ctx* ctx, const double* beta, const double*
   const double* dh = (const double*)(ctx->ws + ctx->L.hfield);
   double* lnz = (double*)(ctx->ws + ctx->L.lnz);
   if (ctx->prec == HOTRG_FP64)
-    CK(launch_init<double>(db, dh, tensor_ptr<double>(ctx, 0, 0, 0),
+    LK(1, launch_init<double>(db, dh, tensor_ptr<double>(ctx, 0, 0, 0),
                            ctx->impure ? tensor_ptr<double>(ctx, 1, 0, 0) : nullptr, ctx->L.cap, lnz, ctx->batch, st),
        "init");
   else
-    CK(launch_init<float>(db, dh, tensor_ptr<float>(ctx, 0, 0, 0),
+    LK(1, launch_init<float>(db, dh, tensor_ptr<float>(ctx, 0, 0, 0),
                           ctx->impure ? tensor_ptr<float>(ctx, 1, 0, 0) : nullptr, ctx->L.cap, lnz, ctx->batch, st),
        "init");
   // the beta/h uploads read host memory that may go away: make them complete now
@@ -967,11 +1014,11 @@ hotrg_status hotrg_step(hotrg_ctx* ctx, int dir, int dcut) {
 static hotrg_status traces(hotrg_ctx* ctx, int which, std::vector<double>& out) {
   const double* dtr = (const double*)(ctx->ws + ctx->L.trace);
   if (ctx->prec == HOTRG_FP64)
-    CK(launch_trace<double>(tensor_ptr<double>(ctx, which, ctx->cur, 0), ctx->L.cap, ctx->dims, ctx->batch,
+    LK(1, launch_trace<double>(tensor_ptr<double>(ctx, which, ctx->cur, 0), ctx->L.cap, ctx->dims, ctx->batch,
                             (double*)dtr + which * ctx->batch, ctx->stream),
        "trace");
   else
-    CK(launch_trace<float>(tensor_ptr<float>(ctx, which, ctx->cur, 0), ctx->L.cap, ctx->dims, ctx->batch,
+    LK(1, launch_trace<float>(tensor_ptr<float>(ctx, which, ctx->cur, 0), ctx->L.cap, ctx->dims, ctx->batch,
                            (double*)dtr + which * ctx->batch, ctx->stream),
        "trace");
   hotrg_status s = sync_and_status(ctx);
@@ -1091,6 +1138,33 @@ hotrg_status hotrg_copy_isometry(hotrg_ctx* ctx, int b, int nu, double* host, si
   CK(cudaStreamSynchronize(ctx->stream), "sync");
   const double* U64 = (const double*)(ctx->ws + ctx->L.U64) + ((int64_t)b * 4 + nu) * kMaxGramN * kMaxLeg;
   CK(cudaMemcpy(host, U64, cnt * 8, cudaMemcpyDeviceToHost), "copy U");
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_profile_enable(hotrg_ctx* ctx, int enable) {
+  if (!ctx) return HOTRG_EINVAL;
+  if (ctx->ready) CK(cudaStreamSynchronize(ctx->stream), "sync");
+  ctx->profiling = enable != 0;
+  ctx->ev_used = 0;
+  ctx->launches = 0;
+  ctx->gemm_launches = 0;
+  ctx->gemm_flops = 0;
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_profile_read(hotrg_ctx* ctx, hotrg_profile* out) {
+  if (!ctx || !out) return HOTRG_EINVAL;
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  double ms = 0;
+  for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+    float t = 0;
+    CK(cudaEventElapsedTime(&t, ctx->ev[i], ctx->ev[i + 1]), "event elapsed");
+    ms += t;
+  }
+  out->launches = ctx->launches;
+  out->gemm_launches = ctx->gemm_launches;
+  out->gemm_ms = ms;
+  out->gemm_flops = ctx->gemm_flops;
   return HOTRG_OK;
 }
 

@@ -38,11 +38,17 @@ class StepRecord(ctypes.Structure):
                 ("degenerate", ctypes.c_int * 4)]
 
 
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("gemm_launches", ctypes.c_uint64), ("gemm_ms", ctypes.c_double),
+                ("gemm_flops", ctypes.c_double)]
+
+
 _LIB = None
 SYMBOLS = ["hotrg_create", "hotrg_destroy", "hotrg_workspace_size", "hotrg_set_workspace", "hotrg_set_stream",
            "hotrg_init_tensor", "hotrg_set_tensor", "hotrg_step", "hotrg_lnZ", "hotrg_impure_magnetization",
            "hotrg_impure_energy", "hotrg_step_info", "hotrg_state", "hotrg_copy_tensor", "hotrg_copy_isometry",
-           "hotrg_step_flops", "hotrg_status_string", "hotrg_last_error"]
+           "hotrg_step_flops", "hotrg_profile_enable", "hotrg_profile_read", "hotrg_status_string",
+           "hotrg_last_error"]
 
 
 def library_path() -> str:
@@ -75,6 +81,8 @@ def _lib():
         "hotrg_copy_tensor": (c_int, [c_void_p, c_int, c_int, P(c_double), c_size_t]),
         "hotrg_copy_isometry": (c_int, [c_void_p, c_int, c_int, P(c_double), c_size_t]),
         "hotrg_step_flops": (c_int, [c_void_p, c_int, c_int, P(c_double), P(c_double)]),
+        "hotrg_profile_enable": (c_int, [c_void_p, c_int]),
+        "hotrg_profile_read": (c_int, [c_void_p, P(Profile)]),
         "hotrg_status_string": (ctypes.c_char_p, [c_int]),
         "hotrg_last_error": (ctypes.c_char_p, []),
     }
@@ -210,6 +218,14 @@ class HOTRG:
         out = np.zeros(16 * 16 * 16)
         _check(self.lib.hotrg_copy_isometry(self.ctx, b, nu, _dptr(out), out.size), "copy_isometry")
         return out[: dold * dold * chi].reshape(dold, dold, chi)
+
+    def profile(self, enable: bool = True):
+        _check(self.lib.hotrg_profile_enable(self.ctx, int(enable)), "profile_enable")
+
+    def profile_read(self) -> dict:
+        p = Profile()
+        _check(self.lib.hotrg_profile_read(self.ctx, ctypes.byref(p)), "profile_read")
+        return dict(launches=p.launches, gemm_launches=p.gemm_launches, gemm_ms=p.gemm_ms, gemm_flops=p.gemm_flops)
 
     def step_flops(self, direction: int, dcut: int):
         m, t = ctypes.c_double(), ctypes.c_double()
