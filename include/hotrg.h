@@ -174,6 +174,31 @@ hotrg_status hotrg_profile_enable(hotrg_ctx* ctx, int enable);
 /* Counters since the last hotrg_profile_enable. Synchronises the stream. */
 hotrg_status hotrg_profile_read(hotrg_ctx* ctx, hotrg_profile* out);
 
+/* HOSVD isometry of one transverse direction, for callers that cannot allocate device
+ * memory. The paper has no counterpart: this is an allocation-free form of the isometry
+ * stage of hotrg_step for code that runs inside another framework's memory pool or
+ * under a fixed memory budget, plugins handed only their input and output buffers, and
+ * threads that must not enter the allocator while other GPU work is in flight.
+ *
+ * Input: T_dev, a device FP64 tensor with bond dimensions dims[4] in the library's
+ * layout (header comment); step direction mu, transverse direction nu (mu != nu), cut
+ * dcut. Output (device memory, caller-owned): U_dev, the isometry as in
+ * hotrg_copy_isometry (row-major [(i1 D_nu + i2)][chi], chi = min(D_nu^2, dcut)),
+ * eps_dev[2], the discarded eigenvalue sums of the nu and nu' sides, primed_dev[0], 1
+ * if the nu' side was taken. Same kernels, tolerances and canonical gauge as the FP64
+ * mode of hotrg_step. Runs on `stream` (cudaStream_t, NULL = legacy default) and
+ * returns after the results are written (synchronises the stream).
+ *
+ * It allocates nothing: all intermediates live in one fixed device array of 8 MiB
+ * inside the library, held by every GPU that loads the library until the process
+ * exits. Limit: every bond dimension <= 8 (larger ones return HOTRG_EINVAL with the
+ * reason in hotrg_last_error). The first call on a device looks up that array's device
+ * address (make it before any stream capture). Calls share the array, so calls that
+ * overlap on the GPU race; each call clears the status words it uses.
+ * Errors: EINVAL, ECUDA, ENOCONV. */
+hotrg_status hotrg_isometry_noalloc(const double* T_dev, const int dims[4], int mu, int nu, int dcut,
+                                    double* U_dev, double* eps_dev, int* primed_dev, void* stream);
+
 /* Text of a status code, and the last CUDA error message seen by this thread. */
 const char* hotrg_status_string(int status);
 const char* hotrg_last_error(void);

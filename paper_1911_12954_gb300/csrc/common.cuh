@@ -91,6 +91,9 @@ struct GramPack { GramJob j[kMaxGramJobs]; };
 struct EigPack { EigJob j[kMaxEigJobs]; };
 struct SelectPack { SelectJob j[kMaxSelectJobs]; };
 
+// Message returned by hotrg_last_error for this host thread.
+void set_last_error(const char* msg);
+
 // Host-side launchers (defined in the .cu files, called by the orchestrator).
 template <typename TI, typename TU, typename TO>
 cudaError_t launch_ttm(const TI* in, const TU* U, TO* out, TO* out_lo, const TTMArgs& a, int mode,

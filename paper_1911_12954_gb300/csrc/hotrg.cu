@@ -37,6 +37,12 @@ namespace {
 
 thread_local std::string g_last_error;
 
+}  // namespace
+
+void hotrg::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
+namespace {
+
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Sizes of one step (elements), derived from the bond dimensions before the step.

@@ -27,7 +27,7 @@ class HotrgError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
         msg = f"{where}: {STATUS.get(status, status)}"
-        if status == -3:
+        if status in (-1, -3):
             msg += " (" + _lib().hotrg_last_error().decode() + ")"
         super().__init__(msg)
 
@@ -47,8 +47,8 @@ _LIB = None
 SYMBOLS = ["hotrg_create", "hotrg_destroy", "hotrg_workspace_size", "hotrg_set_workspace", "hotrg_set_stream",
            "hotrg_init_tensor", "hotrg_set_tensor", "hotrg_step", "hotrg_lnZ", "hotrg_impure_magnetization",
            "hotrg_impure_energy", "hotrg_step_info", "hotrg_state", "hotrg_copy_tensor", "hotrg_copy_isometry",
-           "hotrg_step_flops", "hotrg_profile_enable", "hotrg_profile_read", "hotrg_status_string",
-           "hotrg_last_error"]
+           "hotrg_step_flops", "hotrg_profile_enable", "hotrg_profile_read", "hotrg_isometry_noalloc",
+           "hotrg_status_string", "hotrg_last_error"]
 
 
 def library_path() -> str:
@@ -83,6 +83,8 @@ def _lib():
         "hotrg_step_flops": (c_int, [c_void_p, c_int, c_int, P(c_double), P(c_double)]),
         "hotrg_profile_enable": (c_int, [c_void_p, c_int]),
         "hotrg_profile_read": (c_int, [c_void_p, P(Profile)]),
+        "hotrg_isometry_noalloc": (c_int, [c_void_p, P(c_int), c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
+                                           c_void_p]),
         "hotrg_status_string": (ctypes.c_char_p, [c_int]),
         "hotrg_last_error": (ctypes.c_char_p, []),
     }
