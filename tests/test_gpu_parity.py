@@ -209,3 +209,38 @@ def test_errors_are_reported_not_raised_on_device():
         g.init_tensor(-1.0, 0.0)          # beta < 0
     g.step(0, 4)
     assert math.isfinite(g.lnZ()[0])
+
+
+# ------------------------------------------------------------------ D_cut = 8, the 1024^4 workload
+def test_dcut8_tf32x3_first_8_steps_vs_golden():
+    """The benchmark's workload (T = 6.65, h = 0, D_cut = 8, towards 1024^4) in the launch
+    configuration bench.py times: |Delta ln Z/V| <= 1e-6 against the FP64 oracle over the
+    first 8 steps (step 2 cuts through a degenerate eigenvalue cluster)."""
+    gd = _golden("ising4d_T6.65_h0_dcut8_8steps")
+    cfg = gd["config"]
+    sched = [(s["mu"], cfg["dcut"]) for s in gd["steps"]]
+    g = _gpu(batch=1, dcut_max=8, precision="tf32x3", schedule=sched)
+    g.init_tensor(gd["beta"], cfg["h"])
+    for i, (mu, dc) in enumerate(sched):
+        g.step(mu, dc)
+        ref = gd["steps"][i]
+        assert abs(g.lnZ()[0] - ref["lnZ"]) <= 1e-6, (i + 1, g.lnZ()[0], ref["lnZ"])
+        assert list(g.step_info(i + 1)["dims"]) == ref["dims"]
+
+
+def test_dcut8_fp64_first_4_steps_vs_golden():
+    """FP64 GPU path on the D_cut = 8 workload through the first steady-state step
+    (step 4: every bond dimension 8, a 7e13-flop contraction): 1e-10 relative."""
+    gd = _golden("ising4d_T6.65_h0_dcut8_8steps")
+    cfg = gd["config"]
+    sched = [(s["mu"], cfg["dcut"]) for s in gd["steps"][:4]]
+    g = _gpu(batch=1, dcut_max=8, precision="fp64", schedule=sched)
+    g.init_tensor(gd["beta"], cfg["h"])
+    for i, (mu, dc) in enumerate(sched):
+        g.step(mu, dc)
+        ref = gd["steps"][i]
+        assert g.lnZ()[0] == pytest.approx(ref["lnZ"], rel=1e-10), (i + 1, g.lnZ()[0], ref["lnZ"])
+        info = g.step_info(i + 1)
+        assert info["ln_c"] == pytest.approx(ref["ln_c"], rel=1e-10)
+        for n, (e0, e1) in ref["eps"].items():
+            assert info["eps"][int(n)] == pytest.approx((e0, e1), rel=1e-7, abs=1e-12)
