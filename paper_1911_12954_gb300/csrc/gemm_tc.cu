@@ -41,17 +41,26 @@ namespace tc {
 
 constexpr int BM = 128;
 constexpr int BN = 256;
-constexpr int BK = 32;                                  // fp32 elements per 128-byte row
-constexpr int STAGES = 2;
-constexpr int A_BYTES = BM * BK * 4;                    // 16 KB
-constexpr int B_BYTES = BN * BK * 4;                    // 32 KB
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 96 KB
 constexpr int TMEM_COLS = 2 * BN;                       // two chunk accumulators
 constexpr int GROUP_M = 16;
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
-constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int CHUNK_K = 32;                             // k promoted from TMEM to registers at once
 constexpr unsigned long long kWaitNs = 4000000000ull;
+
+// Pipeline variants. BK fp32 elements per k-block = one swizzle row (128 B or 64 B).
+template <int BK_>
+struct Cfg {
+  static constexpr int BK = BK_;
+  static constexpr int STAGES = BK_ == 32 ? 2 : 4;
+  static constexpr int A_BYTES = BM * BK * 4;
+  static constexpr int B_BYTES = BN * BK * 4;
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int KB_PER_CHUNK = CHUNK_K / BK;
+  static constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr uint64_t LAYOUT = BK_ == 32 ? 2 : 4;          // UMMA swizzle: 128 B or 64 B
+  static constexpr uint32_t SBO = 8 * BK_ * 4;                    // 8 rows of one swizzle row
+};
 
 // instruction descriptor: D = F32, A = B = TF32, both K-major, N = 256, M = 128
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
@@ -106,12 +115,15 @@ __device__ __forceinline__ void tma_load(const CUtensorMap* map, uint64_t* bar, 
       : "memory");
 }
 
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// K-major operand in the canonical swizzled layout TMA writes: rows of one swizzle width,
+// 8-row groups SBO bytes apart.
+template <class C>
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
-  d |= (uint64_t)1 << 16;                            // leading byte offset (unused for SW128 K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;                  // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 16;                            // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(C::SBO >> 4) << 32;                // stride byte offset: 8 rows
   d |= (uint64_t)1 << 46;                            // descriptor version (tcgen05)
-  d |= (uint64_t)2 << 61;                            // 128-byte swizzle
+  d |= C::LAYOUT << 61;                              // swizzle mode
   return d;
 }
 
@@ -155,11 +167,14 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
   tn = r / gm;
 }
 
+template <class CF>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                        const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
                        float* __restrict__ C, int64_t ldc, int M, int N, int K, float alpha, float beta,
                        int* status) {
+  constexpr int STAGES = CF::STAGES, BK = CF::BK, A_BYTES = CF::A_BYTES, B_BYTES = CF::B_BYTES,
+                STAGE_BYTES = CF::STAGE_BYTES, KPC = CF::KB_PER_CHUNK;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
@@ -174,6 +189,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
   const int ntiles = tiles_m * tiles_n;
   const int nkb = (K + BK - 1) / BK;
+  const int nchunk = (nkb + KPC - 1) / KPC;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -239,31 +255,35 @@ __global__ void __launch_bounds__(THREADS, 1)
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       for (int kb = 0; kb < nkb; ++kb) {
-        if (!mbar_wait(&cempty[cb], cph ^ 1, status) || !mbar_wait(&full[s], ph, status)) {
+        const bool first = kb % KPC == 0;
+        const bool last = kb % KPC == KPC - 1 || kb == nkb - 1;
+        if ((first && !mbar_wait(&cempty[cb], cph ^ 1, status)) || !mbar_wait(&full[s], ph, status)) {
           ok = false;
           break;
         }
         fence_after();
         const uint32_t d = tmem + (uint32_t)(cb * BN);
         const uint32_t base = su32(smem + s * STAGE_BYTES);
-        const uint64_t ahi = sw128_desc(base), alo = sw128_desc(base + A_BYTES);
-        const uint64_t bhi = sw128_desc(base + 2 * A_BYTES), blo = sw128_desc(base + 2 * A_BYTES + B_BYTES);
+        const uint64_t ahi = smem_desc<CF>(base), alo = smem_desc<CF>(base + A_BYTES);
+        const uint64_t bhi = smem_desc<CF>(base + 2 * A_BYTES), blo = smem_desc<CF>(base + 2 * A_BYTES + B_BYTES);
 #pragma unroll
         for (int kk = 0; kk < BK / 8; ++kk) {
           const uint64_t off = (uint64_t)(kk * 32) >> 4;   // 8 tf32 = 32 bytes along the swizzled row
-          mma_tf32(d, alo + off, bhi + off, kk != 0);
+          mma_tf32(d, alo + off, bhi + off, (first && kk == 0) ? 0u : 1u);
           mma_tf32(d, ahi + off, blo + off, 1);
           mma_tf32(d, ahi + off, bhi + off, 1);
         }
         mma_commit(&empty[s]);
-        mma_commit(&cfull[cb]);
+        if (last) {
+          mma_commit(&cfull[cb]);
+          if (++cb == 2) {
+            cb = 0;
+            cph ^= 1;
+          }
+        }
         if (++s == STAGES) {
           s = 0;
           ph ^= 1;
-        }
-        if (++cb == 2) {
-          cb = 0;
-          cph ^= 1;
         }
       }
     }
@@ -285,7 +305,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       float acc[BN / 2];
 #pragma unroll
       for (int j = 0; j < BN / 2; ++j) acc[j] = 0.f;
-      for (int kb = 0; kb < nkb; ++kb) {
+      for (int kc = 0; kc < nchunk; ++kc) {
         // warp-uniform outcome: tcgen05.ld below must be executed by all 32 lanes
         if (!__all_sync(0xffffffffu, mbar_wait(&cfull[cb], cph, status))) {
           ok = false;
@@ -354,32 +374,26 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-bool make_map(CUtensorMap* map, const float* ptr, int64_t rows, int64_t K, int64_t ld, int box_rows) {
+bool make_map(CUtensorMap* map, const float* ptr, int64_t rows, int64_t K, int64_t ld, int box_rows, int bk) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)ptr, dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, bk == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
-}  // namespace tc
-
-cudaError_t launch_gemm_tf32x3(const float* Ahi, const float* Alo, int64_t lda, const float* Bhi, const float* Blo,
-                               int64_t ldb, float* C, int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha,
-                               float beta, int* status, cudaStream_t st) {
-  using namespace tc;
-  if (M <= 0 || N <= 0) return cudaSuccess;
-  if (K <= 0 || M > 0x7fffffff || N > 0x7fffffff || K > 0x7fffffff) return cudaErrorInvalidValue;
-  if ((lda & 3) || (ldb & 3) || lda < K || ldb < K) return cudaErrorInvalidValue;
-  if ((((uintptr_t)Ahi) | ((uintptr_t)Alo) | ((uintptr_t)Bhi) | ((uintptr_t)Blo)) & 15) return cudaErrorInvalidValue;
+template <class CF>
+cudaError_t launch_variant(const float* Ahi, const float* Alo, int64_t lda, const float* Bhi, const float* Blo,
+                           int64_t ldb, float* C, int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha,
+                           float beta, int* status, cudaStream_t st) {
   CUtensorMap mAhi, mAlo, mBhi, mBlo;
-  if (!make_map(&mAhi, Ahi, M, K, lda, BM) || !make_map(&mAlo, Alo, M, K, lda, BM) ||
-      !make_map(&mBhi, Bhi, N, K, ldb, BN) || !make_map(&mBlo, Blo, N, K, ldb, BN))
+  if (!make_map(&mAhi, Ahi, M, K, lda, BM, CF::BK) || !make_map(&mAlo, Alo, M, K, lda, BM, CF::BK) ||
+      !make_map(&mBhi, Bhi, N, K, ldb, BN, CF::BK) || !make_map(&mBlo, Blo, N, K, ldb, BN, CF::BK))
     return cudaErrorInvalidValue;
   static int sms = 0;
   static bool attr = false;
@@ -389,15 +403,39 @@ cudaError_t launch_gemm_tf32x3(const float* Ahi, const float* Alo, int64_t lda, 
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(gemm_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    e = cudaFuncSetAttribute(gemm_tf32x3_kernel<CF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)CF::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
   const int grid = (int)(tiles < sms ? tiles : sms);
-  gemm_tf32x3_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(mAhi, mAlo, mBhi, mBlo, C, ldc, (int)M, (int)N, (int)K,
-                                                        alpha, beta, status);
+  gemm_tf32x3_kernel<CF><<<grid, THREADS, CF::SMEM_BYTES, st>>>(mAhi, mAlo, mBhi, mBlo, C, ldc, (int)M, (int)N,
+                                                               (int)K, alpha, beta, status);
   return cudaGetLastError();
+}
+
+}  // namespace tc
+
+// variant 0 (default): k-blocks of 16, 64-byte swizzle, 4 stages; variant 1: k-blocks of
+// 32, 128-byte swizzle, 2 stages.
+cudaError_t launch_gemm_tf32x3_v(const float* Ahi, const float* Alo, int64_t lda, const float* Bhi,
+                                 const float* Blo, int64_t ldb, float* C, int64_t ldc, int64_t M, int64_t N,
+                                 int64_t K, float alpha, float beta, int* status, cudaStream_t st, int variant) {
+  using namespace tc;
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (K <= 0 || M > 0x7fffffff || N > 0x7fffffff || K > 0x7fffffff) return cudaErrorInvalidValue;
+  if ((lda & 3) || (ldb & 3) || lda < K || ldb < K) return cudaErrorInvalidValue;
+  if ((((uintptr_t)Ahi) | ((uintptr_t)Alo) | ((uintptr_t)Bhi) | ((uintptr_t)Blo)) & 15) return cudaErrorInvalidValue;
+  if (variant == 1)
+    return launch_variant<Cfg<32>>(Ahi, Alo, lda, Bhi, Blo, ldb, C, ldc, M, N, K, alpha, beta, status, st);
+  return launch_variant<Cfg<16>>(Ahi, Alo, lda, Bhi, Blo, ldb, C, ldc, M, N, K, alpha, beta, status, st);
+}
+
+cudaError_t launch_gemm_tf32x3(const float* Ahi, const float* Alo, int64_t lda, const float* Bhi, const float* Blo,
+                               int64_t ldb, float* C, int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha,
+                               float beta, int* status, cudaStream_t st) {
+  return launch_gemm_tf32x3_v(Ahi, Alo, lda, Bhi, Blo, ldb, C, ldc, M, N, K, alpha, beta, status, st, 0);
 }
 
 }  // namespace hotrg

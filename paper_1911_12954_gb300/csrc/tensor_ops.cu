@@ -1,6 +1,6 @@
 // tensor_ops.cu - memory-bound tensor kernels of the HOTRG step.
 //
-//  * ttm_kernel     : contraction of one or two legs of a tensor with an isometry
+//  * ttm_fiber_kernel / ttm_kernel : contraction of one or two legs of a tensor with an isometry
 //                     (the half contractions T x U^a x U^b that build the operands of
 //                     the block-spin GEMM, and the closing contractions with U^c,
 //                     Fig. 1C), writing any output leg order, optionally split into
@@ -9,6 +9,8 @@
 //  * sumsq/normalise: c = ||T'||_F in FP64, ln c / 2^k accumulated (ln Z / V), T' /= c.
 //  * trace_kernel   : Tr T (each leg joined to its primed partner), FP64.
 #include <math.h>
+
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -73,11 +75,141 @@ __global__ void __launch_bounds__(256) ttm_kernel(const TI* __restrict__ in, con
   }
 }
 
+// ---------------------------------------------------------------------------- fiber form
+// The same contraction organised by input fibre: the J contracted entries of one fibre
+// are loaded once into registers and every output of the new index (up to two dims,
+// R <= 256 values, U staged in shared memory) is produced from them. Each input element
+// is read once and each output written once; consecutive threads take consecutive
+// fibres, so reads and writes along the innermost fibre dimension are coalesced. Used
+// whenever J <= 64, which covers every pass of a step with bond dimensions <= 8.
+struct FiberArgs {
+  int nf;                       // fibre dims (outermost first)
+  int64_t fdims[kMaxRank], fin[kMaxRank], fout[kMaxRank];
+  int64_t nfib;
+  int R1, R2;                   // new-index dims
+  int64_t ru1, ru2, ro1, ro2;   // their U-column and output strides
+  int J1, J2;                   // contracted dims
+  int64_t ji1, ji2, ju1, ju2;   // their input and U-row strides
+  double alpha;
+};
+
+template <typename R, int JMAX, int MODE>
+__global__ void __launch_bounds__(256) ttm_fiber_kernel(const R* __restrict__ in, const R* __restrict__ U,
+                                                        R* __restrict__ out, R* __restrict__ out_lo, FiberArgs a) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  const int J = a.J1 * a.J2, Rn = a.R1 * a.R2;
+  R* Us = (R*)fsm;                                       // [J][Rn]
+  int64_t* joff = (int64_t*)(fsm + (((size_t)J * Rn * sizeof(R) + 15) / 16) * 16);
+  for (int e = threadIdx.x; e < J * Rn; e += blockDim.x) {
+    const int j = e / Rn, r = e % Rn;
+    const int j1 = j / a.J2, j2 = j % a.J2, r1 = r / a.R2, r2 = r % a.R2;
+    Us[e] = U[j1 * a.ju1 + j2 * a.ju2 + r1 * a.ru1 + r2 * a.ru2];
+  }
+  for (int j = threadIdx.x; j < J; j += blockDim.x) joff[j] = (j / a.J2) * a.ji1 + (j % a.J2) * a.ji2;
+  __syncthreads();
+  using Acc = R;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < a.nfib; f += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q = f, io = 0, oo = 0;
+    for (int d = a.nf - 1; d >= 0; --d) {
+      const int64_t n = a.fdims[d];
+      const int64_t i = q % n;
+      q /= n;
+      io += i * a.fin[d];
+      oo += i * a.fout[d];
+    }
+    R x[JMAX];
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j)
+      if (j < J) x[j] = in[io + joff[j]];
+    for (int r1 = 0; r1 < a.R1; ++r1) {
+      for (int r2 = 0; r2 < a.R2; ++r2) {
+        const int r = r1 * a.R2 + r2;
+        Acc acc = 0;
+#pragma unroll
+        for (int j = 0; j < JMAX; ++j)
+          if (j < J) acc = fma(Us[j * Rn + r], x[j], acc);
+        acc *= (Acc)a.alpha;
+        const int64_t o = oo + r1 * a.ro1 + r2 * a.ro2;
+        if (MODE == kTTMSplitTF32) {
+          const float v = (float)acc;
+          const float hi = tf32_round(v);
+          out[o] = (R)hi;
+          out_lo[o] = (R)tf32_round(v - hi);
+        } else {
+          out[o] = acc;
+        }
+      }
+    }
+  }
+}
+
+// Converts a TTMArgs into the fibre form when it fits; false otherwise.
+bool to_fiber(const TTMArgs& a, size_t rsize, FiberArgs& f) {
+  f = FiberArgs{};
+  int nr = 0;
+  f.R1 = f.R2 = 1;
+  f.ru1 = f.ru2 = f.ro1 = f.ro2 = 0;
+  f.nfib = 1;
+  for (int i = 0; i < a.rank; ++i) {
+    if (a.u_st[i] != 0) {
+      if (a.in_st[i] != 0 || nr == 2) return false;
+      if (nr == 0) {
+        f.R1 = (int)a.dims[i];
+        f.ru1 = a.u_st[i];
+        f.ro1 = a.out_st[i];
+      } else {
+        f.R2 = (int)a.dims[i];
+        f.ru2 = a.u_st[i];
+        f.ro2 = a.out_st[i];
+      }
+      ++nr;
+    } else {
+      f.fdims[f.nf] = a.dims[i];
+      f.fin[f.nf] = a.in_st[i];
+      f.fout[f.nf] = a.out_st[i];
+      f.nfib *= a.dims[i];
+      ++f.nf;
+    }
+  }
+  f.J1 = a.J1;
+  f.J2 = a.J2;
+  f.ji1 = a.in_sj1;
+  f.ji2 = a.in_sj2;
+  f.ju1 = a.u_sj1;
+  f.ju2 = a.u_sj2;
+  f.alpha = a.alpha;
+  const int J = a.J1 * a.J2, Rn = f.R1 * f.R2;
+  if (J > 64 || Rn > 256 || (size_t)J * Rn * rsize > 32768 || f.nf == 0) return false;
+  return true;
+}
+
+template <typename R>
+cudaError_t launch_fiber(const R* in, const R* U, R* out, R* out_lo, const FiberArgs& f, int mode, cudaStream_t st) {
+  const int J = f.J1 * f.J2;
+  const size_t smem = ((size_t)J * f.R1 * f.R2 * sizeof(R) + 15) / 16 * 16 + (size_t)J * sizeof(int64_t);
+  int64_t blocks = (f.nfib + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  const unsigned g = (unsigned)blocks;
+  if (J <= 16) {
+    if (mode == kTTMSplitTF32) ttm_fiber_kernel<R, 16, kTTMSplitTF32><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
+    else ttm_fiber_kernel<R, 16, kTTMStore><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
+  } else {
+    if (mode == kTTMSplitTF32) ttm_fiber_kernel<R, 64, kTTMSplitTF32><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
+    else ttm_fiber_kernel<R, 64, kTTMStore><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
+  }
+  return cudaGetLastError();
+}
+
 template <typename TI, typename TU, typename TO>
 cudaError_t launch_ttm(const TI* in, const TU* U, TO* out, TO* out_lo, const TTMArgs& a, int mode,
                        cudaStream_t st) {
   if (a.outer <= 0 || a.inner <= 0) return cudaSuccess;
   if (a.inner > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if constexpr (std::is_same<TI, TU>::value && std::is_same<TI, TO>::value) {
+    FiberArgs f;
+    if (U != nullptr && mode != kTTMAccumulate && to_fiber(a, sizeof(TI), f))
+      return launch_fiber<TI>(in, U, out, out_lo, f, mode, st);
+  }
   const int64_t blocks = a.outer < 152 * 64 ? a.outer : 152 * 64;
   const int threads = a.inner >= 256 ? 256 : (int)((a.inner + 31) / 32 * 32);
   switch (mode) {
