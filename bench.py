@@ -52,6 +52,8 @@ def parse_args():
     p.add_argument("--fp64", type=int, default=1, help="time one FP64 GPU step for the mixed-vs-FP64 ratio")
     p.add_argument("--e2e", type=int, default=1, help="time the whole 40-step job through the public API")
     p.add_argument("--cpu", type=int, default=1, help="time the FP64 oracle on a bounded sample (rank 0, N=1)")
+    p.add_argument("--batch", type=int, default=1, help="temperatures per GPU (evenly spaced in [6.60, 6.72])")
+    p.add_argument("--impure", type=int, default=0, help="propagate the sigma and sigma-sigma impure tensors")
     return p.parse_args()
 
 
@@ -120,6 +122,52 @@ class ClockSampler:
                 continue
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- replicas
+def replica_temperatures(batch: int, rank: int, world: int):
+    """Temperatures of one rank. Replicas share no data: with batch == 1 every rank runs
+    T = 6.65 + 0.001 rank; otherwise the batch * world temperatures evenly spaced in
+    [6.60, 6.72] are dealt out in contiguous blocks of `batch`."""
+    import numpy as np
+
+    if batch == 1:
+        return [T_WORK + 0.001 * rank]
+    allt = np.linspace(6.60, 6.72, batch * world)
+    return [float(t) for t in allt[rank * batch:(rank + 1) * batch]]
+
+
+class RankSync:
+    """Timing plumbing across ranks: barrier, max and sum of one scalar. No data of the
+    method crosses ranks. `dist` is torch.distributed (or None for one rank); `device`
+    is where the reduction tensor lives (cuda for NCCL, cpu for gloo)."""
+
+    def __init__(self, dist=None, device="cpu"):
+        self.dist = dist
+        self.device = device
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def _reduce(self, x, op):
+        if self.dist is None:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x):
+        return self._reduce(x, None if self.dist is None else self.dist.ReduceOp.MAX)
+
+    def sum(self, x):
+        return self._reduce(x, None if self.dist is None else self.dist.ReduceOp.SUM)
+
+    def throughput(self, flops_local: float, ms_local: float):
+        """Whole-job TFLOP/s: every rank's flops over the slowest rank's time."""
+        ms = self.max(ms_local)
+        return self.sum(flops_local) / (ms * 1e-3) / 1e12, ms
 
 
 # --------------------------------------------------------------------------- CPU oracle sample
@@ -203,35 +251,37 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
+    sync = RankSync(dist, device=torch.device("cuda", local))
+
     def barrier():
         torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
+        sync.barrier()
         torch.cuda.synchronize()
 
-    def allmax(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def allsum(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    allmax, allsum = sync.max, sync.sum
 
     D = args.dcut
-    temp = T_WORK + 0.001 * rank           # replicas: one temperature per rank
-    beta = 1.0 / temp
+    temps = replica_temperatures(args.batch, rank, world)
+    betas = [1.0 / t for t in temps]
+    beta = betas[0]
+    hfield = 1e-5 if args.impure else H_WORK
+    impure = 3 if args.impure else 0
     nsteps = args.warmup + args.steps
     sched = [(i % 4, D) for i in range(max(nsteps, 8))]
 
+    def step_flops(run, mu, dc, kdone):
+        """Algorithmic flops of one step for the whole batch: per temperature the Gram and
+        isometry work once, the contraction once per tensor product (5 with impure
+        tensors: TT, ST, TS, MT, TM; 4 at the first step: TT, ST, TS, SS)."""
+        main, total = run.step_flops(mu, dc)
+        if not impure:
+            return args.batch * total
+        nprod = 4 if kdone == 0 else 5
+        return args.batch * (nprod * main + 3 * (total - main))
+
     # ---------------------------------------------------------------- mixed precision, timed
-    run = HOTRG(batch=1, dcut_max=D, precision="tf32x3", schedule=sched)
-    run.init_tensor(beta, H_WORK)
+    run = HOTRG(batch=args.batch, dcut_max=D, precision="tf32x3", impure=impure, schedule=sched)
+    run.init_tensor(betas, hfield)
     for i in range(args.warmup):
         run.step(*sched[i])
     barrier()
@@ -241,26 +291,28 @@ def main():
         run.profile(True)
         start.record(run.stream)
         for i in range(args.warmup, nsteps):
-            flops += run.step_flops(*sched[i])[1]
+            flops += step_flops(run, *sched[i], i)
             run.step(*sched[i])
         stop.record(run.stream)
         barrier()
     prof = run.profile_read()
     run.profile(False)
-    ms = start.elapsed_time(stop)
-    ms_max = allmax(ms)
-    flops_all = allsum(flops)
-    value = flops_all / (ms_max * 1e-3) / 1e12
-    lnz_run = float(run.lnZ()[0])
+    value, ms_max = sync.throughput(flops, start.elapsed_time(stop))
+    lnz_run = [float(x) for x in run.lnZ()]
+    obs = {}
+    if impure:
+        e, ss = run.energy()
+        obs = {"magnetization": [float(x) for x in run.magnetization()], "energy": [float(x) for x in e]}
     del run
     torch.cuda.empty_cache()
 
-    # ---------------------------------------------------------------- accuracy vs FP64 oracle
+    # ---------------------------------------------------------------- accuracy vs FP64
     accuracy = {}
-    ver = HOTRG(batch=1, dcut_max=D, precision="tf32x3", schedule=sched[:8])
+    nver = 8 if D <= 8 else 3
+    ver = HOTRG(batch=1, dcut_max=D, precision="tf32x3", schedule=sched[:nver])
     ver.init_tensor(beta, H_WORK)
     mixed_lnz = []
-    for i in range(8):
+    for i in range(nver):
         ver.step(*sched[i])
         mixed_lnz.append(float(ver.lnZ()[0]))
     del ver
@@ -272,13 +324,18 @@ def main():
         accuracy["max_abs_dlnZ_vs_fp64_oracle_steps1to8"] = max(diffs)
         accuracy["dlnZ_per_step"] = diffs
 
-    # ---------------------------------------------------------------- FP64 GPU path, one step
+    # ---------------------------------------------------------------- FP64 GPU path
+    # steps 1..3 always (cheap); step 4, the first steady-state step, timed when D <= 8
     fp64 = None
-    if args.fp64:
-        r64 = HOTRG(batch=1, dcut_max=D, precision="fp64", schedule=sched[:4])
-        r64.init_tensor(beta, H_WORK)
-        for i in range(3):
-            r64.step(*sched[i])
+    ntimed64 = 1 if (args.fp64 and D <= 8) else 0
+    r64 = HOTRG(batch=1, dcut_max=D, precision="fp64", schedule=sched[:3 + ntimed64])
+    r64.init_tensor(beta, H_WORK)
+    d64 = []
+    for i in range(3):
+        r64.step(*sched[i])
+        d64.append(abs(mixed_lnz[i] - float(r64.lnZ()[0])))
+    accuracy["abs_dlnZ_mixed_vs_fp64_gpu_steps1to3"] = d64
+    if ntimed64:
         barrier()
         f64 = r64.step_flops(*sched[3])[1]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -290,14 +347,14 @@ def main():
         lnz64 = float(r64.lnZ()[0])
         fp64 = {"value": allsum(f64) / (ms64 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms64,
                 "steps": 1, "warmup": 3, "timed_step": 4,
-                "speedup_mixed_vs_fp64": ms64 / (ms_max / args.steps)}
+                "speedup_mixed_vs_fp64": ms64 / (ms_max / args.steps) * args.batch * (5 if impure else 1)}
         accuracy["abs_dlnZ_mixed_vs_fp64_gpu_step4"] = abs(mixed_lnz[3] - lnz64)
-        del r64
-        torch.cuda.empty_cache()
+    del r64
+    torch.cuda.empty_cache()
 
     # ---------------------------------------------------------------- end to end, public API
     e2e = None
-    if args.e2e:
+    if args.e2e and args.batch == 1 and not impure:
         full = [(i % 4, D) for i in range(LATTICE_STEPS)]
         job = HOTRG(batch=1, dcut_max=D, precision="tf32x3", schedule=full)
         bh = torch.tensor([beta], dtype=torch.float64).pin_memory()
@@ -338,9 +395,13 @@ def main():
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "tf32x3", "data": "synthetic",
-        "config": {"workload": f"4D Ising HOTRG, T={T_WORK}, h={H_WORK}, D_cut={D}, 1024^4 lattice schedule "
-                               f"(x,y,z,t cycled); timed steps {args.warmup + 1}..{nsteps} (steady state)",
-                   "dcut": D, "temperatures_per_gpu": 1, "lattice": "1024^4", "precision": "tf32x3 (fp32 storage)",
+        "config": {"workload": (f"4D Ising HOTRG, T={T_WORK}, h={H_WORK}" if args.batch == 1 else
+                                f"4D Ising HOTRG, {args.batch * world} temperatures in [6.60, 6.72], h={hfield}")
+                               + (", pure + sigma + sigma-sigma impure tensors" if impure else "")
+                               + f", D_cut={D}, 1024^4 lattice schedule (x,y,z,t cycled); timed steps "
+                               f"{args.warmup + 1}..{nsteps} (steady state)",
+                   "dcut": D, "temperatures_per_gpu": args.batch, "impure": bool(impure), "lattice": "1024^4",
+                   "precision": "tf32x3 (fp32 storage)",
                    "l2": "operands larger than L2 (GEMM A and B: 2 x 4.3 GB per step, hi + lo)"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
@@ -350,7 +411,7 @@ def main():
                      "tensor_pipe_flops_frac": (3 * achieved / peak) if achieved else None},
         "gpu_launches": prof["launches"],
         "clocks": clk.summary(),
-        "fp64": fp64, "accuracy": accuracy, "lnZ_over_V_after_timed_steps": lnz_run,
+        "fp64": fp64, "accuracy": accuracy, "lnZ_over_V_after_timed_steps": lnz_run, "observables": obs,
         "cpu_baseline": cpu, "e2e": e2e,
     }
     if rank == 0:

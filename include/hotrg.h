@@ -71,6 +71,8 @@ typedef struct {
   double eps[4][2];  /* per transverse nu: discarded eigenvalue sum, nu and nu' side   */
   double ln_c;       /* ln of the Frobenius norm of the new tensor before normalising */
   int degenerate[4]; /* per transverse nu: the cut fell inside an eigenvalue cluster   */
+  int slices[2];     /* slices of the new a leg taken for A (rows) and for B (rows) when
+                        the workspace was smaller than the unsliced plan (1 = unsliced) */
 } hotrg_step_record;
 
 /* Create a context for `batch` runs with bond dimensions up to `dcut_max`

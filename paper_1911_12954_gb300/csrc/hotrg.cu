@@ -55,7 +55,8 @@ struct StepPlan {
   int64_t rowsA_full;     // xs = chi_a
   int64_t rowsB;          // chi_a chi_b Dc^2 Dmu
   int64_t K, ldk;         // Da^2 Db^2 Dmu, padded to 4
-  int xs;                 // X values per slice
+  int xs;                 // X values per slice (rows of A and C)
+  int xs2;                // X' values per slice (rows of B, columns of C)
   // Gram
   int R[4];               // rows of the half-Gram per direction = D_nu D_mu
   int Rmax, nmax, nchunks;
@@ -86,6 +87,7 @@ struct hotrg_ctx {
   int k = 0;
   int dims[4] = {2, 2, 2, 2};
   int mu_hist[kMaxSteps];
+  int slices_hist[kMaxSteps][2];
   int dims_hist[kMaxSteps][4];
   int cur = 0;               // which tensor buffer holds the current tensors
   int last_chi[4] = {0, 0, 0, 0};
@@ -216,6 +218,7 @@ StepPlan make_plan(const int D[4], int mu, int dcut) {
   p.K = (int64_t)Da * Da * Db * Db * Dm;
   p.ldk = (p.K + 3) / 4 * 4;
   p.xs = p.chi[p.a];
+  p.xs2 = p.chi[p.a];
   p.Rmax = 0;
   p.nmax = 0;
   for (int n = 0; n < 4; ++n) {
@@ -248,14 +251,14 @@ StepPlan make_plan(const int D[4], int mu, int dcut) {
 
 int ntensors(int impure) { return (impure & HOTRG_IMPURE_SIGMASIGMA) ? 3 : ((impure & HOTRG_IMPURE_SIGMA) ? 2 : 1); }
 
-// Scratch bytes of one step with slice size xs.
+// Scratch bytes of one step with slice sizes xs (new X) and xs2 (new X').
 struct Scratch {
   size_t gpart, npart, gA, G, jwork, lam, eps, degen, Uside;
   size_t O1A, A, Alo, O1B, B, Blo, C, O3;
   size_t total;
 };
 
-Scratch scratch_layout(const StepPlan& p, int xs, int prec, int impure, size_t rs) {
+Scratch scratch_layout(const StepPlan& p, int xs, int xs2, int prec, int impure, size_t rs) {
   Scratch s{};
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -274,15 +277,16 @@ Scratch scratch_layout(const StepPlan& p, int xs, int prec, int impure, size_t r
   s.degen = take(6 * 4);
   s.Uside = take((size_t)6 * p.nmax * kMaxLeg * 8);
   const int64_t rowsA = (int64_t)xs * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[p.mu];
+  const int64_t rowsB = (int64_t)xs2 * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[p.mu];
   const bool split = prec == HOTRG_TF32X3;
   s.O1A = take((size_t)xs * p.E * rs);
   s.A = take((size_t)nt * rowsA * p.ldk * rs);
   s.Alo = split ? take((size_t)nt * rowsA * p.ldk * rs) : 0;
-  s.O1B = take((size_t)p.chi[p.a] * p.E * rs);
-  s.B = take((size_t)nt * p.rowsB * p.ldk * rs);
-  s.Blo = split ? take((size_t)nt * p.rowsB * p.ldk * rs) : 0;
-  s.C = take((size_t)nt * rowsA * p.rowsB * rs);
-  s.O3 = take((size_t)rowsA * p.rowsB / (p.D[p.c] * p.D[p.c]) * p.chi[p.c] * rs);
+  s.O1B = take((size_t)xs2 * p.E * rs);
+  s.B = take((size_t)nt * rowsB * p.ldk * rs);
+  s.Blo = split ? take((size_t)nt * rowsB * p.ldk * rs) : 0;
+  s.C = take((size_t)nt * rowsA * rowsB * rs);
+  s.O3 = take((size_t)rowsA * rowsB / (p.D[p.c] * p.D[p.c]) * p.chi[p.c] * rs);
   s.total = off;
   return s;
 }
@@ -431,19 +435,19 @@ hotrg_status build_A(hotrg_ctx* ctx, const StepPlan& p, const R* P, const R* Ua,
 }
 
 template <typename R>
-hotrg_status build_B(hotrg_ctx* ctx, const StepPlan& p, const R* Q, const R* Ua, const R* Ub, R* O1, R* B, R* Blo,
-                     cudaStream_t st) {
+hotrg_status build_B(hotrg_ctx* ctx, const StepPlan& p, const R* Q, const R* Ua, const R* Ub, int x0, int xs,
+                     R* O1, R* B, R* Blo, cudaStream_t st) {
   const int mu = p.mu, a = p.a, b = p.b, c = p.c;
   const int Da = p.D[a], Db = p.D[b], Dc = p.D[c], Dm = p.D[mu];
   const int ca = p.chi[a], cb = p.chi[b];
   int64_t ts[8];
   canon_strides(p.D, ts);
-  // O1[X', b2', c2, c2', mu2', a2, b2, a1', k] = sum_a2' U^a[a1', a2', X'] Q[...]
-  const std::vector<int64_t> on = {ca, Db, Dc, Dc, Dm, Da, Db, Da, Dm};
+  // O1[X', b2', c2, c2', mu2', a2, b2, a1', k] = sum_a2' U^a[a1', a2', X'] Q[...], X' in [x0, x0 + xs)
+  const std::vector<int64_t> on = {xs, Db, Dc, Dc, Dm, Da, Db, Da, Dm};
   const std::vector<int64_t> os = rm_strides(on);
   {
     std::vector<Dim> d = {
-        {ca, 0, 1, os[0]},                       // X'
+        {xs, 0, 1, os[0]},                       // X'  (U col X', offset x0 on U)
         {Db, ts[2 * b + 1], 0, os[1]},           // b2'
         {Dc, ts[2 * c], 0, os[2]},               // c2
         {Dc, ts[2 * c + 1], 0, os[3]},           // c2'
@@ -454,17 +458,17 @@ hotrg_status build_B(hotrg_ctx* ctx, const StepPlan& p, const R* Q, const R* Ua,
         {Dm, ts[2 * mu], 0, os[8]},              // k = T2.mu
     };
     TTMArgs t = make_ttm(d, Da, ts[2 * a + 1], ca, 1, 0, 0, 1.0, 0.0);
-    ttm_limits(p.E, (int64_t)Da * Da * ca, (int64_t)ca * p.E);
-    LK(1, launch_ttm_r<R>(Q, Ua, O1, nullptr, t, kTTMStore, st), "ttm B1");
+    ttm_limits(p.E, (int64_t)Da * Da * ca - x0, (int64_t)xs * p.E);
+    LK(1, launch_ttm_r<R>(Q, Ua + x0, O1, nullptr, t, kTTMStore, st), "ttm B1");
   }
   {
     const int64_t ld = p.ldk;
-    const std::vector<int64_t> rn = {ca, cb, Dc, Dc, Dm};
+    const std::vector<int64_t> rn = {xs, cb, Dc, Dc, Dm};
     const std::vector<int64_t> rs = rm_strides(rn);
     const std::vector<int64_t> kn = {Da, Db, Da, Db, Dm};
     const std::vector<int64_t> ks = rm_strides(kn);
     std::vector<Dim> d = {
-        {ca, os[0], 0, rs[0] * ld},             // X'
+        {xs, os[0], 0, rs[0] * ld},             // X'
         {cb, 0, 1, rs[1] * ld},                 // Y'
         {Dc, os[2], 0, rs[2] * ld},             // c2
         {Dc, os[3], 0, rs[3] * ld},             // c2'
@@ -477,7 +481,7 @@ hotrg_status build_B(hotrg_ctx* ctx, const StepPlan& p, const R* Q, const R* Ua,
     };
     TTMArgs t = make_ttm(d, Db, os[1], cb, 1, 0, 0, 1.0, 0.0);
     const int mode = Blo ? kTTMSplitTF32 : kTTMStore;
-    ttm_limits((int64_t)ca * p.E, (int64_t)Db * Db * cb, p.rowsB * ld);
+    ttm_limits((int64_t)xs * p.E, (int64_t)Db * Db * cb, (int64_t)xs * cb * Dc * Dc * Dm * ld);
     LK(1, launch_ttm_r<R>(O1, Ub, B, Blo, t, mode, st), "ttm B2");
   }
   return HOTRG_OK;
@@ -485,19 +489,20 @@ hotrg_status build_B(hotrg_ctx* ctx, const StepPlan& p, const R* Q, const R* Ua,
 
 // T'[slice] = C x_{(c1 c2)} U^c x_{(c1' c2')} U^c, written into the canonical layout.
 template <typename R>
-hotrg_status close_C(hotrg_ctx* ctx, const StepPlan& p, const R* C, const R* Uc, int x0, int xs, R* O3, R* Tn,
-                     cudaStream_t st) {
+hotrg_status close_C(hotrg_ctx* ctx, const StepPlan& p, const R* C, const R* Uc, int x0, int xs, int x20, int xs2,
+                     R* O3, R* Tn, cudaStream_t st) {
   const int mu = p.mu, a = p.a, b = p.b, c = p.c;
   const int Dc = p.D[c], Dm = p.D[mu];
-  const int ca = p.chi[a], cb = p.chi[b], cc = p.chi[c];
-  const int64_t N = p.rowsB;
-  // C row m = (X, Y, c1, c1', mu1), col n = (X', Y', c2, c2', mu2')
+  const int cb = p.chi[b], cc = p.chi[c];
+  // C block: rows m = (X, Y, c1, c1', mu1), X in [x0, x0 + xs); columns n = (X', Y', c2, c2', mu2'),
+  // X' in [x20, x20 + xs2); row-major with N = its column count
+  const int64_t N = (int64_t)xs2 * cb * Dc * Dc * Dm;
   const std::vector<int64_t> mn = {xs, cb, Dc, Dc, Dm};
   const std::vector<int64_t> ms = rm_strides(mn);
-  const std::vector<int64_t> nn = {ca, cb, Dc, Dc, Dm};
+  const std::vector<int64_t> nn = {xs2, cb, Dc, Dc, Dm};
   const std::vector<int64_t> ns = rm_strides(nn);
   // O3[Z, X, Y, c1', mu1, X', Y', c2', mu2']
-  const std::vector<int64_t> on = {cc, xs, cb, Dc, Dm, ca, cb, Dc, Dm};
+  const std::vector<int64_t> on = {cc, xs, cb, Dc, Dm, xs2, cb, Dc, Dm};
   const std::vector<int64_t> os = rm_strides(on);
   {
     std::vector<Dim> d = {
@@ -506,7 +511,7 @@ hotrg_status close_C(hotrg_ctx* ctx, const StepPlan& p, const R* C, const R* Uc,
         {cb, ms[1] * N, 0, os[2]},      // Y
         {Dc, ms[3] * N, 0, os[3]},      // c1'
         {Dm, ms[4] * N, 0, os[4]},      // mu1
-        {ca, ns[0], 0, os[5]},          // X'
+        {xs2, ns[0], 0, os[5]},         // X'
         {cb, ns[1], 0, os[6]},          // Y'
         {Dc, ns[3], 0, os[7]},          // c2'
         {Dm, ns[4], 0, os[8]},          // mu2'
@@ -529,6 +534,7 @@ hotrg_status close_C(hotrg_ctx* ctx, const StepPlan& p, const R* C, const R* Uc,
             sz = xs;
             in = os[1];
           } else {
+            sz = xs2;
             in = os[5];
           }
         } else if (n == b) {
@@ -547,8 +553,8 @@ hotrg_status close_C(hotrg_ctx* ctx, const StepPlan& p, const R* C, const R* Uc,
     std::vector<Dim> d;
     for (int leg = 0; leg < 8; ++leg) d.push_back({sizes[leg], in_st[leg], u_st[leg], tn[leg]});
     TTMArgs t = make_ttm(d, Dc, os[3], (int64_t)Dc * cc, Dc, os[7], cc, 1.0, 0.0);
-    R* out = Tn + (int64_t)x0 * tn[2 * a];
-    ttm_limits(on[0] * os[0], (int64_t)Dc * Dc * cc, p.Enew - (int64_t)x0 * tn[2 * a]);
+    R* out = Tn + (int64_t)x0 * tn[2 * a] + (int64_t)x20 * tn[2 * a + 1];
+    ttm_limits(on[0] * os[0], (int64_t)Dc * Dc * cc, p.Enew - (int64_t)x0 * tn[2 * a] - (int64_t)x20 * tn[2 * a + 1]);
     LK(1, launch_ttm_r<R>(O3, Uc, out, nullptr, t, kTTMStore, st), "ttm close2");
   }
   return HOTRG_OK;
@@ -596,7 +602,7 @@ hotrg_status gemm_launch(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, c
 template <typename R>
 hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
   cudaStream_t st = ctx->stream;
-  const Scratch sc = scratch_layout(p, p.xs, ctx->prec, ctx->impure_active, ctx->rsize);
+  const Scratch sc = scratch_layout(p, p.xs, p.xs2, ctx->prec, ctx->impure_active, ctx->rsize);
   char* sb = ctx->ws + ctx->L.persistent_end;
   const int mu = p.mu;
   const int kstep = ctx->k;  // steps done before this one
@@ -604,6 +610,9 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
   const int nt = ntensors(ctx->impure_active);
   const bool split = ctx->prec == HOTRG_TF32X3;
   const int64_t rowsA = (int64_t)p.xs * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[mu];
+  const int64_t rowsB = (int64_t)p.xs2 * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[mu];
+  const int ca = p.chi[p.a];
+  const bool b_sliced = p.xs2 < ca;
 
   for (int bidx = 0; bidx < ctx->batch; ++bidx) {
     const R* T = tensor_ptr<R>(ctx, 0, ctx->cur, bidx);
@@ -718,7 +727,7 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
     R* Blob = split ? (R*)(sb + sc.Blo) : nullptr;
     R* Cbuf = (R*)(sb + sc.C);
     R* O3 = (R*)(sb + sc.O3);
-    const int64_t Asz = rowsA * p.ldk, Bsz = p.rowsB * p.ldk, Csz = rowsA * p.rowsB;
+    const int64_t Asz = rowsA * p.ldk, Bsz = rowsB * p.ldk, Csz = rowsA * rowsB;
     const R* src[3];
     R* dst[3];
     for (int w = 0; w < nt; ++w) {
@@ -734,46 +743,62 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
         CK(cudaMemsetAsync(Blob, 0, (size_t)nt * Bsz * ctx->rsize, st), "memset Blo");
       }
     }
-    for (int w = 0; w < nt; ++w) {
-      hotrg_status s = build_B<R>(ctx, p, src[w], Ua, Ub, O1B, Bbuf + w * Bsz, split ? Blob + w * Bsz : nullptr, st);
+    auto buildB = [&](int x20, int xs2) -> hotrg_status {
+      for (int w = 0; w < nt; ++w) {
+        hotrg_status s = build_B<R>(ctx, p, src[w], Ua, Ub, x20, xs2, O1B, Bbuf + w * Bsz,
+                                    split ? Blob + w * Bsz : nullptr, st);
+        if (s != HOTRG_OK) return s;
+      }
+      return HOTRG_OK;
+    };
+    if (!b_sliced) {
+      hotrg_status s = buildB(0, ca);
       if (s != HOTRG_OK) return s;
     }
-    for (int x0 = 0; x0 < p.chi[p.a]; x0 += p.xs) {
-      const int xs = std::min(p.xs, p.chi[p.a] - x0);
+    for (int x0 = 0; x0 < ca; x0 += p.xs) {
+      const int xs = std::min(p.xs, ca - x0);
       const int64_t rA = (int64_t)xs * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[mu];
       for (int w = 0; w < nt; ++w) {
         hotrg_status s = build_A<R>(ctx, p, src[w], Ua, Ub, x0, xs, O1A, Abuf + w * Asz,
                                     split ? Alob + w * Asz : nullptr, st);
         if (s != HOTRG_OK) return s;
       }
-      auto Ap = [&](int w) { return Abuf + w * Asz; };
-      auto Alp = [&](int w) { return split ? Alob + w * Asz : nullptr; };
-      auto Bp = [&](int w) { return Bbuf + w * Bsz; };
-      auto Blp = [&](int w) { return split ? Blob + w * Bsz : nullptr; };
-      hotrg_status s;
-      // C_T = A(T) B(T)^T
-      s = gemm<R>(ctx, Ap(0), Alp(0), Bp(0), Blp(0), p.ldk, Cbuf, rA, p.rowsB, p.K, 1.0, 0.0, st);
-      if (s != HOTRG_OK) return s;
-      if (nt >= 2) {  // C_S = (A(S) B(T)^T + A(T) B(S)^T) / 2
-        s = gemm<R>(ctx, Ap(1), Alp(1), Bp(0), Blp(0), p.ldk, Cbuf + Csz, rA, p.rowsB, p.K, 0.5, 0.0, st);
-        if (s != HOTRG_OK) return s;
-        s = gemm<R>(ctx, Ap(0), Alp(0), Bp(1), Blp(1), p.ldk, Cbuf + Csz, rA, p.rowsB, p.K, 0.5, 1.0, st);
-        if (s != HOTRG_OK) return s;
-      }
-      if (nt >= 3) {
-        if (kstep == 0) {  // M_1 = A(S) B(S)^T: the nearest-neighbour pair inside the first block
-          s = gemm<R>(ctx, Ap(1), Alp(1), Bp(1), Blp(1), p.ldk, Cbuf + 2 * Csz, rA, p.rowsB, p.K, 1.0, 0.0, st);
-          if (s != HOTRG_OK) return s;
-        } else {           // M' = (A(M) B(T)^T + A(T) B(M)^T) / 2
-          s = gemm<R>(ctx, Ap(2), Alp(2), Bp(0), Blp(0), p.ldk, Cbuf + 2 * Csz, rA, p.rowsB, p.K, 0.5, 0.0, st);
-          if (s != HOTRG_OK) return s;
-          s = gemm<R>(ctx, Ap(0), Alp(0), Bp(2), Blp(2), p.ldk, Cbuf + 2 * Csz, rA, p.rowsB, p.K, 0.5, 1.0, st);
+      for (int x20 = 0; x20 < ca; x20 += p.xs2) {
+        const int xs2 = std::min(p.xs2, ca - x20);
+        const int64_t rB = (int64_t)xs2 * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[mu];
+        if (b_sliced) {
+          hotrg_status s = buildB(x20, xs2);
           if (s != HOTRG_OK) return s;
         }
-      }
-      for (int w = 0; w < nt; ++w) {
-        s = close_C<R>(ctx, p, Cbuf + w * Csz, Uc, x0, xs, O3, dst[w], st);
+        auto Ap = [&](int w) { return Abuf + w * Asz; };
+        auto Alp = [&](int w) { return split ? Alob + w * Asz : nullptr; };
+        auto Bp = [&](int w) { return Bbuf + w * Bsz; };
+        auto Blp = [&](int w) { return split ? Blob + w * Bsz : nullptr; };
+        hotrg_status s;
+        // C_T = A(T) B(T)^T
+        s = gemm<R>(ctx, Ap(0), Alp(0), Bp(0), Blp(0), p.ldk, Cbuf, rA, rB, p.K, 1.0, 0.0, st);
         if (s != HOTRG_OK) return s;
+        if (nt >= 2) {  // C_S = (A(S) B(T)^T + A(T) B(S)^T) / 2
+          s = gemm<R>(ctx, Ap(1), Alp(1), Bp(0), Blp(0), p.ldk, Cbuf + Csz, rA, rB, p.K, 0.5, 0.0, st);
+          if (s != HOTRG_OK) return s;
+          s = gemm<R>(ctx, Ap(0), Alp(0), Bp(1), Blp(1), p.ldk, Cbuf + Csz, rA, rB, p.K, 0.5, 1.0, st);
+          if (s != HOTRG_OK) return s;
+        }
+        if (nt >= 3) {
+          if (kstep == 0) {  // M_1 = A(S) B(S)^T: the nearest-neighbour pair inside the first block
+            s = gemm<R>(ctx, Ap(1), Alp(1), Bp(1), Blp(1), p.ldk, Cbuf + 2 * Csz, rA, rB, p.K, 1.0, 0.0, st);
+            if (s != HOTRG_OK) return s;
+          } else {           // M' = (A(M) B(T)^T + A(T) B(M)^T) / 2
+            s = gemm<R>(ctx, Ap(2), Alp(2), Bp(0), Blp(0), p.ldk, Cbuf + 2 * Csz, rA, rB, p.K, 0.5, 0.0, st);
+            if (s != HOTRG_OK) return s;
+            s = gemm<R>(ctx, Ap(0), Alp(0), Bp(2), Blp(2), p.ldk, Cbuf + 2 * Csz, rA, rB, p.K, 0.5, 1.0, st);
+            if (s != HOTRG_OK) return s;
+          }
+        }
+        for (int w = 0; w < nt; ++w) {
+          s = close_C<R>(ctx, p, Cbuf + w * Csz, Uc, x0, xs, x20, xs2, O3, dst[w], st);
+          if (s != HOTRG_OK) return s;
+        }
       }
     }
     // ---------------------------------------------------------------- 4. normalise
@@ -864,13 +889,13 @@ hotrg_status hotrg_workspace_size(hotrg_ctx* ctx, int nsteps, const int* dirs, c
   if (nsteps == 0) {
     int Dm[4] = {ctx->dcut_max, ctx->dcut_max, ctx->dcut_max, ctx->dcut_max};
     StepPlan p = make_plan(Dm, 0, ctx->dcut_max);
-    scratch = scratch_layout(p, p.xs, ctx->prec, ctx->impure, ctx->rsize).total;
+    scratch = scratch_layout(p, p.xs, p.xs2, ctx->prec, ctx->impure, ctx->rsize).total;
     cap = std::max(cap, tensor_elems(Dm));
   } else {
     for (int i = 0; i < nsteps; ++i) {
       if (dirs[i] < 0 || dirs[i] > 3 || dcuts[i] < 1 || dcuts[i] > ctx->dcut_max) return HOTRG_EINVAL;
       StepPlan p = make_plan(D, dirs[i], dcuts[i]);
-      scratch = std::max(scratch, scratch_layout(p, p.xs, ctx->prec, ctx->impure, ctx->rsize).total);
+      scratch = std::max(scratch, scratch_layout(p, p.xs, p.xs2, ctx->prec, ctx->impure, ctx->rsize).total);
       for (int n = 0; n < 4; ++n) {
         D[n] = p.newD[n];
         if (D[n] > kMaxLeg) return HOTRG_EINVAL;
@@ -996,15 +1021,32 @@ hotrg_status hotrg_step(hotrg_ctx* ctx, int dir, int dcut) {
   for (int n = 0; n < 4; ++n)
     if (p.newD[n] > kMaxLeg) return HOTRG_EINVAL;
   if (p.Enew > ctx->L.cap) return HOTRG_EWORKSPACE;
-  // largest X slice whose scratch fits
+  // slice sizes (X for A and C rows, X' for B rows and C columns): the pair that fits with
+  // the fewest GEMM blocks, then the largest X' slice
   const size_t avail = ctx->ws_bytes - ctx->L.persistent_end;
-  int xs = p.chi[p.a];
-  while (xs > 1 && scratch_layout(p, xs, ctx->prec, ctx->impure_active, ctx->rsize).total > avail) --xs;
-  if (scratch_layout(p, xs, ctx->prec, ctx->impure_active, ctx->rsize).total > avail) return HOTRG_EWORKSPACE;
-  p.xs = xs;
+  const int ca = p.chi[p.a];
+  int best_xs = 0, best_xs2 = 0;
+  int64_t best_blocks = -1;
+  for (int xs = ca; xs >= 1; --xs) {
+    for (int xs2 = ca; xs2 >= 1; --xs2) {
+      if (scratch_layout(p, xs, xs2, ctx->prec, ctx->impure_active, ctx->rsize).total > avail) continue;
+      const int64_t blocks = (int64_t)((ca + xs - 1) / xs) * ((ca + xs2 - 1) / xs2);
+      if (best_blocks < 0 || blocks < best_blocks || (blocks == best_blocks && xs2 > best_xs2)) {
+        best_blocks = blocks;
+        best_xs = xs;
+        best_xs2 = xs2;
+      }
+      break;  // smaller xs2 only adds blocks for this xs
+    }
+  }
+  if (best_blocks < 0) return HOTRG_EWORKSPACE;
+  p.xs = best_xs;
+  p.xs2 = best_xs2;
   hotrg_status s = ctx->prec == HOTRG_FP64 ? do_step<double>(ctx, p) : do_step<float>(ctx, p);
   if (s != HOTRG_OK) return s;
   ctx->mu_hist[ctx->k] = dir;
+  ctx->slices_hist[ctx->k][0] = (p.chi[p.a] + p.xs - 1) / p.xs;
+  ctx->slices_hist[ctx->k][1] = (p.chi[p.a] + p.xs2 - 1) / p.xs2;
   for (int n = 0; n < 4; ++n) {
     ctx->dims_hist[ctx->k][n] = p.newD[n];
     ctx->dims[n] = p.newD[n];
@@ -1102,6 +1144,8 @@ hotrg_status hotrg_step_info(hotrg_ctx* ctx, int b, int step, hotrg_step_record*
     rec->eps[n][1] = d.eps[n][1];
   }
   rec->ln_c = d.ln_c;
+  rec->slices[0] = ctx->slices_hist[step - 1][0];
+  rec->slices[1] = ctx->slices_hist[step - 1][1];
   return HOTRG_OK;
 }
 

@@ -35,7 +35,7 @@ class HotrgError(RuntimeError):
 class StepRecord(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_int), ("dims", ctypes.c_int * 4), ("primed", ctypes.c_int * 4),
                 ("eps", (ctypes.c_double * 2) * 4), ("ln_c", ctypes.c_double),
-                ("degenerate", ctypes.c_int * 4)]
+                ("degenerate", ctypes.c_int * 4), ("slices", ctypes.c_int * 2)]
 
 
 class Profile(ctypes.Structure):
@@ -141,6 +141,11 @@ class HOTRG:
         nbytes = self.workspace_size(schedule, dims0)
         if workspace_bytes is not None:
             nbytes = int(workspace_bytes)
+        else:
+            # the unsliced plan may exceed the device: give what is free, the steps slice
+            free, _ = torch.cuda.mem_get_info(self.device)
+            cap = int(free * 0.92) // 256 * 256
+            nbytes = min(nbytes, cap)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         _check(self.lib.hotrg_set_workspace(self.ctx, ctypes.c_void_p(self.workspace.data_ptr()), nbytes),
                "set_workspace")
@@ -207,7 +212,7 @@ class HOTRG:
         _check(self.lib.hotrg_step_info(self.ctx, b, step, ctypes.byref(r)), "step_info")
         return dict(mu=r.mu, dims=tuple(r.dims), primed=tuple(r.primed),
                     eps=tuple(tuple(r.eps[n]) for n in range(4)), ln_c=r.ln_c,
-                    degenerate=tuple(r.degenerate))
+                    degenerate=tuple(r.degenerate), slices=tuple(r.slices))
 
     def tensor(self, which: int = 0, b: int = 0) -> np.ndarray:
         _, dims = self.state()

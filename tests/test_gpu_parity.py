@@ -116,6 +116,45 @@ def test_sliced_contraction_matches_unsliced():
     assert np.allclose(small.tensor(), full.tensor(), atol=1e-14)
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-14), ("tf32x3", 1e-6)])
+def test_two_dimensional_slicing_matches_unsliced(prec, tol):
+    """Workspaces between the smallest that works and the unsliced plan make the step
+    slice the new X (rows of A) and then also the new X' (rows of B, columns of C); every
+    slicing gives the unsliced tensor, and a workspace below the smallest is refused."""
+    from paper_1911_12954_gb300 import HotrgError
+    dims, mu, dcut = (4, 2, 4, 2), 2, 9
+    T = random_tensor(78, dims)
+
+    def run(nbytes):
+        g = _gpu(batch=1, dcut_max=9, precision=prec, schedule=[(mu, dcut)], dims0=dims, workspace_bytes=nbytes)
+        g.set_tensor(T)
+        g.step(mu, dcut)
+        return g.tensor(), g.step_info(1)["slices"]
+
+    full = _gpu(batch=1, dcut_max=9, precision=prec, schedule=[(mu, dcut)], dims0=dims)
+    need = full.workspace_size([(mu, dcut)], dims)
+    ref, sl = run(need)
+    assert sl == (1, 1)
+    lo, hi = 0, need                      # smallest workspace that runs, by bisection
+    while hi - lo > 4096:
+        mid = (lo + hi) // 2 // 256 * 256
+        try:
+            run(mid)
+            hi = mid
+        except HotrgError as e:
+            assert "EWORKSPACE" in str(e)
+            lo = mid
+    seen = set()
+    for frac in (0.0, 0.1, 0.25, 0.5, 0.75):
+        nbytes = (hi + int((need - hi) * frac)) // 256 * 256 + 256
+        Tn, sl = run(nbytes)
+        seen.add(sl)
+        assert np.allclose(Tn, ref, atol=tol * np.abs(ref).max()), (frac, sl)
+    assert any(a > 1 and b > 1 for a, b in seen), seen
+    with pytest.raises(HotrgError, match="EWORKSPACE"):
+        run(lo // 256 * 256)
+
+
 # ------------------------------------------------------------------ Ising runs
 def test_untruncated_two_steps_impure_vs_oracle():
     """Two untruncated steps (dims 4,4,16,16) = the exactly enumerable 2x2x1x1 lattice."""
