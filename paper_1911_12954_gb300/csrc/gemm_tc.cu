@@ -107,11 +107,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* sta
   }
 }
 
-__device__ __forceinline__ void tma_load(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
+// Operands are stored in K panels: element (row, k) with k = p Kp + kin sits at
+// [(p rows + row) kps + kin] (kps = Kp rounded up to 4). The 3D tensor map is
+// {Kp, rows, P}; a panel keeps the rows of one k range contiguous, so a box of 128 rows
+// spans at most a few pages even when K is in the hundreds of thousands.
+__device__ __forceinline__ void tma_load(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y, int z) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
-          "r"(su32(dst)),
-      "l"((uint64_t)map), "r"(su32(bar)), "r"(x), "r"(y)
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+      "[%2];" ::"r"(su32(dst)),
+      "l"((uint64_t)map), "r"(su32(bar)), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
 
@@ -171,7 +175,7 @@ template <class CF>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                        const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
-                       float* __restrict__ C, int64_t ldc, int M, int N, int K, float alpha, float beta,
+                       float* __restrict__ C, int64_t ldc, int M, int N, int Kp, int P, float alpha, float beta,
                        int* status) {
   constexpr int STAGES = CF::STAGES, BK = CF::BK, A_BYTES = CF::A_BYTES, B_BYTES = CF::B_BYTES,
                 STAGE_BYTES = CF::STAGE_BYTES, KPC = CF::KB_PER_CHUNK;
@@ -188,7 +192,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
   const int ntiles = tiles_m * tiles_n;
-  const int nkb = (K + BK - 1) / BK;
+  const int nkbp = (Kp + BK - 1) / BK;   // k-blocks per panel (the last one zero-filled past Kp)
+  const int nkb = P * nkbp;
   const int nchunk = (nkb + KPC - 1) / KPC;
 
   if (threadIdx.x == 0) {
@@ -233,11 +238,12 @@ __global__ void __launch_bounds__(THREADS, 1)
           break;
         }
         uint8_t* st = smem + s * STAGE_BYTES;
+        const int pn = kb / nkbp, kx = (kb - pn * nkbp) * BK;
         mbar_expect_tx(&full[s], STAGE_BYTES);
-        tma_load(&mAhi, &full[s], st, kb * BK, tm * BM);
-        tma_load(&mAlo, &full[s], st + A_BYTES, kb * BK, tm * BM);
-        tma_load(&mBhi, &full[s], st + 2 * A_BYTES, kb * BK, tn * BN);
-        tma_load(&mBlo, &full[s], st + 2 * A_BYTES + B_BYTES, kb * BK, tn * BN);
+        tma_load(&mAhi, &full[s], st, kx, tm * BM, pn);
+        tma_load(&mAlo, &full[s], st + A_BYTES, kx, tm * BM, pn);
+        tma_load(&mBhi, &full[s], st + 2 * A_BYTES, kx, tn * BN, pn);
+        tma_load(&mBlo, &full[s], st + 2 * A_BYTES + B_BYTES, kx, tn * BN, pn);
         ++issued[s];
         if (++s == STAGES) {
           s = 0;
@@ -374,26 +380,27 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-bool make_map(CUtensorMap* map, const float* ptr, int64_t rows, int64_t K, int64_t ld, int box_rows, int bk) {
+bool make_map(CUtensorMap* map, const float* ptr, int64_t rows, int64_t Kp, int64_t kps, int64_t P, int box_rows,
+              int bk) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
-  cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)box_rows};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)ptr, dims, strides, box, estr,
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)P};
+  cuuint64_t strides[2] = {(cuuint64_t)(kps * 4), (cuuint64_t)(rows * kps * 4)};
+  cuuint32_t box[3] = {(cuuint32_t)bk, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)ptr, dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, bk == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
 template <class CF>
-cudaError_t launch_variant(const float* Ahi, const float* Alo, int64_t lda, const float* Bhi, const float* Blo,
-                           int64_t ldb, float* C, int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha,
+cudaError_t launch_variant(const float* Ahi, const float* Alo, const float* Bhi, const float* Blo, int64_t Kp,
+                           int64_t kps, int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha,
                            float beta, int* status, cudaStream_t st) {
   CUtensorMap mAhi, mAlo, mBhi, mBlo;
-  if (!make_map(&mAhi, Ahi, M, K, lda, BM, CF::BK) || !make_map(&mAlo, Alo, M, K, lda, BM, CF::BK) ||
-      !make_map(&mBhi, Bhi, N, K, ldb, BN, CF::BK) || !make_map(&mBlo, Blo, N, K, ldb, BN, CF::BK))
+  if (!make_map(&mAhi, Ahi, M, Kp, kps, P, BM, CF::BK) || !make_map(&mAlo, Alo, M, Kp, kps, P, BM, CF::BK) ||
+      !make_map(&mBhi, Bhi, N, Kp, kps, P, BN, CF::BK) || !make_map(&mBlo, Blo, N, Kp, kps, P, BN, CF::BK))
     return cudaErrorInvalidValue;
   static int sms = 0;
   static bool attr = false;
@@ -411,31 +418,33 @@ cudaError_t launch_variant(const float* Ahi, const float* Alo, int64_t lda, cons
   const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
   const int grid = (int)(tiles < sms ? tiles : sms);
   gemm_tf32x3_kernel<CF><<<grid, THREADS, CF::SMEM_BYTES, st>>>(mAhi, mAlo, mBhi, mBlo, C, ldc, (int)M, (int)N,
-                                                               (int)K, alpha, beta, status);
+                                                               (int)Kp, (int)P, alpha, beta, status);
   return cudaGetLastError();
 }
 
 }  // namespace tc
 
-// variant 0 (default): k-blocks of 16, 64-byte swizzle, 4 stages; variant 1: k-blocks of
-// 32, 128-byte swizzle, 2 stages.
-cudaError_t launch_gemm_tf32x3_v(const float* Ahi, const float* Alo, int64_t lda, const float* Bhi,
-                                 const float* Blo, int64_t ldb, float* C, int64_t ldc, int64_t M, int64_t N,
-                                 int64_t K, float alpha, float beta, int* status, cudaStream_t st, int variant) {
+// C[M][N] (ldc) = alpha * A B^T + beta * C with A, B in K panels (see tma_load): panel
+// width Kp (kps = its stride, a multiple of 4), P panels, K = P Kp. P = 1, kps = ld is the
+// plain row-major K-major layout. variant 0 (default): k-blocks of 16, 64-byte swizzle,
+// 4 stages; variant 1: k-blocks of 32, 128-byte swizzle, 2 stages.
+cudaError_t launch_gemm_tf32x3_v(const float* Ahi, const float* Alo, const float* Bhi, const float* Blo, int64_t Kp,
+                                 int64_t kps, int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha,
+                                 float beta, int* status, cudaStream_t st, int variant) {
   using namespace tc;
   if (M <= 0 || N <= 0) return cudaSuccess;
-  if (K <= 0 || M > 0x7fffffff || N > 0x7fffffff || K > 0x7fffffff) return cudaErrorInvalidValue;
-  if ((lda & 3) || (ldb & 3) || lda < K || ldb < K) return cudaErrorInvalidValue;
+  if (Kp <= 0 || P <= 0 || M > 0x7fffffff || N > 0x7fffffff || Kp * P > 0x7fffffff) return cudaErrorInvalidValue;
+  if ((kps & 3) || kps < Kp) return cudaErrorInvalidValue;
   if ((((uintptr_t)Ahi) | ((uintptr_t)Alo) | ((uintptr_t)Bhi) | ((uintptr_t)Blo)) & 15) return cudaErrorInvalidValue;
   if (variant == 1)
-    return launch_variant<Cfg<32>>(Ahi, Alo, lda, Bhi, Blo, ldb, C, ldc, M, N, K, alpha, beta, status, st);
-  return launch_variant<Cfg<16>>(Ahi, Alo, lda, Bhi, Blo, ldb, C, ldc, M, N, K, alpha, beta, status, st);
+    return launch_variant<Cfg<32>>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
+  return launch_variant<Cfg<16>>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
 }
 
-cudaError_t launch_gemm_tf32x3(const float* Ahi, const float* Alo, int64_t lda, const float* Bhi, const float* Blo,
-                               int64_t ldb, float* C, int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha,
+cudaError_t launch_gemm_tf32x3(const float* Ahi, const float* Alo, const float* Bhi, const float* Blo, int64_t Kp,
+                               int64_t kps, int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha,
                                float beta, int* status, cudaStream_t st) {
-  return launch_gemm_tf32x3_v(Ahi, Alo, lda, Bhi, Blo, ldb, C, ldc, M, N, K, alpha, beta, status, st, 0);
+  return launch_gemm_tf32x3_v(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st, 0);
 }
 
 }  // namespace hotrg

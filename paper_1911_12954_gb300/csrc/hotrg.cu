@@ -26,8 +26,8 @@
 #include "hotrg.h"
 
 namespace hotrg {
-cudaError_t launch_gemm_tf32x3(const float* Ahi, const float* Alo, int64_t lda, const float* Bhi, const float* Blo,
-                               int64_t ldb, float* C, int64_t ldc, int64_t M, int64_t N, int64_t K, float alpha,
+cudaError_t launch_gemm_tf32x3(const float* Ahi, const float* Alo, const float* Bhi, const float* Blo, int64_t Kp,
+                               int64_t kps, int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha,
                                float beta, int* status, cudaStream_t st);
 }
 
@@ -54,7 +54,11 @@ struct StepPlan {
   int64_t E, Enew;        // tensor elements before / after
   int64_t rowsA_full;     // xs = chi_a
   int64_t rowsB;          // chi_a chi_b Dc^2 Dmu
-  int64_t K, ldk;         // Da^2 Db^2 Dmu, padded to 4
+  int64_t K;              // Da^2 Db^2 Dmu = P Kp
+  // GEMM operands in K panels: element (row, k = p Kp + kin) at [(p rows + row) kps + kin];
+  // the panel holds the last `ksuf` of the summed legs (a2, b2, a1', b1', k)
+  int ksuf;
+  int64_t Kp, kps, P;
   int xs;                 // X values per slice (rows of A and C)
   int xs2;                // X' values per slice (rows of B, columns of C)
   // Gram
@@ -121,8 +125,8 @@ hotrg_status cuda_fail(hotrg_ctx* ctx, cudaError_t e, const char* where) {
   } while (0)
 
 template <typename R>
-hotrg_status gemm_launch(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R* Blo, int64_t ld, R* C,
-                         int64_t M, int64_t N, int64_t K, double alpha, double beta, cudaStream_t st);
+hotrg_status gemm_launch(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R* Blo, const StepPlan& p, R* C,
+                         int64_t M, int64_t N, double alpha, double beta, cudaStream_t st);
 
 // A launcher call that issues `n` kernels.
 #define LK(n, call, where)                                \
@@ -179,7 +183,7 @@ double plan_main_flops(const int D[4], const int chi[4], int mu, int a, int b, i
   return 2.0 * rows * rows * K;
 }
 
-StepPlan make_plan(const int D[4], int mu, int dcut) {
+StepPlan make_plan(const int D[4], int mu, int dcut, int prec) {
   StepPlan p{};
   p.mu = mu;
   for (int n = 0; n < 4; ++n) {
@@ -216,7 +220,22 @@ StepPlan make_plan(const int D[4], int mu, int dcut) {
   p.rowsB = (int64_t)p.chi[p.a] * p.chi[p.b] * Dc * Dc * Dm;
   p.rowsA_full = p.rowsB;
   p.K = (int64_t)Da * Da * Db * Db * Dm;
-  p.ldk = (p.K + 3) / 4 * 4;
+  {
+    // tensor-core operands: the widest panel of trailing summed legs up to 4096 values, so
+    // one box of 128 rows stays within 2 MB; CUDA-core operands: one panel, plain rows
+    const int64_t kd[5] = {Da, Db, Da, Db, Dm};
+    int64_t prod = 1;
+    p.ksuf = 0;
+    for (int q = 1; q <= 5; ++q) {
+      const int64_t next = prod * kd[5 - q];
+      if (prec == HOTRG_TF32X3 && next > 4096 && q > 1) break;
+      prod = next;
+      p.ksuf = q;
+    }
+    p.Kp = prod;
+    p.kps = (p.Kp + 3) / 4 * 4;
+    p.P = p.K / p.Kp;
+  }
   p.xs = p.chi[p.a];
   p.xs2 = p.chi[p.a];
   p.Rmax = 0;
@@ -280,11 +299,11 @@ Scratch scratch_layout(const StepPlan& p, int xs, int xs2, int prec, int impure,
   const int64_t rowsB = (int64_t)xs2 * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[p.mu];
   const bool split = prec == HOTRG_TF32X3;
   s.O1A = take((size_t)xs * p.E * rs);
-  s.A = take((size_t)nt * rowsA * p.ldk * rs);
-  s.Alo = split ? take((size_t)nt * rowsA * p.ldk * rs) : 0;
+  s.A = take((size_t)nt * p.P * rowsA * p.kps * rs);
+  s.Alo = split ? take((size_t)nt * p.P * rowsA * p.kps * rs) : 0;
   s.O1B = take((size_t)xs2 * p.E * rs);
-  s.B = take((size_t)nt * rowsB * p.ldk * rs);
-  s.Blo = split ? take((size_t)nt * rowsB * p.ldk * rs) : 0;
+  s.B = take((size_t)nt * p.P * rowsB * p.kps * rs);
+  s.Blo = split ? take((size_t)nt * p.P * rowsB * p.kps * rs) : 0;
   s.C = take((size_t)nt * rowsA * rowsB * rs);
   s.O3 = take((size_t)rowsA * rowsB / (p.D[p.c] * p.D[p.c]) * p.chi[p.c] * rs);
   s.total = off;
@@ -378,6 +397,28 @@ std::vector<int64_t> rm_strides(const std::vector<int64_t>& n) {
   return s;
 }
 
+// Output strides of the 10 legs of a GEMM operand (rows: the 5 row legs, then the summed
+// legs a2, b2, a1', b1', k) in the K-panel layout with `rows` rows per panel.
+void operand_strides(const StepPlan& p, const std::vector<int64_t>& rn, int64_t out[10]) {
+  const std::vector<int64_t> rs = rm_strides(rn);
+  int64_t rows = 1;
+  for (int64_t x : rn) rows *= x;
+  for (int i = 0; i < 5; ++i) out[i] = rs[i] * p.kps;
+  const int Da = p.D[p.a], Db = p.D[p.b], Dm = p.D[p.mu];
+  const int64_t kd[5] = {Da, Db, Da, Db, Dm};
+  const int split = 5 - p.ksuf;  // legs [0, split) select the panel, [split, 5) lie inside it
+  int64_t inner = 1;
+  for (int j = 4; j >= split; --j) {
+    out[5 + j] = inner;
+    inner *= kd[j];
+  }
+  int64_t outer = rows * p.kps;
+  for (int j = split - 1; j >= 0; --j) {
+    out[5 + j] = outer;
+    outer *= kd[j];
+  }
+}
+
 template <typename R>
 hotrg_status build_A(hotrg_ctx* ctx, const StepPlan& p, const R* P, const R* Ua, const R* Ub, int x0, int xs,
                      R* O1, R* A, R* Alo, cudaStream_t st) {
@@ -407,28 +448,23 @@ hotrg_status build_A(hotrg_ctx* ctx, const StepPlan& p, const R* P, const R* Ua,
   }
   // A[(X Y c1 c1' mu1), (a2 b2 a1' b1' k)] = sum_b1 U^b[b1, b2, Y] O1[X, b1, ...]
   {
-    const int64_t Kk = (int64_t)Da * Db * Da * Db * Dm;
-    (void)Kk;
-    const int64_t ld = p.ldk;
-    const std::vector<int64_t> rn = {xs, cb, Dc, Dc, Dm};
-    const std::vector<int64_t> rs = rm_strides(rn);
-    const std::vector<int64_t> kn = {Da, Db, Da, Db, Dm};
-    const std::vector<int64_t> ks = rm_strides(kn);
+    int64_t o[10];
+    operand_strides(p, {xs, cb, Dc, Dc, Dm}, o);
     std::vector<Dim> d = {
-        {xs, os[0], 0, rs[0] * ld},   // X
-        {cb, 0, 1, rs[1] * ld},       // Y
-        {Dc, os[2], 0, rs[2] * ld},   // c1
-        {Dc, os[3], 0, rs[3] * ld},   // c1'
-        {Dm, os[4], 0, rs[4] * ld},   // mu1
-        {Da, os[5], 0, ks[0]},        // a2
-        {Db, 0, cb, ks[1]},           // b2
-        {Da, os[6], 0, ks[2]},        // a1'
-        {Db, os[7], 0, ks[3]},        // b1'
-        {Dm, os[8], 0, ks[4]},        // k
+        {xs, os[0], 0, o[0]},   // X
+        {cb, 0, 1, o[1]},       // Y
+        {Dc, os[2], 0, o[2]},   // c1
+        {Dc, os[3], 0, o[3]},   // c1'
+        {Dm, os[4], 0, o[4]},   // mu1
+        {Da, os[5], 0, o[5]},   // a2
+        {Db, 0, cb, o[6]},      // b2
+        {Da, os[6], 0, o[7]},   // a1'
+        {Db, os[7], 0, o[8]},   // b1'
+        {Dm, os[8], 0, o[9]},   // k
     };
     TTMArgs t = make_ttm(d, Db, os[1], (int64_t)Db * cb, 1, 0, 0, 1.0, 0.0);
     const int mode = Alo ? kTTMSplitTF32 : kTTMStore;
-    ttm_limits((int64_t)xs * p.E, (int64_t)Db * Db * cb, (int64_t)xs * cb * Dc * Dc * Dm * ld);
+    ttm_limits((int64_t)xs * p.E, (int64_t)Db * Db * cb, p.P * ((int64_t)xs * cb * Dc * Dc * Dm) * p.kps);
     LK(1, launch_ttm_r<R>(O1, Ub, A, Alo, t, mode, st), "ttm A2");
   }
   return HOTRG_OK;
@@ -462,26 +498,23 @@ hotrg_status build_B(hotrg_ctx* ctx, const StepPlan& p, const R* Q, const R* Ua,
     LK(1, launch_ttm_r<R>(Q, Ua + x0, O1, nullptr, t, kTTMStore, st), "ttm B1");
   }
   {
-    const int64_t ld = p.ldk;
-    const std::vector<int64_t> rn = {xs, cb, Dc, Dc, Dm};
-    const std::vector<int64_t> rs = rm_strides(rn);
-    const std::vector<int64_t> kn = {Da, Db, Da, Db, Dm};
-    const std::vector<int64_t> ks = rm_strides(kn);
+    int64_t o[10];
+    operand_strides(p, {xs, cb, Dc, Dc, Dm}, o);
     std::vector<Dim> d = {
-        {xs, os[0], 0, rs[0] * ld},             // X'
-        {cb, 0, 1, rs[1] * ld},                 // Y'
-        {Dc, os[2], 0, rs[2] * ld},             // c2
-        {Dc, os[3], 0, rs[3] * ld},             // c2'
-        {Dm, os[4], 0, rs[4] * ld},             // mu2'
-        {Da, os[5], 0, ks[0]},                  // a2
-        {Db, os[6], 0, ks[1]},                  // b2
-        {Da, os[7], 0, ks[2]},                  // a1'
-        {Db, 0, (int64_t)Db * cb, ks[3]},       // b1'
-        {Dm, os[8], 0, ks[4]},                  // k
+        {xs, os[0], 0, o[0]},                   // X'
+        {cb, 0, 1, o[1]},                       // Y'
+        {Dc, os[2], 0, o[2]},                   // c2
+        {Dc, os[3], 0, o[3]},                   // c2'
+        {Dm, os[4], 0, o[4]},                   // mu2'
+        {Da, os[5], 0, o[5]},                   // a2
+        {Db, os[6], 0, o[6]},                   // b2
+        {Da, os[7], 0, o[7]},                   // a1'
+        {Db, 0, (int64_t)Db * cb, o[8]},        // b1'
+        {Dm, os[8], 0, o[9]},                   // k
     };
     TTMArgs t = make_ttm(d, Db, os[1], cb, 1, 0, 0, 1.0, 0.0);
     const int mode = Blo ? kTTMSplitTF32 : kTTMStore;
-    ttm_limits((int64_t)xs * p.E, (int64_t)Db * Db * cb, (int64_t)xs * cb * Dc * Dc * Dm * ld);
+    ttm_limits((int64_t)xs * p.E, (int64_t)Db * Db * cb, p.P * ((int64_t)xs * cb * Dc * Dc * Dm) * p.kps);
     LK(1, launch_ttm_r<R>(O1, Ub, B, Blo, t, mode, st), "ttm B2");
   }
   return HOTRG_OK;
@@ -561,8 +594,9 @@ hotrg_status close_C(hotrg_ctx* ctx, const StepPlan& p, const R* C, const R* Uc,
 }
 
 template <typename R>
-hotrg_status gemm(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R* Blo, int64_t ld, R* C, int64_t M,
-                  int64_t N, int64_t K, double alpha, double beta, cudaStream_t st) {
+hotrg_status gemm(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R* Blo, const StepPlan& p, R* C,
+                  int64_t M, int64_t N, double alpha, double beta, cudaStream_t st) {
+  const int64_t K = p.K;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (ctx->profiling) {
     while (ctx->ev.size() < ctx->ev_used + 2) {
@@ -575,7 +609,7 @@ hotrg_status gemm(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R*
     ctx->ev_used += 2;
     CK(cudaEventRecord(e0, st), "event record");
   }
-  hotrg_status r = gemm_launch<R>(ctx, A, Alo, B, Blo, ld, C, M, N, K, alpha, beta, st);
+  hotrg_status r = gemm_launch<R>(ctx, A, Alo, B, Blo, p, C, M, N, alpha, beta, st);
   if (r != HOTRG_OK) return r;
   ctx->launches += 1;
   if (ctx->profiling) {
@@ -587,14 +621,15 @@ hotrg_status gemm(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R*
 }
 
 template <typename R>
-hotrg_status gemm_launch(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R* Blo, int64_t ld, R* C,
-                         int64_t M, int64_t N, int64_t K, double alpha, double beta, cudaStream_t st) {
+hotrg_status gemm_launch(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R* Blo, const StepPlan& p, R* C,
+                         int64_t M, int64_t N, double alpha, double beta, cudaStream_t st) {
   if (ctx->prec == HOTRG_TF32X3) {
-    CK(launch_gemm_tf32x3((const float*)A, (const float*)Alo, ld, (const float*)B, (const float*)Blo, ld, (float*)C,
-                          N, M, N, K, (float)alpha, (float)beta, (int*)(ctx->ws + ctx->L.status), st),
+    CK(launch_gemm_tf32x3((const float*)A, (const float*)Alo, (const float*)B, (const float*)Blo, p.Kp, p.kps, p.P,
+                          (float*)C, N, M, N, (float)alpha, (float)beta, (int*)(ctx->ws + ctx->L.status), st),
        "gemm tf32x3");
   } else {
-    CK(launch_gemm_simt<R>(A, ld, B, ld, C, N, M, N, K, alpha, beta, st), "gemm simt");
+    if (p.P != 1) return HOTRG_EUNSUPPORTED;
+    CK(launch_gemm_simt<R>(A, p.kps, B, p.kps, C, N, M, N, p.K, alpha, beta, st), "gemm simt");
   }
   return HOTRG_OK;
 }
@@ -727,22 +762,15 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
     R* Blob = split ? (R*)(sb + sc.Blo) : nullptr;
     R* Cbuf = (R*)(sb + sc.C);
     R* O3 = (R*)(sb + sc.O3);
-    const int64_t Asz = rowsA * p.ldk, Bsz = rowsB * p.ldk, Csz = rowsA * rowsB;
+    const int64_t Asz = p.P * rowsA * p.kps, Bsz = p.P * rowsB * p.kps, Csz = rowsA * rowsB;
     const R* src[3];
     R* dst[3];
     for (int w = 0; w < nt; ++w) {
       src[w] = tensor_ptr<R>(ctx, w, ctx->cur, bidx);
       dst[w] = tensor_ptr<R>(ctx, w, 1 - ctx->cur, bidx);
     }
-    // zero the padding columns of A and B (read by nothing when ldk == K)
-    if (p.ldk != p.K) {
-      CK(cudaMemsetAsync(Abuf, 0, (size_t)nt * Asz * ctx->rsize, st), "memset A");
-      CK(cudaMemsetAsync(Bbuf, 0, (size_t)nt * Bsz * ctx->rsize, st), "memset B");
-      if (split) {
-        CK(cudaMemsetAsync(Alob, 0, (size_t)nt * Asz * ctx->rsize, st), "memset Alo");
-        CK(cudaMemsetAsync(Blob, 0, (size_t)nt * Bsz * ctx->rsize, st), "memset Blo");
-      }
-    }
+    // Padding columns of a panel (kin >= Kp) are never read: the tensor maps stop at Kp and
+    // the CUDA-core GEMM at K, so the operand buffers need no clearing.
     auto buildB = [&](int x20, int xs2) -> hotrg_status {
       for (int w = 0; w < nt; ++w) {
         hotrg_status s = build_B<R>(ctx, p, src[w], Ua, Ub, x20, xs2, O1B, Bbuf + w * Bsz,
@@ -776,22 +804,22 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
         auto Blp = [&](int w) { return split ? Blob + w * Bsz : nullptr; };
         hotrg_status s;
         // C_T = A(T) B(T)^T
-        s = gemm<R>(ctx, Ap(0), Alp(0), Bp(0), Blp(0), p.ldk, Cbuf, rA, rB, p.K, 1.0, 0.0, st);
+        s = gemm<R>(ctx, Ap(0), Alp(0), Bp(0), Blp(0), p, Cbuf, rA, rB, 1.0, 0.0, st);
         if (s != HOTRG_OK) return s;
         if (nt >= 2) {  // C_S = (A(S) B(T)^T + A(T) B(S)^T) / 2
-          s = gemm<R>(ctx, Ap(1), Alp(1), Bp(0), Blp(0), p.ldk, Cbuf + Csz, rA, rB, p.K, 0.5, 0.0, st);
+          s = gemm<R>(ctx, Ap(1), Alp(1), Bp(0), Blp(0), p, Cbuf + Csz, rA, rB, 0.5, 0.0, st);
           if (s != HOTRG_OK) return s;
-          s = gemm<R>(ctx, Ap(0), Alp(0), Bp(1), Blp(1), p.ldk, Cbuf + Csz, rA, rB, p.K, 0.5, 1.0, st);
+          s = gemm<R>(ctx, Ap(0), Alp(0), Bp(1), Blp(1), p, Cbuf + Csz, rA, rB, 0.5, 1.0, st);
           if (s != HOTRG_OK) return s;
         }
         if (nt >= 3) {
           if (kstep == 0) {  // M_1 = A(S) B(S)^T: the nearest-neighbour pair inside the first block
-            s = gemm<R>(ctx, Ap(1), Alp(1), Bp(1), Blp(1), p.ldk, Cbuf + 2 * Csz, rA, rB, p.K, 1.0, 0.0, st);
+            s = gemm<R>(ctx, Ap(1), Alp(1), Bp(1), Blp(1), p, Cbuf + 2 * Csz, rA, rB, 1.0, 0.0, st);
             if (s != HOTRG_OK) return s;
           } else {           // M' = (A(M) B(T)^T + A(T) B(M)^T) / 2
-            s = gemm<R>(ctx, Ap(2), Alp(2), Bp(0), Blp(0), p.ldk, Cbuf + 2 * Csz, rA, rB, p.K, 0.5, 0.0, st);
+            s = gemm<R>(ctx, Ap(2), Alp(2), Bp(0), Blp(0), p, Cbuf + 2 * Csz, rA, rB, 0.5, 0.0, st);
             if (s != HOTRG_OK) return s;
-            s = gemm<R>(ctx, Ap(0), Alp(0), Bp(2), Blp(2), p.ldk, Cbuf + 2 * Csz, rA, rB, p.K, 0.5, 1.0, st);
+            s = gemm<R>(ctx, Ap(0), Alp(0), Bp(2), Blp(2), p, Cbuf + 2 * Csz, rA, rB, 0.5, 1.0, st);
             if (s != HOTRG_OK) return s;
           }
         }
@@ -888,13 +916,13 @@ hotrg_status hotrg_workspace_size(hotrg_ctx* ctx, int nsteps, const int* dirs, c
   int64_t cap = tensor_elems(D);
   if (nsteps == 0) {
     int Dm[4] = {ctx->dcut_max, ctx->dcut_max, ctx->dcut_max, ctx->dcut_max};
-    StepPlan p = make_plan(Dm, 0, ctx->dcut_max);
+    StepPlan p = make_plan(Dm, 0, ctx->dcut_max, ctx->prec);
     scratch = scratch_layout(p, p.xs, p.xs2, ctx->prec, ctx->impure, ctx->rsize).total;
     cap = std::max(cap, tensor_elems(Dm));
   } else {
     for (int i = 0; i < nsteps; ++i) {
       if (dirs[i] < 0 || dirs[i] > 3 || dcuts[i] < 1 || dcuts[i] > ctx->dcut_max) return HOTRG_EINVAL;
-      StepPlan p = make_plan(D, dirs[i], dcuts[i]);
+      StepPlan p = make_plan(D, dirs[i], dcuts[i], ctx->prec);
       scratch = std::max(scratch, scratch_layout(p, p.xs, p.xs2, ctx->prec, ctx->impure, ctx->rsize).total);
       for (int n = 0; n < 4; ++n) {
         D[n] = p.newD[n];
@@ -1017,7 +1045,7 @@ hotrg_status hotrg_step(hotrg_ctx* ctx, int dir, int dcut) {
   if (dir < 0 || dir > 3 || dcut < 1 || dcut > ctx->dcut_max) return HOTRG_EINVAL;
   if (!ctx->initialised || ctx->sticky) return HOTRG_ESTATE;
   if (ctx->k >= kMaxSteps) return HOTRG_ESTATE;
-  StepPlan p = make_plan(ctx->dims, dir, dcut);
+  StepPlan p = make_plan(ctx->dims, dir, dcut, ctx->prec);
   for (int n = 0; n < 4; ++n)
     if (p.newD[n] > kMaxLeg) return HOTRG_EINVAL;
   if (p.Enew > ctx->L.cap) return HOTRG_EWORKSPACE;
@@ -1220,7 +1248,7 @@ hotrg_status hotrg_profile_read(hotrg_ctx* ctx, hotrg_profile* out) {
 
 hotrg_status hotrg_step_flops(const hotrg_ctx* ctx, int dir, int dcut, double* main_flops, double* total_flops) {
   if (!ctx || dir < 0 || dir > 3 || dcut < 1) return HOTRG_EINVAL;
-  StepPlan p = make_plan(ctx->dims, dir, dcut);
+  StepPlan p = make_plan(ctx->dims, dir, dcut, ctx->prec);
   if (main_flops) *main_flops = p.main_flops;
   if (total_flops) *total_flops = p.total_flops;
   return HOTRG_OK;

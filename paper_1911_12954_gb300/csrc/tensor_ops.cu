@@ -143,6 +143,52 @@ __global__ void __launch_bounds__(256) ttm_fiber_kernel(const R* __restrict__ in
   }
 }
 
+// Fibre form for long contractions (J > 64, as in the closing passes at D >= 9) with a
+// short new index (R <= 32): the outputs of one fibre stay in registers and the J inputs
+// stream through once, each read by one thread with consecutive threads on consecutive
+// fibres.
+template <typename R, int RMAX>
+__global__ void __launch_bounds__(256) ttm_fiber_long_kernel(const R* __restrict__ in, const R* __restrict__ U,
+                                                             R* __restrict__ out, FiberArgs a) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  const int J = a.J1 * a.J2, Rn = a.R1 * a.R2;
+  R* Us = (R*)fsm;                                       // [J][Rn]
+  int64_t* joff = (int64_t*)(fsm + (((size_t)J * Rn * sizeof(R) + 15) / 16) * 16);
+  for (int e = threadIdx.x; e < J * Rn; e += blockDim.x) {
+    const int j = e / Rn, r = e % Rn;
+    const int j1 = j / a.J2, j2 = j % a.J2, r1 = r / a.R2, r2 = r % a.R2;
+    Us[e] = U[j1 * a.ju1 + j2 * a.ju2 + r1 * a.ru1 + r2 * a.ru2];
+  }
+  for (int j = threadIdx.x; j < J; j += blockDim.x) joff[j] = (j / a.J2) * a.ji1 + (j % a.J2) * a.ji2;
+  __syncthreads();
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < a.nfib; f += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q = f, io = 0, oo = 0;
+    for (int d = a.nf - 1; d >= 0; --d) {
+      const int64_t n = a.fdims[d];
+      const int64_t i = q % n;
+      q /= n;
+      io += i * a.fin[d];
+      oo += i * a.fout[d];
+    }
+    R acc[RMAX];
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) acc[r] = 0;
+    for (int j = 0; j < J; ++j) {
+      const R x = in[io + joff[j]];
+      const R* u = Us + j * Rn;
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r)
+        if (r < Rn) acc[r] = fma(u[r], x, acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      if (r >= Rn) break;
+      const int r1 = r / a.R2, r2 = r % a.R2;
+      out[oo + r1 * a.ro1 + r2 * a.ro2] = acc[r] * (R)a.alpha;
+    }
+  }
+}
+
 // Converts a TTMArgs into the fibre form when it fits; false otherwise.
 bool to_fiber(const TTMArgs& a, size_t rsize, FiberArgs& f) {
   f = FiberArgs{};
@@ -179,8 +225,9 @@ bool to_fiber(const TTMArgs& a, size_t rsize, FiberArgs& f) {
   f.ju2 = a.u_sj2;
   f.alpha = a.alpha;
   const int J = a.J1 * a.J2, Rn = f.R1 * f.R2;
-  if (J > 64 || Rn > 256 || (size_t)J * Rn * rsize > 32768 || f.nf == 0) return false;
-  return true;
+  if (f.nf == 0 || (size_t)J * Rn * rsize > 32768) return false;
+  if (J <= 64) return Rn <= 256;
+  return Rn <= 32;                 // long form
 }
 
 template <typename R>
@@ -190,6 +237,12 @@ cudaError_t launch_fiber(const R* in, const R* U, R* out, R* out_lo, const Fiber
   int64_t blocks = (f.nfib + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   const unsigned g = (unsigned)blocks;
+  if (J > 64) {                    // long form (plain store only)
+    if (mode != kTTMStore) return cudaErrorInvalidValue;
+    if (f.R1 * f.R2 <= 16) ttm_fiber_long_kernel<R, 16><<<g, 256, smem, st>>>(in, U, out, f);
+    else ttm_fiber_long_kernel<R, 32><<<g, 256, smem, st>>>(in, U, out, f);
+    return cudaGetLastError();
+  }
   if (J <= 16) {
     if (mode == kTTMSplitTF32) ttm_fiber_kernel<R, 16, kTTMSplitTF32><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
     else ttm_fiber_kernel<R, 16, kTTMStore><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
@@ -207,7 +260,8 @@ cudaError_t launch_ttm(const TI* in, const TU* U, TO* out, TO* out_lo, const TTM
   if (a.inner > 0x7fffffffLL) return cudaErrorInvalidValue;
   if constexpr (std::is_same<TI, TU>::value && std::is_same<TI, TO>::value) {
     FiberArgs f;
-    if (U != nullptr && mode != kTTMAccumulate && to_fiber(a, sizeof(TI), f))
+    if (U != nullptr && mode != kTTMAccumulate && to_fiber(a, sizeof(TI), f) &&
+        (f.J1 * f.J2 <= 64 || mode == kTTMStore))
       return launch_fiber<TI>(in, U, out, out_lo, f, mode, st);
   }
   const int64_t blocks = a.outer < 152 * 64 ? a.outer : 152 * 64;

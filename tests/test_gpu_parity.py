@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 from oracle import hotrg as H
-from workloads import random_tensor
+from workloads import decaying_tensor, random_tensor
 
 pytestmark = pytest.mark.gpu
 
@@ -283,3 +283,22 @@ def test_dcut8_fp64_first_4_steps_vs_golden():
         assert info["ln_c"] == pytest.approx(ref["ln_c"], rel=1e-10)
         for n, (e0, e1) in ref["eps"].items():
             assert info["eps"][int(n)] == pytest.approx((e0, e1), rel=1e-7, abs=1e-12)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("tf32x3", 3e-5)])
+def test_long_closing_contraction(prec, tol):
+    """Uniform bond dimension 9: the closing passes contract D_c^2 = 81 > 64 values per
+    output (the register-accumulator fibre kernel); chi = 2 keeps the GEMM small. A
+    decaying tensor keeps the kept eigenvalues apart (a random one has a flat Gram
+    spectrum, whose top eigenvectors are ill-conditioned)."""
+    dims, mu, dcut = (9, 9, 9, 9), 0, 2
+    T = decaying_tensor(99, dims, 0.7)
+    ref = H.HOTRG.from_tensor(T)
+    ref.step(mu, dcut)
+    g = _gpu(batch=1, dcut_max=9, precision=prec, schedule=[(mu, dcut)], dims0=dims)
+    g.set_tensor(T)
+    g.step(mu, dcut)
+    Tg = g.tensor()
+    assert np.abs(Tg - ref.T).max() <= tol * np.abs(ref.T).max()
+    # ln c sums 1.7e8 squares in a different order on each side: 1e-10 absolute
+    assert g.step_info(1)["ln_c"] == pytest.approx(ref.history[0].ln_c, abs=max(tol, 1e-10))
