@@ -161,6 +161,22 @@ hotrg_status hotrg_copy_isometry(hotrg_ctx* ctx, int b, int nu, double* host, si
 hotrg_status hotrg_step_flops(const hotrg_ctx* ctx, int dir, int dcut, double* main_flops,
                               double* total_flops);
 
+/* Tuning and test options of a context (host-side; take effect from the next step).
+ * HOTRG_OPT_JACOBI_SWEEPS: sweep limit of the eigensolver, 1..60 (default 60); reaching it
+ *   raises HOTRG_ENOCONV at the next synchronising call (used to test that path).
+ * HOTRG_OPT_GEMM_VARIANT: tensor-core GEMM pipeline, 0 = 4 stages of 16-wide k-blocks
+ *   (default), 1 = 2 stages of 32-wide k-blocks. Errors: EINVAL. */
+enum { HOTRG_OPT_JACOBI_SWEEPS = 1, HOTRG_OPT_GEMM_VARIANT = 2 };
+hotrg_status hotrg_set_option(hotrg_ctx* ctx, int option, int value);
+
+/* Failure-detection self-test: on the context's stream, one thread waits, with the same
+ * bounded wait the tensor-core GEMM uses on its mbarriers, on a barrier that nothing
+ * signals, for limit_ms (1..1000) milliseconds. The wait gives up, raises the timeout status
+ * word in the workspace and the kernel returns; no copies or MMAs are in flight in it. The
+ * call synchronises and returns HOTRG_ETIMEOUT like any device-side timeout; the context is
+ * sticky until hotrg_init_tensor / hotrg_set_tensor, and the CUDA context stays usable. */
+hotrg_status hotrg_selftest_wait(hotrg_ctx* ctx, int limit_ms);
+
 /* Launch accounting of one context, for benchmarks. */
 typedef struct {
   uint64_t launches;      /* CUDA kernels this context launched since the last reset         */

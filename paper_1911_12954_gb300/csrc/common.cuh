@@ -106,7 +106,11 @@ cudaError_t launch_gram_reduce(const double* partial, int nchunks, int64_t RR, d
 cudaError_t launch_gram_merge(const double* A1, const double* A2, int Dn, int Dk, double* G,
                               cudaStream_t st);
 cudaError_t launch_jacobi(const EigPack& jobs, int njobs, int nmax, double cluster_tau, int* status,
-                          cudaStream_t st);
+                          cudaStream_t st, int max_sweeps = kJacobiMaxSweeps);
+cudaError_t launch_wait_selftest(int* status, unsigned long long limit_ns, cudaStream_t st);
+cudaError_t launch_gemm_tf32x3_v(const float* Ahi, const float* Alo, const float* Bhi, const float* Blo, int64_t Kp,
+                                 int64_t kps, int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha,
+                                 float beta, int* status, cudaStream_t st, int variant);
 
 template <typename R>
 cudaError_t launch_select(const SelectPack& jobs, int njobs, double side_rel, cudaStream_t st);

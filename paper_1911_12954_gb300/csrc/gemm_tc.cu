@@ -95,15 +95,27 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait; false (and the timeout status raised) when it gives up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* status) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* status,
+                                          unsigned long long limit_ns = kWaitNs) {
   if (mbar_try(b, parity)) return true;
   const unsigned long long t0 = now_ns();
   while (true) {
     if (mbar_try(b, parity)) return true;
-    if (now_ns() - t0 > kWaitNs) {
+    if (now_ns() - t0 > limit_ns) {
       atomicAdd(&status[kStTimeout], 1);
       return false;
     }
+  }
+}
+
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing arrives at
+// (no copies, no MMAs in flight), gives up after limit_ns and raises the status word.
+__global__ void wait_selftest_kernel(int* status, unsigned long long limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_wait(&bar, 0, status, limit_ns);
   }
 }
 
@@ -439,6 +451,11 @@ cudaError_t launch_gemm_tf32x3_v(const float* Ahi, const float* Alo, const float
   if (variant == 1)
     return launch_variant<Cfg<32>>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
   return launch_variant<Cfg<16>>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
+}
+
+cudaError_t launch_wait_selftest(int* status, unsigned long long limit_ns, cudaStream_t st) {
+  tc::wait_selftest_kernel<<<1, 32, 0, st>>>(status, limit_ns);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_tf32x3(const float* Ahi, const float* Alo, const float* Bhi, const float* Blo, int64_t Kp,

@@ -98,6 +98,8 @@ struct hotrg_ctx {
   int last_Dold[4] = {0, 0, 0, 0};
   int last_mu = -1;
   std::vector<double> h_host;
+  int jacobi_sweeps = kJacobiMaxSweeps;
+  int gemm_variant = 0;
   // launch accounting
   uint64_t launches = 0;
   bool profiling = false;
@@ -624,8 +626,9 @@ template <typename R>
 hotrg_status gemm_launch(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R* Blo, const StepPlan& p, R* C,
                          int64_t M, int64_t N, double alpha, double beta, cudaStream_t st) {
   if (ctx->prec == HOTRG_TF32X3) {
-    CK(launch_gemm_tf32x3((const float*)A, (const float*)Alo, (const float*)B, (const float*)Blo, p.Kp, p.kps, p.P,
-                          (float*)C, N, M, N, (float)alpha, (float)beta, (int*)(ctx->ws + ctx->L.status), st),
+    CK(launch_gemm_tf32x3_v((const float*)A, (const float*)Alo, (const float*)B, (const float*)Blo, p.Kp, p.kps, p.P,
+                            (float*)C, N, M, N, (float)alpha, (float)beta, (int*)(ctx->ws + ctx->L.status), st,
+                            ctx->gemm_variant),
        "gemm tf32x3");
   } else {
     if (p.P != 1) return HOTRG_EUNSUPPORTED;
@@ -727,7 +730,7 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
       }
     }
     const bool fp64 = ctx->prec == HOTRG_FP64;
-    LK(1, launch_jacobi(ep, 6, nmax, fp64 ? 1e-10 : 1e-6, status, st), "jacobi");
+    LK(1, launch_jacobi(ep, 6, nmax, fp64 ? 1e-10 : 1e-6, status, st, ctx->jacobi_sweeps), "jacobi");
     SelectPack sp{};
     double* U64 = (double*)(ctx->ws + ctx->L.U64) + (int64_t)bidx * 4 * kMaxGramN * kMaxLeg;
     R* Ur = (R*)(ctx->ws + ctx->L.Ur) + (int64_t)bidx * 4 * kMaxGramN * kMaxLeg;
@@ -1217,6 +1220,31 @@ hotrg_status hotrg_copy_isometry(hotrg_ctx* ctx, int b, int nu, double* host, si
   const double* U64 = (const double*)(ctx->ws + ctx->L.U64) + ((int64_t)b * 4 + nu) * kMaxGramN * kMaxLeg;
   CK(cudaMemcpy(host, U64, cnt * 8, cudaMemcpyDeviceToHost), "copy U");
   return HOTRG_OK;
+}
+
+hotrg_status hotrg_set_option(hotrg_ctx* ctx, int option, int value) {
+  if (!ctx) return HOTRG_EINVAL;
+  switch (option) {
+    case HOTRG_OPT_JACOBI_SWEEPS:
+      if (value < 1 || value > kJacobiMaxSweeps) return HOTRG_EINVAL;
+      ctx->jacobi_sweeps = value;
+      return HOTRG_OK;
+    case HOTRG_OPT_GEMM_VARIANT:
+      if (value < 0 || value > 1) return HOTRG_EINVAL;
+      ctx->gemm_variant = value;
+      return HOTRG_OK;
+    default:
+      return HOTRG_EINVAL;
+  }
+}
+
+hotrg_status hotrg_selftest_wait(hotrg_ctx* ctx, int limit_ms) {
+  hotrg_status r = check_ready(ctx);
+  if (r != HOTRG_OK) return r;
+  if (limit_ms < 1 || limit_ms > 1000) return HOTRG_EINVAL;
+  int* status = (int*)(ctx->ws + ctx->L.status);
+  LK(1, launch_wait_selftest(status, (unsigned long long)limit_ms * 1000000ull, ctx->stream), "selftest");
+  return sync_and_status(ctx);
 }
 
 hotrg_status hotrg_profile_enable(hotrg_ctx* ctx, int enable) {

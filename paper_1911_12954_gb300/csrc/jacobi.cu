@@ -5,7 +5,8 @@
 // order: each round rotates n/2 disjoint index pairs at once, so every 2x2 block of A is
 // updated by exactly one thread and the rounds need only block barriers. A pair is
 // rotated when |a_pq| > max(1e-18 ||G||_F, 2^-52 sqrt|a_pp a_qq|); a sweep without
-// rotations ends the loop, and kJacobiMaxSweeps sweeps raise the no-convergence status
+// rotations ends the loop, and max_sweeps sweeps (kJacobiMaxSweeps unless the context
+// overrides it) raise the no-convergence status
 // (results are still written). Then: eigenvalues sorted descending, the discarded sum
 // eps = sum_{j >= chi} lambda_j, and the first chi eigenvectors in the canonical gauge:
 // eigenvalues closer than cluster_tau * lambda_0 form a cluster (cluster_tau is set
@@ -57,7 +58,7 @@ __device__ double block_sum(double v, double* red) {
 }
 
 __global__ void __launch_bounds__(kJT) jacobi_kernel(const __grid_constant__ EigPack jobs, int use_smem,
-                                                     double cluster_tau, int* status) {
+                                                     double cluster_tau, int max_sweeps, int* status) {
   extern __shared__ double dyn[];
   __shared__ double cs[kMaxGramN / 2 + 1], sn[kMaxGramN / 2 + 1];
   __shared__ int pp[kMaxGramN / 2 + 1], qq[kMaxGramN / 2 + 1];
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(kJT) jacobi_kernel(const __grid_constant__ Eig
   const int half = m / 2;
 
   int sweep = 0;
-  for (; sweep < kJacobiMaxSweeps && n > 1; ++sweep) {
+  for (; sweep < max_sweeps && n > 1; ++sweep) {
     if (tid == 0) rotated = 0;
     __syncthreads();
     for (int r = 0; r < m - 1; ++r) {
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(kJT) jacobi_kernel(const __grid_constant__ Eig
     if (rotated == 0) break;
     __syncthreads();
   }
-  if (tid == 0 && sweep >= kJacobiMaxSweeps) atomicAdd(&status[kStNoConv], 1);
+  if (tid == 0 && sweep >= max_sweeps && n > 1) atomicAdd(&status[kStNoConv], 1);
 
   // ---- sort descending (rank = number of larger eigenvalues, ties by index)
   for (int i = tid; i < n; i += kJT) nrm[i] = A[i * n + i];
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(kJT) jacobi_kernel(const __grid_constant__ Eig
 }
 
 cudaError_t launch_jacobi(const EigPack& jobs, int njobs, int nmax, double cluster_tau, int* status,
-                          cudaStream_t st) {
+                          cudaStream_t st, int max_sweeps) {
   const int smem_n = nmax <= kSmemJacobiN ? nmax : 0;
   const size_t smem = (size_t)2 * smem_n * smem_n * sizeof(double);
   static bool attr = false;
@@ -251,7 +252,7 @@ cudaError_t launch_jacobi(const EigPack& jobs, int njobs, int nmax, double clust
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  jacobi_kernel<<<njobs, kJT, smem, st>>>(jobs, smem_n > 0 ? 1 : 0, cluster_tau, status);
+  jacobi_kernel<<<njobs, kJT, smem, st>>>(jobs, smem_n > 0 ? 1 : 0, cluster_tau, max_sweeps, status);
   return cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@ from . import build as _build
 FP64, FP32, TF32X3 = 0, 1, 2
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32x3": TF32X3}
 IMPURE_NONE, IMPURE_SIGMA, IMPURE_SIGMASIGMA = 0, 1, 2
+OPT_JACOBI_SWEEPS, OPT_GEMM_VARIANT = 1, 2
 
 STATUS = {0: "ok", -1: "EINVAL", -2: "EWORKSPACE", -3: "ECUDA", -4: "ENOCONV", -5: "ENONFINITE",
           -6: "ETIMEOUT", -7: "ESTATE", -8: "EUNSUPPORTED"}
@@ -47,7 +48,8 @@ _LIB = None
 SYMBOLS = ["hotrg_create", "hotrg_destroy", "hotrg_workspace_size", "hotrg_set_workspace", "hotrg_set_stream",
            "hotrg_init_tensor", "hotrg_set_tensor", "hotrg_step", "hotrg_lnZ", "hotrg_impure_magnetization",
            "hotrg_impure_energy", "hotrg_step_info", "hotrg_state", "hotrg_copy_tensor", "hotrg_copy_isometry",
-           "hotrg_step_flops", "hotrg_profile_enable", "hotrg_profile_read", "hotrg_isometry_noalloc",
+           "hotrg_step_flops", "hotrg_set_option", "hotrg_selftest_wait", "hotrg_profile_enable",
+           "hotrg_profile_read", "hotrg_isometry_noalloc",
            "hotrg_status_string", "hotrg_last_error"]
 
 
@@ -81,6 +83,8 @@ def _lib():
         "hotrg_copy_tensor": (c_int, [c_void_p, c_int, c_int, P(c_double), c_size_t]),
         "hotrg_copy_isometry": (c_int, [c_void_p, c_int, c_int, P(c_double), c_size_t]),
         "hotrg_step_flops": (c_int, [c_void_p, c_int, c_int, P(c_double), P(c_double)]),
+        "hotrg_set_option": (c_int, [c_void_p, c_int, c_int]),
+        "hotrg_selftest_wait": (c_int, [c_void_p, c_int]),
         "hotrg_profile_enable": (c_int, [c_void_p, c_int]),
         "hotrg_profile_read": (c_int, [c_void_p, P(Profile)]),
         "hotrg_isometry_noalloc": (c_int, [c_void_p, P(c_int), c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
@@ -225,6 +229,9 @@ class HOTRG:
         out = np.zeros(16 * 16 * 16)
         _check(self.lib.hotrg_copy_isometry(self.ctx, b, nu, _dptr(out), out.size), "copy_isometry")
         return out[: dold * dold * chi].reshape(dold, dold, chi)
+
+    def set_option(self, option: int, value: int):
+        _check(self.lib.hotrg_set_option(self.ctx, option, value), "set_option")
 
     def profile(self, enable: bool = True):
         _check(self.lib.hotrg_profile_enable(self.ctx, int(enable)), "profile_enable")

@@ -302,3 +302,99 @@ def test_long_closing_contraction(prec, tol):
     assert np.abs(Tg - ref.T).max() <= tol * np.abs(ref.T).max()
     # ln c sums 1.7e8 squares in a different order on each side: 1e-10 absolute
     assert g.step_info(1)["ln_c"] == pytest.approx(ref.history[0].ln_c, abs=max(tol, 1e-10))
+
+
+# ------------------------------------------------------------------ impure tensors in mixed precision
+def test_tf32x3_impure_run_vs_golden():
+    """sigma and sigma-sigma impure tensors through the tensor-core path, D_cut = 4,
+    h = 1e-5, 12 steps: <sigma>, <sigma sigma> and E/V against the FP64 oracle."""
+    gd = _golden("ising4d_T6.65_h1e-5_dcut4_impure_12steps")
+    cfg = gd["config"]
+    sched = [(s["mu"], cfg["dcut"]) for s in gd["steps"]]
+    g = _gpu(batch=2, dcut_max=cfg["dcut"], precision="tf32x3", impure=3, schedule=sched)
+    g.init_tensor([gd["beta"]] * 2, cfg["h"])
+    for i, (mu, dc) in enumerate(sched):
+        g.step(mu, dc)
+        ref = gd["steps"][i]
+        lnz, m = g.lnZ(), g.magnetization()
+        e, ss = g.energy()
+        for b in range(2):                    # both batch elements see the same run
+            assert abs(lnz[b] - ref["lnZ"]) < 2e-6
+            assert abs(m[b] - ref["m"]) < 2e-6
+            assert abs(ss[b] - ref["sigma_sigma"]) < 2e-6
+            assert abs(e[b] - ref["energy"]) < 1e-5
+
+
+def test_dcut8_impure_z2_and_bounds():
+    """D_cut = 8, h = 0, TF32x3 with impure tensors, 6 steps: Z2 symmetry makes <sigma>
+    vanish (to the arithmetic's noise); 0 < <sigma sigma> < 1; E/V = -4 <sigma sigma>;
+    ln Z/V equals the pure run's to 1e-6 (the impure tensors do not feed back)."""
+    sched = [(i % 4, 8) for i in range(6)]
+    g = _gpu(batch=1, dcut_max=8, precision="tf32x3", impure=3, schedule=sched)
+    g.init_tensor(1 / 6.65, 0.0)
+    gd = _golden("ising4d_T6.65_h0_dcut8_8steps")
+    for i, (mu, dc) in enumerate(sched):
+        g.step(mu, dc)
+        assert abs(g.lnZ()[0] - gd["steps"][i]["lnZ"]) <= 1e-6
+        assert abs(g.magnetization()[0]) < 1e-6
+        e, ss = g.energy()
+        assert 0.0 < ss[0] < 1.0 and e[0] == pytest.approx(-4 * ss[0], rel=1e-12)
+
+
+# ------------------------------------------------------------------ failure detection (no GPU fault)
+def test_bounded_wait_times_out_and_context_recovers():
+    """A device-side wait on a barrier nothing signals gives up after 20 ms and reports
+    ETIMEOUT; the context is sticky until re-initialised and then steps normally."""
+    from paper_1911_12954_gb300 import HotrgError
+    g = _gpu(batch=1, dcut_max=4, precision="tf32x3", schedule=[(0, 4), (1, 4)])
+    assert g.lib.hotrg_selftest_wait(g.ctx, 20) == -6          # HOTRG_ETIMEOUT
+    with pytest.raises(HotrgError, match="ESTATE"):
+        g.step(0, 4)                                        # sticky after the device error
+    g.init_tensor(1 / 6.65, 0.0)
+    g.step(0, 4)
+    g.step(1, 4)
+    assert g.lnZ()[0] == pytest.approx(H.run(4, 1 / 6.65, 0.0, 4, 2).lnZ(), abs=2e-6)
+
+
+def test_jacobi_sweep_limit_reports_enoconv():
+    from paper_1911_12954_gb300 import OPT_JACOBI_SWEEPS, HotrgError
+    g = _gpu(batch=1, dcut_max=4, precision="fp64", schedule=[(i % 4, 4) for i in range(3)])
+    g.set_option(OPT_JACOBI_SWEEPS, 1)
+    g.init_tensor(1 / 6.65, 0.0)
+    g.step(0, 4)
+    g.step(1, 4)                      # 16 x 16 Gram matrices need more than one sweep
+    with pytest.raises(HotrgError, match="ENOCONV"):
+        g.lnZ()
+    g.set_option(OPT_JACOBI_SWEEPS, 60)
+    g.init_tensor(1 / 6.65, 0.0)
+    for i in range(3):
+        g.step(i % 4, 4)
+    assert g.lnZ()[0] == pytest.approx(H.run(4, 1 / 6.65, 0.0, 4, 3).lnZ(), rel=1e-10)
+
+
+def test_nonfinite_input_is_rejected_on_the_host():
+    from paper_1911_12954_gb300 import HotrgError
+    dims = (2, 2, 2, 2)
+    T = random_tensor(3, dims)
+    T[0, 1, 0, 1, 1, 0, 0, 1] = np.nan
+    g = _gpu(batch=1, dcut_max=4, precision="fp64", schedule=[(0, 4)], dims0=dims)
+    with pytest.raises(HotrgError, match="EINVAL"):
+        g.set_tensor(T)
+    T[0, 1, 0, 1, 1, 0, 0, 1] = np.inf
+    with pytest.raises(HotrgError, match="EINVAL"):
+        g.set_tensor(T)
+
+
+def test_gemm_pipeline_variants_agree():
+    """Both tensor-core pipelines (4 x 16-wide and 2 x 32-wide k-blocks) give the same step."""
+    from paper_1911_12954_gb300 import OPT_GEMM_VARIANT
+    dims, mu, dcut = (3, 3, 2, 3), 2, 6
+    T = random_tensor(12, dims)
+    out = []
+    for v in (0, 1):
+        g = _gpu(batch=1, dcut_max=9, precision="tf32x3", schedule=[(mu, dcut)], dims0=dims)
+        g.set_option(OPT_GEMM_VARIANT, v)
+        g.set_tensor(T)
+        g.step(mu, dcut)
+        out.append(g.tensor())
+    assert np.allclose(out[0], out[1], atol=1e-6 * np.abs(out[0]).max())
