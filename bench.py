@@ -54,6 +54,7 @@ def parse_args():
     p.add_argument("--cpu", type=int, default=1, help="time the FP64 oracle on a bounded sample (rank 0, N=1)")
     p.add_argument("--batch", type=int, default=1, help="temperatures per GPU (evenly spaced in [6.60, 6.72])")
     p.add_argument("--impure", type=int, default=0, help="propagate the sigma and sigma-sigma impure tensors")
+    p.add_argument("--graphs", type=int, default=0, help="replay each distinct step as a captured CUDA graph")
     return p.parse_args()
 
 
@@ -287,7 +288,8 @@ def main():
         return args.batch * (nprod * main + 3 * (total - main))
 
     # ---------------------------------------------------------------- mixed precision, timed
-    run = HOTRG(batch=args.batch, dcut_max=D, precision="tf32x3", impure=impure, schedule=sched)
+    run = HOTRG(batch=args.batch, dcut_max=D, precision="tf32x3", impure=impure, schedule=sched,
+                graphs=bool(args.graphs))
     run.init_tensor(betas, hfield)
     for i in range(args.warmup):
         run.step(*sched[i])
@@ -410,7 +412,7 @@ def main():
                                + f", D_cut={D}, 1024^4 lattice schedule (x,y,z,t cycled); timed steps "
                                f"{args.warmup + 1}..{nsteps} (steady state)",
                    "dcut": D, "temperatures_per_gpu": args.batch, "impure": bool(impure), "lattice": "1024^4",
-                   "precision": "tf32x3 (fp32 storage)",
+                   "precision": "tf32x3 (fp32 storage)", "cuda_graphs": bool(args.graphs),
                    "l2": "operands larger than L2 (GEMM A and B: 2 x 4.3 GB per step, hi + lo)"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,

@@ -165,8 +165,12 @@ hotrg_status hotrg_step_flops(const hotrg_ctx* ctx, int dir, int dcut, double* m
  * HOTRG_OPT_JACOBI_SWEEPS: sweep limit of the eigensolver, 1..60 (default 60); reaching it
  *   raises HOTRG_ENOCONV at the next synchronising call (used to test that path).
  * HOTRG_OPT_GEMM_VARIANT: tensor-core GEMM pipeline, 0 = 4 stages of 16-wide k-blocks
- *   (default), 1 = 2 stages of 32-wide k-blocks. Errors: EINVAL. */
-enum { HOTRG_OPT_JACOBI_SWEEPS = 1, HOTRG_OPT_GEMM_VARIANT = 2 };
+ *   (default), 1 = 2 stages of 32-wide k-blocks.
+ * HOTRG_OPT_GRAPHS: 1 = capture each distinct step (plan, buffer, first step or not) once
+ *   into a CUDA graph and replay it (every kernel of the step for every batch element in
+ *   one graph launch); needs a non-default stream (hotrg_set_stream). Per-GEMM profiling
+ *   events are not recorded in this mode. Errors: EINVAL. */
+enum { HOTRG_OPT_JACOBI_SWEEPS = 1, HOTRG_OPT_GEMM_VARIANT = 2, HOTRG_OPT_GRAPHS = 3 };
 hotrg_status hotrg_set_option(hotrg_ctx* ctx, int option, int value);
 
 /* Failure-detection self-test: on the context's stream, one thread waits, with the same

@@ -72,6 +72,11 @@ struct SelectJob {
   double* rec_eps;         // step record: eps of both sides
   int* rec_primed;         // step record: side taken
   int* rec_degen;          // step record: degenerate cut on the side taken
+  // when rec_b != nullptr the record fields above are ignored and the kernel writes
+  // rec_b[*step].{eps,primed,degen}[nu] (step counter read on the device)
+  struct DevRecord* rec_b;
+  const int* step;
+  int nu;
 };
 
 // Step record as kept on the device for each batch element and step.
@@ -118,8 +123,11 @@ template <typename R>
 cudaError_t launch_init(const double* beta, const double* h, R* T, R* S, int64_t slot, double* lnz_acc,
                         int batch, cudaStream_t st);
 template <typename R>
-cudaError_t launch_norm(const R* x, int64_t n, double* partial, double weight, double* c_out, double* lnz_acc,
-                        double* ln_c_rec, int* status, cudaStream_t st);
+cudaError_t launch_norm(const R* x, int64_t n, double* partial, const int* step, double* c_out, double* lnz_acc,
+                        DevRecord* rec_b, int* status, cudaStream_t st);
+cudaError_t launch_step_end(int* step, cudaStream_t st);
+void jacobi_prepare();
+void gemm_prepare();
 template <typename R>
 cudaError_t launch_scale(R* x, int64_t n, const double* c, cudaStream_t st);
 template <typename R>

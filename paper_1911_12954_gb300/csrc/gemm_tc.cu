@@ -453,6 +453,21 @@ cudaError_t launch_gemm_tf32x3_v(const float* Ahi, const float* Alo, const float
   return launch_variant<Cfg<16>>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
 }
 
+// Sets the kernels' shared-memory attributes and caches the SM count ahead of time, so no
+// first launch does host-side set-up (which must not happen inside a stream capture).
+void gemm_prepare() {
+  using namespace tc;
+  static bool done = false;
+  if (done) return;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  cudaFuncSetAttribute(gemm_tf32x3_kernel<Cfg<16>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)Cfg<16>::SMEM_BYTES);
+  cudaFuncSetAttribute(gemm_tf32x3_kernel<Cfg<32>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)Cfg<32>::SMEM_BYTES);
+  done = true;
+}
+
 cudaError_t launch_wait_selftest(int* status, unsigned long long limit_ns, cudaStream_t st) {
   tc::wait_selftest_kernel<<<1, 32, 0, st>>>(status, limit_ns);
   return cudaGetLastError();

@@ -19,6 +19,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -69,7 +70,7 @@ struct StepPlan {
 
 struct Layout {
   // persistent
-  size_t status, lnz, cval, trace, rec, beta, hfield, U64, Ur, tensors;
+  size_t status, step, lnz, cval, trace, rec, beta, hfield, U64, Ur, tensors;
   int64_t cap;            // elements per tensor slot
   size_t persistent_end;
 };
@@ -100,6 +101,12 @@ struct hotrg_ctx {
   std::vector<double> h_host;
   int jacobi_sweeps = kJacobiMaxSweeps;
   int gemm_variant = 0;
+  bool use_graphs = false;
+  struct GraphEntry {
+    cudaGraphExec_t exec;
+    uint64_t launches;
+  };
+  std::map<std::string, GraphEntry> graphs;   // captured steps, keyed by everything a step's launches depend on
   // launch accounting
   uint64_t launches = 0;
   bool profiling = false;
@@ -107,8 +114,13 @@ struct hotrg_ctx {
   size_t ev_used = 0;
   uint64_t gemm_launches = 0;
   double gemm_flops = 0;
+  void drop_graphs() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.exec);
+    graphs.clear();
+  }
   ~hotrg_ctx() {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    drop_graphs();
   }
 };
 
@@ -321,6 +333,7 @@ Layout persistent_layout(int batch, int64_t cap, int impure, size_t rs) {
     return o;
   };
   L.status = take(kStWords * 4);
+  L.step = take(sizeof(int));
   L.lnz = take(batch * 8);
   L.cval = take(batch * 8);
   L.trace = take(3 * batch * 8);
@@ -600,7 +613,7 @@ hotrg_status gemm(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R*
                   int64_t M, int64_t N, double alpha, double beta, cudaStream_t st) {
   const int64_t K = p.K;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (ctx->profiling) {
+  if (ctx->profiling && !ctx->use_graphs) {
     while (ctx->ev.size() < ctx->ev_used + 2) {
       cudaEvent_t e;
       CK(cudaEventCreate(&e), "event create");
@@ -614,7 +627,7 @@ hotrg_status gemm(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R*
   hotrg_status r = gemm_launch<R>(ctx, A, Alo, B, Blo, p, C, M, N, alpha, beta, st);
   if (r != HOTRG_OK) return r;
   ctx->launches += 1;
-  if (ctx->profiling) {
+  if (ctx->profiling && !ctx->use_graphs) {
     CK(cudaEventRecord(e1, st), "event record");
     ctx->gemm_launches += 1;
     ctx->gemm_flops += 2.0 * (double)M * (double)N * (double)K;
@@ -654,7 +667,8 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
 
   for (int bidx = 0; bidx < ctx->batch; ++bidx) {
     const R* T = tensor_ptr<R>(ctx, 0, ctx->cur, bidx);
-    DevRecord* rec = (DevRecord*)(ctx->ws + ctx->L.rec) + (int64_t)bidx * kMaxSteps + kstep;
+    DevRecord* rec_b = (DevRecord*)(ctx->ws + ctx->L.rec) + (int64_t)bidx * kMaxSteps;
+    const int* dstep = (const int*)(ctx->ws + ctx->L.step);
     // ---------------------------------------------------------------- 1. Gram
     int64_t ts[8];
     canon_strides(p.D, ts);
@@ -748,9 +762,12 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
       j.Ur = Ur + (int64_t)n * kMaxGramN * kMaxLeg;
       j.n = ep.j[i * 2].n;
       j.chi = ep.j[i * 2].chi;
-      j.rec_eps = rec->eps[n];
-      j.rec_primed = &rec->primed[n];
-      j.rec_degen = &rec->degen[n];
+      j.rec_eps = nullptr;
+      j.rec_primed = nullptr;
+      j.rec_degen = nullptr;
+      j.rec_b = rec_b;
+      j.step = dstep;
+      j.nu = n;
     }
     LK(1, launch_select<R>(sp, 3, fp64 ? 1e-9 : 1e-6, st), "select");
     const R* Ua = Ur + (int64_t)p.a * kMaxGramN * kMaxLeg;
@@ -835,11 +852,10 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
     // ---------------------------------------------------------------- 4. normalise
     double* lnz = (double*)(ctx->ws + ctx->L.lnz) + bidx;
     double* cval = (double*)(ctx->ws + ctx->L.cval) + bidx;
-    const double weight = ldexp(1.0, -(kstep + 1));
-    LK(2, launch_norm<R>(dst[0], p.Enew, (double*)(sb + sc.npart), weight, cval, lnz, &rec->ln_c, status, st),
-       "norm");
+    LK(2, launch_norm<R>(dst[0], p.Enew, (double*)(sb + sc.npart), dstep, cval, lnz, rec_b, status, st), "norm");
     for (int w = 0; w < nt; ++w) LK(1, launch_scale<R>(dst[w], p.Enew, cval, st), "scale");
   }
+  LK(1, launch_step_end((int*)(ctx->ws + ctx->L.step), st), "step end");
   return HOTRG_OK;
 }
 
@@ -948,6 +964,9 @@ hotrg_status hotrg_set_workspace(hotrg_ctx* ctx, void* dev_ptr, size_t bytes) {
   }
   Layout L = persistent_layout(ctx->batch, cap, ctx->impure, ctx->rsize);
   if (L.persistent_end > bytes) return HOTRG_EWORKSPACE;
+  ctx->drop_graphs();
+  jacobi_prepare();
+  gemm_prepare();
   ctx->ws = (char*)dev_ptr;
   ctx->ws_bytes = bytes;
   ctx->L = L;
@@ -958,6 +977,7 @@ hotrg_status hotrg_set_workspace(hotrg_ctx* ctx, void* dev_ptr, size_t bytes) {
 
 hotrg_status hotrg_set_stream(hotrg_ctx* ctx, void* s) {
   if (!ctx) return HOTRG_EINVAL;
+  if (ctx->use_graphs && s == nullptr) return HOTRG_EINVAL;   // the legacy stream cannot be captured
   ctx->stream = (cudaStream_t)s;
   return HOTRG_OK;
 }
@@ -971,6 +991,7 @@ hotrg_status hotrg_init_tensor(hotrg_ctx* ctx, const double* beta, const double*
   if (ctx->L.cap < 256) return HOTRG_EWORKSPACE;
   cudaStream_t st = ctx->stream;
   CK(cudaMemsetAsync(ctx->ws + ctx->L.status, 0, kStWords * 4, st), "init status");
+  CK(cudaMemsetAsync(ctx->ws + ctx->L.step, 0, sizeof(int), st), "init step");
   CK(cudaMemsetAsync(ctx->ws + ctx->L.rec, 0, (size_t)ctx->batch * kMaxSteps * sizeof(DevRecord), st), "init rec");
   CK(cudaMemcpyAsync(ctx->ws + ctx->L.beta, beta, ctx->batch * 8, cudaMemcpyHostToDevice, st), "beta");
   CK(cudaMemcpyAsync(ctx->ws + ctx->L.hfield, h, ctx->batch * 8, cudaMemcpyHostToDevice, st), "h");
@@ -1018,6 +1039,7 @@ hotrg_status hotrg_set_tensor(hotrg_ctx* ctx, int b, const int dims[4], const do
   CK(cudaStreamSynchronize(st), "set_tensor sync");
   if (b == 0) {
     CK(cudaMemset(ctx->ws + ctx->L.status, 0, kStWords * 4), "status");
+    CK(cudaMemset(ctx->ws + ctx->L.step, 0, sizeof(int)), "step");
     CK(cudaMemset(ctx->ws + ctx->L.rec, 0, (size_t)ctx->batch * kMaxSteps * sizeof(DevRecord)), "rec");
     ctx->cur = 0;
   }
@@ -1073,8 +1095,39 @@ hotrg_status hotrg_step(hotrg_ctx* ctx, int dir, int dcut) {
   if (best_blocks < 0) return HOTRG_EWORKSPACE;
   p.xs = best_xs;
   p.xs2 = best_xs2;
-  hotrg_status s = ctx->prec == HOTRG_FP64 ? do_step<double>(ctx, p) : do_step<float>(ctx, p);
-  if (s != HOTRG_OK) return s;
+  hotrg_status s = HOTRG_OK;
+  if (!ctx->use_graphs) {
+    s = ctx->prec == HOTRG_FP64 ? do_step<double>(ctx, p) : do_step<float>(ctx, p);
+    if (s != HOTRG_OK) return s;
+  } else {
+    // Everything the step's launches depend on: the plan (dims, direction, cut, slices),
+    // which buffer holds the tensors, whether it is the first step (M_1 = C(S,S)) and the
+    // impure tensors in use. ln c / 2^k and the record slot come from the device counter.
+    char key[256];
+    snprintf(key, sizeof(key), "%d %d %d %d %d %d %d %d %d %d %d %d", dir, dcut, ctx->dims[0], ctx->dims[1],
+             ctx->dims[2], ctx->dims[3], ctx->cur, ctx->k == 0, ctx->impure_active, p.xs, p.xs2, ctx->batch);
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) {
+      const uint64_t l0 = ctx->launches;
+      CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+      s = ctx->prec == HOTRG_FP64 ? do_step<double>(ctx, p) : do_step<float>(ctx, p);
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+      if (s != HOTRG_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+      }
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+      cudaGraphExec_t exec = nullptr;
+      e = cudaGraphInstantiate(&exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "instantiate");
+      it = ctx->graphs.emplace(key, hotrg_ctx::GraphEntry{exec, ctx->launches - l0}).first;
+      ctx->launches = l0;
+    }
+    CK(cudaGraphLaunch(it->second.exec, ctx->stream), "graph launch");
+    ctx->launches += it->second.launches;
+  }
   ctx->mu_hist[ctx->k] = dir;
   ctx->slices_hist[ctx->k][0] = (p.chi[p.a] + p.xs - 1) / p.xs;
   ctx->slices_hist[ctx->k][1] = (p.chi[p.a] + p.xs2 - 1) / p.xs2;
@@ -1228,10 +1281,17 @@ hotrg_status hotrg_set_option(hotrg_ctx* ctx, int option, int value) {
     case HOTRG_OPT_JACOBI_SWEEPS:
       if (value < 1 || value > kJacobiMaxSweeps) return HOTRG_EINVAL;
       ctx->jacobi_sweeps = value;
+      ctx->drop_graphs();
       return HOTRG_OK;
     case HOTRG_OPT_GEMM_VARIANT:
       if (value < 0 || value > 1) return HOTRG_EINVAL;
       ctx->gemm_variant = value;
+      ctx->drop_graphs();
+      return HOTRG_OK;
+    case HOTRG_OPT_GRAPHS:
+      if (value < 0 || value > 1) return HOTRG_EINVAL;
+      if (value && ctx->stream == nullptr) return HOTRG_EINVAL;
+      ctx->use_graphs = value != 0;
       return HOTRG_OK;
     default:
       return HOTRG_EINVAL;

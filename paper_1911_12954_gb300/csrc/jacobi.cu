@@ -241,6 +241,11 @@ __global__ void __launch_bounds__(kJT) jacobi_kernel(const __grid_constant__ Eig
   }
 }
 
+void jacobi_prepare() {
+  cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       2 * kSmemJacobiN * kSmemJacobiN * (int)sizeof(double));
+}
+
 cudaError_t launch_jacobi(const EigPack& jobs, int njobs, int nmax, double cluster_tau, int* status,
                           cudaStream_t st, int max_sweeps) {
   const int smem_n = nmax <= kSmemJacobiN ? nmax : 0;
@@ -266,10 +271,19 @@ __global__ void __launch_bounds__(256) select_kernel(const __grid_constant__ Sel
   if (tid == 0) {
     const double e0 = *jb.eps[0], e1 = *jb.eps[1];
     side = (e0 - e1 > side_rel * (fabs(e0) + fabs(e1)) + 1e-13 * fabs(jb.lam0[0])) ? 1 : 0;
-    jb.rec_eps[0] = e0;
-    jb.rec_eps[1] = e1;
-    *jb.rec_primed = side;
-    *jb.rec_degen = *jb.degen[side];
+    double* re = jb.rec_eps;
+    int* rp = jb.rec_primed;
+    int* rd = jb.rec_degen;
+    if (jb.rec_b != nullptr) {           // record slot of the current step, read on the device
+      const int k = *jb.step < kMaxSteps ? *jb.step : kMaxSteps - 1;
+      re = jb.rec_b[k].eps[jb.nu];
+      rp = &jb.rec_b[k].primed[jb.nu];
+      rd = &jb.rec_b[k].degen[jb.nu];
+    }
+    re[0] = e0;
+    re[1] = e1;
+    *rp = side;
+    *rd = *jb.degen[side];
   }
   __syncthreads();
   const double* src = jb.U[side];

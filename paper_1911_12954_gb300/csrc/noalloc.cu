@@ -186,6 +186,9 @@ extern "C" hotrg_status hotrg_isometry_noalloc(const double* T_dev, const int di
   sj.rec_eps = eps_dev;
   sj.rec_primed = primed_dev;
   sj.rec_degen = &rec->degen[0];
+  sj.rec_b = nullptr;             // explicit record pointers above
+  sj.step = nullptr;
+  sj.nu = nu;
   NA_CK(launch_select<double>(sp, 1, 1e-9, st), "select");
   int host_status[kStWords];
   NA_CK(cudaMemcpyAsync(host_status, status, sizeof(host_status), cudaMemcpyDeviceToHost, st), "status read");

@@ -358,9 +358,11 @@ __global__ void __launch_bounds__(256) sumsq_kernel(const R* __restrict__ x, int
   }
 }
 
-// Pass 2 (one block): c = sqrt(sum), ln Z accumulator += ln(c) / 2^k, record ln c.
-__global__ void norm_finish_kernel(const double* __restrict__ partial, int np, double weight, double* c_out,
-                                   double* lnz_acc, double* ln_c_rec, int* status) {
+// Pass 2 (one block): c = sqrt(sum), ln Z accumulator += ln(c) / 2^(k+1), record ln c in
+// rec_b[k] where k = *step is the number of steps done before this one (read on the
+// device, so a captured step replays correctly at any k).
+__global__ void norm_finish_kernel(const double* __restrict__ partial, int np, const int* __restrict__ step,
+                                   double* c_out, double* lnz_acc, DevRecord* rec_b, int* status) {
   __shared__ double red[256];
   double s = 0;
   for (int i = threadIdx.x; i < np; i += blockDim.x) s += partial[i];
@@ -371,17 +373,29 @@ __global__ void norm_finish_kernel(const double* __restrict__ partial, int np, d
     __syncthreads();
   }
   if (threadIdx.x == 0) {
+    const int k = *step;
     const double c = sqrt(red[0]);
+    double* ln_c_rec = &rec_b[k < kMaxSteps ? k : kMaxSteps - 1].ln_c;
     if (!(c > 0.0) || !isfinite(c)) {
       atomicAdd(&status[kStNonFinite], 1);
       *c_out = 1.0;
       *ln_c_rec = nan("");
     } else {
       *c_out = c;
-      *lnz_acc += log(c) * weight;
+      *lnz_acc += log(c) * ldexp(1.0, -(k + 1));
       *ln_c_rec = log(c);
     }
   }
+}
+
+// Advances the device step counter at the end of a step.
+__global__ void step_end_kernel(int* step) {
+  if (threadIdx.x == 0) *step += 1;
+}
+
+cudaError_t launch_step_end(int* step, cudaStream_t st) {
+  step_end_kernel<<<1, 32, 0, st>>>(step);
+  return cudaGetLastError();
 }
 
 template <typename R>
@@ -392,10 +406,10 @@ __global__ void __launch_bounds__(256) scale_kernel(R* __restrict__ x, int64_t n
 }
 
 template <typename R>
-cudaError_t launch_norm(const R* x, int64_t n, double* partial, double weight, double* c_out, double* lnz_acc,
-                        double* ln_c_rec, int* status, cudaStream_t st) {
+cudaError_t launch_norm(const R* x, int64_t n, double* partial, const int* step, double* c_out, double* lnz_acc,
+                        DevRecord* rec_b, int* status, cudaStream_t st) {
   sumsq_kernel<R><<<kNormBlocks, 256, 0, st>>>(x, n, partial);
-  norm_finish_kernel<<<1, 256, 0, st>>>(partial, kNormBlocks, weight, c_out, lnz_acc, ln_c_rec, status);
+  norm_finish_kernel<<<1, 256, 0, st>>>(partial, kNormBlocks, step, c_out, lnz_acc, rec_b, status);
   return cudaGetLastError();
 }
 template <typename R>
@@ -406,10 +420,10 @@ cudaError_t launch_scale(R* x, int64_t n, const double* c, cudaStream_t st) {
   scale_kernel<R><<<(unsigned)blocks, 256, 0, st>>>(x, n, c);
   return cudaGetLastError();
 }
-template cudaError_t launch_norm<double>(const double*, int64_t, double*, double, double*, double*, double*, int*,
-                                         cudaStream_t);
-template cudaError_t launch_norm<float>(const float*, int64_t, double*, double, double*, double*, double*, int*,
-                                        cudaStream_t);
+template cudaError_t launch_norm<double>(const double*, int64_t, double*, const int*, double*, double*, DevRecord*,
+                                         int*, cudaStream_t);
+template cudaError_t launch_norm<float>(const float*, int64_t, double*, const int*, double*, double*, DevRecord*,
+                                        int*, cudaStream_t);
 template cudaError_t launch_scale<double>(double*, int64_t, const double*, cudaStream_t);
 template cudaError_t launch_scale<float>(float*, int64_t, const double*, cudaStream_t);
 

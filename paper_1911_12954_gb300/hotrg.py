@@ -18,7 +18,7 @@ from . import build as _build
 FP64, FP32, TF32X3 = 0, 1, 2
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32x3": TF32X3}
 IMPURE_NONE, IMPURE_SIGMA, IMPURE_SIGMASIGMA = 0, 1, 2
-OPT_JACOBI_SWEEPS, OPT_GEMM_VARIANT = 1, 2
+OPT_JACOBI_SWEEPS, OPT_GEMM_VARIANT, OPT_GRAPHS = 1, 2, 3
 
 STATUS = {0: "ok", -1: "EINVAL", -2: "EWORKSPACE", -3: "ECUDA", -4: "ENOCONV", -5: "ENONFINITE",
           -6: "ETIMEOUT", -7: "ESTATE", -8: "EUNSUPPORTED"}
@@ -125,10 +125,11 @@ class HOTRG:
     schedule : list of (dir, dcut) used to size the workspace (None: steady state at
         dcut_max), dims0 : starting bond dimensions for set_tensor runs.
     workspace_bytes : override of the workspace size (smaller makes steps slice).
+    graphs : capture each distinct step into a CUDA graph and replay it (own stream).
     """
 
     def __init__(self, batch=1, dcut_max=4, precision="fp64", impure=0, schedule=None, dims0=None,
-                 workspace_bytes=None, device=None, stream=None):
+                 workspace_bytes=None, device=None, stream=None, graphs=False):
         import torch
 
         if not torch.cuda.is_available():
@@ -153,8 +154,13 @@ class HOTRG:
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         _check(self.lib.hotrg_set_workspace(self.ctx, ctypes.c_void_p(self.workspace.data_ptr()), nbytes),
                "set_workspace")
-        self.stream = stream or torch.cuda.current_stream(self.device)
+        if stream is None:
+            # graph capture needs a stream of its own (the legacy default stream cannot be captured)
+            stream = torch.cuda.Stream(self.device) if graphs else torch.cuda.current_stream(self.device)
+        self.stream = stream
         _check(self.lib.hotrg_set_stream(self.ctx, ctypes.c_void_p(self.stream.cuda_stream)), "set_stream")
+        if graphs:
+            _check(self.lib.hotrg_set_option(self.ctx, OPT_GRAPHS, 1), "set_option(graphs)")
 
     def workspace_size(self, schedule=None, dims0=None) -> int:
         n = 0 if schedule is None else len(schedule)
