@@ -5,7 +5,8 @@ Workload (synthetic, deterministic): the 4D Ising site tensor at T = 6.65, h = 0
 D_cut = 8, directions cycled x, y, z, t towards the 1024^4 lattice (40 steps). A
 benchmark "step" is one HOTRG coarse-graining step: Gram matrices on both sides of the
 three transverse bond pairs, FP64 Jacobi eigensolves and isometries, the block-spin
-contraction (2 D^15 flops, tcgen05 TF32x3), normalisation and ln Z accumulation. The
+contraction (2 D^15 flops on tcgen05 tensor cores: each FP32 operand split into an fp16
+hi + lo pair, three products, FP32 accumulation), normalisation and ln Z accumulation. The
 W warm-up steps are steps 1..W of the run (bond dimensions reach 8 at step 3), the K
 timed steps are the steady-state steps W+1..W+K.
 
@@ -55,25 +56,28 @@ def parse_args():
     p.add_argument("--batch", type=int, default=1, help="temperatures per GPU (evenly spaced in [6.60, 6.72])")
     p.add_argument("--impure", type=int, default=0, help="propagate the sigma and sigma-sigma impure tensors")
     p.add_argument("--graphs", type=int, default=0, help="replay each distinct step as a captured CUDA graph")
+    p.add_argument("--precision", choices=["tf32x3", "fp16x3"], default="fp16x3",
+                   help="tensor-core split of the block-spin contraction (default: fp16 hi/lo on kind::f16)")
     return p.parse_args()
 
 
 # --------------------------------------------------------------------------- helpers
-def tf32_peak(sustained: bool = True):
-    """Dense TF32 tensor peak: a measured BF16 peak x the nominal TF32/BF16 ratio
-    (1.1 / 2.25 PFLOP/s). The GEMM is timed inside seconds of back-to-back steps, so the
-    sustained BF16 figure applies; the burst one is reported beside it. Falls back to the
-    profiling recipe's 1.9 / 1.7 PFLOP/s when no measurement exists."""
+def tensor_peak(precision: str, sustained: bool = True):
+    """Dense tensor peak of the GEMM's operand type. fp16 runs at the BF16 rate (the
+    measured BF16 figure applies as is); TF32 = that figure x the nominal TF32/BF16 ratio
+    1.1 / 2.25. The GEMM is timed inside seconds of back-to-back steps, so the sustained
+    figure applies; the burst one is reported beside it. Falls back to the profiling
+    recipe's 1.9 / 1.7 PFLOP/s when no measurement exists."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    r = 1.1 / 2.25
+    r, rname = (1.0, "fp16 = bf16 rate") if precision == "fp16x3" else (1.1 / 2.25, "x nominal tf32/bf16 1.1/2.25")
     try:
         with open(path) as f:
             mp = json.load(f)
         b = mp["bf16_tflops_sustained"] if sustained else mp["bf16_tflops"]
-        return b * r, ("measured bf16 sustained" if sustained else "measured bf16 burst") + " x nominal tf32/bf16 1.1/2.25"
+        return b * r, ("measured bf16 sustained" if sustained else "measured bf16 burst") + " " + rname
     except Exception:
         b = 1700.0 if sustained else 1900.0
-        return b * r, f"fallback bf16 {b / 1000:.1f} PF x nominal tf32/bf16 1.1/2.25"
+        return b * r, f"fallback bf16 {b / 1000:.1f} PF " + rname
 
 
 class ClockSampler:
@@ -288,7 +292,7 @@ def main():
         return args.batch * (nprod * main + 3 * (total - main))
 
     # ---------------------------------------------------------------- mixed precision, timed
-    run = HOTRG(batch=args.batch, dcut_max=D, precision="tf32x3", impure=impure, schedule=sched,
+    run = HOTRG(batch=args.batch, dcut_max=D, precision=args.precision, impure=impure, schedule=sched,
                 graphs=bool(args.graphs))
     run.init_tensor(betas, hfield)
     for i in range(args.warmup):
@@ -319,7 +323,7 @@ def main():
     accuracy = {}
     nver = 8 if D <= 8 else 3
     # the first temperature of this rank's workload, with its field and impure tensors
-    ver = HOTRG(batch=1, dcut_max=D, precision="tf32x3", impure=impure, schedule=sched[:nver])
+    ver = HOTRG(batch=1, dcut_max=D, precision=args.precision, impure=impure, schedule=sched[:nver])
     ver.init_tensor(beta, hfield)
     mixed_lnz = []
     for i in range(nver):
@@ -366,7 +370,7 @@ def main():
     e2e = None
     if args.e2e and args.batch == 1 and not impure:
         full = [(i % 4, D) for i in range(LATTICE_STEPS)]
-        job = HOTRG(batch=1, dcut_max=D, precision="tf32x3", schedule=full)
+        job = HOTRG(batch=1, dcut_max=D, precision=args.precision, schedule=full)
         bh = torch.tensor([beta], dtype=torch.float64).pin_memory()
         hh = torch.tensor([H_WORK], dtype=torch.float64).pin_memory()
         job.init_tensor(bh.numpy(), hh.numpy())           # warm the job once
@@ -398,25 +402,26 @@ def main():
                          f"shape ({D},)*8: full HOSVD + the block-spin contraction restricted to X = X' = 0 "
                          f"(1/{D * D} of the D^15 product); {s:.1f} s"}
 
-    peak, peak_src = tf32_peak(True)
-    peak_burst, _ = tf32_peak(False)
+    peak, peak_src = tensor_peak(args.precision, True)
+    peak_burst, _ = tensor_peak(args.precision, False)
     achieved = prof["gemm_flops"] / (prof["gemm_ms"] * 1e-3) / 1e12 if prof["gemm_ms"] > 0 else None
     traffic = None
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "tf32x3", "data": "synthetic",
+        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": (f"4D Ising HOTRG, T={T_WORK}, h={H_WORK}" if args.batch == 1 else
                                 f"4D Ising HOTRG, {args.batch * world} temperatures in [6.60, 6.72], h={hfield}")
                                + (", pure + sigma + sigma-sigma impure tensors" if impure else "")
                                + f", D_cut={D}, 1024^4 lattice schedule (x,y,z,t cycled); timed steps "
                                f"{args.warmup + 1}..{nsteps} (steady state)",
                    "dcut": D, "temperatures_per_gpu": args.batch, "impure": bool(impure), "lattice": "1024^4",
-                   "precision": "tf32x3 (fp32 storage)", "cuda_graphs": bool(args.graphs),
+                   "precision": f"{args.precision} (fp32 storage)", "cuda_graphs": bool(args.graphs),
                    "l2": "operands larger than L2 (GEMM A and B: 2 x 4.3 GB per step, hi + lo)"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "kernel": "gemm_tf32x3_kernel (block-spin contraction, 2 M N K algorithmic flops per launch)",
+                     "kernel": f"gemm_tf32x3_kernel<{'CfgF16' if args.precision == 'fp16x3' else 'CfgTF32'}> "
+                               "(block-spin contraction, 2 M N K algorithmic flops per launch)",
                      "peak_source": peak_src, "launches": prof["gemm_launches"],
                      "avg_launch_ms": prof["gemm_ms"] / max(1, prof["gemm_launches"]),
                      "tensor_pipe_flops_frac": (3 * achieved / peak) if achieved else None,

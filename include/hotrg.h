@@ -52,10 +52,14 @@ typedef enum {
  * HOTRG_FP64  : FP64 everywhere (DFMA).                                     reference
  * HOTRG_FP32  : FP32 SIMT FMA, FP32 accumulation; tensors stored in FP32.
  * HOTRG_TF32X3: tcgen05 tensor cores, each FP32 operand split into tf32 hi + lo,
- *               products hi*hi + hi*lo + lo*hi accumulated in FP32 (TMEM).
+ *               products hi*hi + hi*lo + lo*hi accumulated in FP32 (TMEM, promoted
+ *               to FP32 registers every 32 k).
+ * HOTRG_FP16X3: the same three products on fp16 hi + lo planes of 2^14 x (kind::f16:
+ *               twice the tensor rate and half the operand bytes of TF32X3; the scale
+ *               keeps normalised tensors inside fp16's normal range).
  * In every mode the Gram matrices are accumulated in FP64, and the eigensolver, the
  * isometries, the norm and ln Z / V are FP64. */
-typedef enum { HOTRG_FP64 = 0, HOTRG_FP32 = 1, HOTRG_TF32X3 = 2 } hotrg_precision;
+typedef enum { HOTRG_FP64 = 0, HOTRG_FP32 = 1, HOTRG_TF32X3 = 2, HOTRG_FP16X3 = 3 } hotrg_precision;
 
 /* Impure tensors propagated with the pure one (same isometries, same c):
  * SIGMA: S (one sigma inserted) -> magnetisation <sigma> = Tr S / Tr T.

@@ -35,7 +35,11 @@ struct TTMArgs {
   double alpha, beta;
 };
 
-enum TTMMode { kTTMStore = 0, kTTMSplitTF32 = 1, kTTMAccumulate = 2 };
+enum TTMMode { kTTMStore = 0, kTTMSplitTF32 = 1, kTTMAccumulate = 2, kTTMSplitF16 = 3 };
+// Scale applied to operands stored as fp16 hi/lo pairs: |x| <= 1 (normalised tensors
+// contracted with isometries) becomes <= 2^14, inside fp16's normal range with room for
+// the products; the GEMM undoes it with alpha * 2^-28.
+constexpr float kF16Scale = 16384.0f;
 
 // One half-Gram job: A[(i1 i2), (j1 j2)] = sum_rest T[i1@l1, i2@l2, rest] T[j1, j2, rest].
 struct GramJob {
@@ -111,9 +115,9 @@ cudaError_t launch_gram_reduce(const double* partial, int nchunks, int64_t RR, d
 cudaError_t launch_gram_merge(const double* A1, const double* A2, int Dn, int Dk, double* G,
                               cudaStream_t st);
 cudaError_t launch_jacobi(const EigPack& jobs, int njobs, int nmax, double cluster_tau, int* status,
-                          cudaStream_t st, int max_sweeps = kJacobiMaxSweeps);
+                          cudaStream_t st, int max_sweeps = kJacobiMaxSweeps, double tie_rel = 1e-8);
 cudaError_t launch_wait_selftest(int* status, unsigned long long limit_ns, cudaStream_t st);
-cudaError_t launch_gemm_tf32x3_v(const float* Ahi, const float* Alo, const float* Bhi, const float* Blo, int64_t Kp,
+cudaError_t launch_gemm_tf32x3_v(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int64_t Kp,
                                  int64_t kps, int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha,
                                  float beta, int* status, cudaStream_t st, int variant);
 

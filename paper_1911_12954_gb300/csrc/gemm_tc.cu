@@ -48,23 +48,30 @@ constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int CHUNK_K = 32;                             // k promoted from TMEM to registers at once
 constexpr unsigned long long kWaitNs = 4000000000ull;
 
-// Pipeline variants. BK fp32 elements per k-block = one swizzle row (128 B or 64 B).
-template <int BK_>
+// Pipeline variants. One k-block = one swizzle row of ROWB bytes (128 B or 64 B) per
+// operand row; F16 selects fp16 operands (kind::f16, K = 16 per MMA) instead of tf32
+// (kind::tf32, K = 8). Either way an MMA k-step spans 32 bytes of the row.
+template <int ROWB, bool F16>
 struct Cfg {
-  static constexpr int BK = BK_;
-  static constexpr int STAGES = BK_ == 32 ? 2 : 4;
-  static constexpr int A_BYTES = BM * BK * 4;
-  static constexpr int B_BYTES = BN * BK * 4;
+  static constexpr bool kF16 = F16;
+  static constexpr int ELT = F16 ? 2 : 4;
+  static constexpr int BK = ROWB / ELT;                            // elements per k-block
+  static constexpr int KSTEPS = ROWB / 32;                         // MMAs per product per k-block
+  static constexpr int STAGES = ROWB == 128 ? 2 : 4;
+  static constexpr int A_BYTES = BM * ROWB;
+  static constexpr int B_BYTES = BN * ROWB;
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr int KB_PER_CHUNK = CHUNK_K / BK;
+  static constexpr int KB_PER_CHUNK = (F16 ? 64 : CHUNK_K) / BK;   // k promoted per chunk: 32 (tf32), 64 (f16)
   static constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
-  static constexpr uint64_t LAYOUT = BK_ == 32 ? 2 : 4;          // UMMA swizzle: 128 B or 64 B
-  static constexpr uint32_t SBO = 8 * BK_ * 4;                    // 8 rows of one swizzle row
+  static constexpr uint64_t LAYOUT = ROWB == 128 ? 2 : 4;         // UMMA swizzle: 128 B or 64 B
+  static constexpr uint32_t SBO = 8 * ROWB;                       // 8 rows of one swizzle row
+  // instruction descriptor: D = F32; A = B = TF32 (2) or F16 (0); both K-major; N = 256, M = 128
+  static constexpr uint32_t IDESC = (1u << 4) | ((F16 ? 0u : 2u) << 7) | ((F16 ? 0u : 2u) << 10) |
+                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 };
-
-// instruction descriptor: D = F32, A = B = TF32, both K-major, N = 256, M = 128
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+using CfgTF32 = Cfg<64, false>;      // default tf32 pipeline: 4 stages of 16-wide k-blocks
+using CfgTF32W = Cfg<128, false>;    // tf32, 2 stages of 32-wide k-blocks
+using CfgF16 = Cfg<64, true>;        // fp16: 4 stages of 32-wide k-blocks
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -143,13 +150,23 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   return d;
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
-      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
-      : "memory");
+template <class CF>
+__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  if constexpr (CF::kF16) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(CF::IDESC), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(CF::IDESC), "r"(accumulate)
+        : "memory");
+  }
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
@@ -285,11 +302,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint64_t ahi = smem_desc<CF>(base), alo = smem_desc<CF>(base + A_BYTES);
         const uint64_t bhi = smem_desc<CF>(base + 2 * A_BYTES), blo = smem_desc<CF>(base + 2 * A_BYTES + B_BYTES);
 #pragma unroll
-        for (int kk = 0; kk < BK / 8; ++kk) {
-          const uint64_t off = (uint64_t)(kk * 32) >> 4;   // 8 tf32 = 32 bytes along the swizzled row
-          mma_tf32(d, alo + off, bhi + off, (first && kk == 0) ? 0u : 1u);
-          mma_tf32(d, ahi + off, blo + off, 1);
-          mma_tf32(d, ahi + off, bhi + off, 1);
+        for (int kk = 0; kk < CF::KSTEPS; ++kk) {
+          const uint64_t off = (uint64_t)(kk * 32) >> 4;   // one k-step = 32 bytes along the swizzled row
+          mma<CF>(d, alo + off, bhi + off, (first && kk == 0) ? 0u : 1u);
+          mma<CF>(d, ahi + off, blo + off, 1);
+          mma<CF>(d, ahi + off, bhi + off, 1);
         }
         mma_commit(&empty[s]);
         if (last) {
@@ -392,27 +409,28 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-bool make_map(CUtensorMap* map, const float* ptr, int64_t rows, int64_t Kp, int64_t kps, int64_t P, int box_rows,
-              int bk) {
+template <class CF>
+bool make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t Kp, int64_t kps, int64_t P, int box_rows) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)P};
-  cuuint64_t strides[2] = {(cuuint64_t)(kps * 4), (cuuint64_t)(rows * kps * 4)};
-  cuuint32_t box[3] = {(cuuint32_t)bk, (cuuint32_t)box_rows, 1};
+  cuuint64_t strides[2] = {(cuuint64_t)(kps * CF::ELT), (cuuint64_t)(rows * kps * CF::ELT)};
+  cuuint32_t box[3] = {(cuuint32_t)CF::BK, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)ptr, dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, bk == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+  CUresult r = enc(map, CF::kF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)ptr,
+                   dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CF::LAYOUT == 2 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
 template <class CF>
-cudaError_t launch_variant(const float* Ahi, const float* Alo, const float* Bhi, const float* Blo, int64_t Kp,
+cudaError_t launch_variant(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int64_t Kp,
                            int64_t kps, int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha,
                            float beta, int* status, cudaStream_t st) {
   CUtensorMap mAhi, mAlo, mBhi, mBlo;
-  if (!make_map(&mAhi, Ahi, M, Kp, kps, P, BM, CF::BK) || !make_map(&mAlo, Alo, M, Kp, kps, P, BM, CF::BK) ||
-      !make_map(&mBhi, Bhi, N, Kp, kps, P, BN, CF::BK) || !make_map(&mBlo, Blo, N, Kp, kps, P, BN, CF::BK))
+  if (!make_map<CF>(&mAhi, Ahi, M, Kp, kps, P, BM) || !make_map<CF>(&mAlo, Alo, M, Kp, kps, P, BM) ||
+      !make_map<CF>(&mBhi, Bhi, N, Kp, kps, P, BN) || !make_map<CF>(&mBlo, Blo, N, Kp, kps, P, BN))
     return cudaErrorInvalidValue;
   static int sms = 0;
   static bool attr = false;
@@ -437,20 +455,23 @@ cudaError_t launch_variant(const float* Ahi, const float* Alo, const float* Bhi,
 }  // namespace tc
 
 // C[M][N] (ldc) = alpha * A B^T + beta * C with A, B in K panels (see tma_load): panel
-// width Kp (kps = its stride, a multiple of 4), P panels, K = P Kp. P = 1, kps = ld is the
-// plain row-major K-major layout. variant 0 (default): k-blocks of 16, 64-byte swizzle,
-// 4 stages; variant 1: k-blocks of 32, 128-byte swizzle, 2 stages.
-cudaError_t launch_gemm_tf32x3_v(const float* Ahi, const float* Alo, const float* Bhi, const float* Blo, int64_t Kp,
+// width Kp (kps = its stride), P panels, K = P Kp. P = 1, kps = ld is the plain row-major
+// K-major layout. variant 0 (default): tf32, k-blocks of 16, 64-byte swizzle, 4 stages;
+// variant 1: tf32, k-blocks of 32, 128-byte swizzle, 2 stages; variant 2: fp16 operands
+// (hi/lo planes of __half), k-blocks of 32, 64-byte swizzle, 4 stages (kps % 8 == 0).
+cudaError_t launch_gemm_tf32x3_v(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int64_t Kp,
                                  int64_t kps, int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha,
                                  float beta, int* status, cudaStream_t st, int variant) {
   using namespace tc;
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (Kp <= 0 || P <= 0 || M > 0x7fffffff || N > 0x7fffffff || Kp * P > 0x7fffffff) return cudaErrorInvalidValue;
-  if ((kps & 3) || kps < Kp) return cudaErrorInvalidValue;
+  if ((kps & (variant == 2 ? 7 : 3)) || kps < Kp) return cudaErrorInvalidValue;
   if ((((uintptr_t)Ahi) | ((uintptr_t)Alo) | ((uintptr_t)Bhi) | ((uintptr_t)Blo)) & 15) return cudaErrorInvalidValue;
+  if (variant == 2)
+    return launch_variant<CfgF16>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
   if (variant == 1)
-    return launch_variant<Cfg<32>>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
-  return launch_variant<Cfg<16>>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
+    return launch_variant<CfgTF32W>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
+  return launch_variant<CfgTF32>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
 }
 
 // Sets the kernels' shared-memory attributes and caches the SM count ahead of time, so no
@@ -461,10 +482,12 @@ void gemm_prepare() {
   if (done) return;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return;
-  cudaFuncSetAttribute(gemm_tf32x3_kernel<Cfg<16>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)Cfg<16>::SMEM_BYTES);
-  cudaFuncSetAttribute(gemm_tf32x3_kernel<Cfg<32>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)Cfg<32>::SMEM_BYTES);
+  cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)CfgTF32::SMEM_BYTES);
+  cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgTF32W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)CfgTF32W::SMEM_BYTES);
+  cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)CfgF16::SMEM_BYTES);
   done = true;
 }
 
@@ -476,6 +499,7 @@ cudaError_t launch_wait_selftest(int* status, unsigned long long limit_ns, cudaS
 cudaError_t launch_gemm_tf32x3(const float* Ahi, const float* Alo, const float* Bhi, const float* Blo, int64_t Kp,
                                int64_t kps, int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha,
                                float beta, int* status, cudaStream_t st) {
+  // plain tf32 entry: pipeline variant 0
   return launch_gemm_tf32x3_v(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st, 0);
 }
 

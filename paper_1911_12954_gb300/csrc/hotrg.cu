@@ -191,6 +191,10 @@ int64_t tensor_elems(const int D[4]) {
   return e;
 }
 
+// Tensor-core modes split each operand into hi + lo planes; operand element size in bytes.
+inline bool tc_mode(int prec) { return prec == HOTRG_TF32X3 || prec == HOTRG_FP16X3; }
+inline size_t operand_size(int prec) { return prec == HOTRG_FP64 ? 8 : (prec == HOTRG_FP16X3 ? 2 : 4); }
+
 double plan_main_flops(const int D[4], const int chi[4], int mu, int a, int b, int c) {
   const double rows = (double)chi[a] * chi[b] * D[c] * D[c] * D[mu];
   const double K = (double)D[a] * D[a] * D[b] * D[b] * D[mu];
@@ -242,12 +246,13 @@ StepPlan make_plan(const int D[4], int mu, int dcut, int prec) {
     p.ksuf = 0;
     for (int q = 1; q <= 5; ++q) {
       const int64_t next = prod * kd[5 - q];
-      if (prec == HOTRG_TF32X3 && next > 4096 && q > 1) break;
+      if (tc_mode(prec) && next > 4096 && q > 1) break;
       prod = next;
       p.ksuf = q;
     }
     p.Kp = prod;
-    p.kps = (p.Kp + 3) / 4 * 4;
+    const int64_t al = prec == HOTRG_FP16X3 ? 8 : 4;     // 16-byte TMA rows
+    p.kps = (p.Kp + al - 1) / al * al;
     p.P = p.K / p.Kp;
   }
   p.xs = p.chi[p.a];
@@ -311,13 +316,14 @@ Scratch scratch_layout(const StepPlan& p, int xs, int xs2, int prec, int impure,
   s.Uside = take((size_t)6 * p.nmax * kMaxLeg * 8);
   const int64_t rowsA = (int64_t)xs * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[p.mu];
   const int64_t rowsB = (int64_t)xs2 * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[p.mu];
-  const bool split = prec == HOTRG_TF32X3;
+  const bool split = tc_mode(prec);
+  const size_t os = operand_size(prec);
   s.O1A = take((size_t)xs * p.E * rs);
-  s.A = take((size_t)nt * p.P * rowsA * p.kps * rs);
-  s.Alo = split ? take((size_t)nt * p.P * rowsA * p.kps * rs) : 0;
+  s.A = take((size_t)nt * p.P * rowsA * p.kps * os);
+  s.Alo = split ? take((size_t)nt * p.P * rowsA * p.kps * os) : 0;
   s.O1B = take((size_t)xs2 * p.E * rs);
-  s.B = take((size_t)nt * p.P * rowsB * p.kps * rs);
-  s.Blo = split ? take((size_t)nt * p.P * rowsB * p.kps * rs) : 0;
+  s.B = take((size_t)nt * p.P * rowsB * p.kps * os);
+  s.Blo = split ? take((size_t)nt * p.P * rowsB * p.kps * os) : 0;
   s.C = take((size_t)nt * rowsA * rowsB * rs);
   s.O3 = take((size_t)rowsA * rowsB / (p.D[p.c] * p.D[p.c]) * p.chi[p.c] * rs);
   s.total = off;
@@ -478,7 +484,7 @@ hotrg_status build_A(hotrg_ctx* ctx, const StepPlan& p, const R* P, const R* Ua,
         {Dm, os[8], 0, o[9]},   // k
     };
     TTMArgs t = make_ttm(d, Db, os[1], (int64_t)Db * cb, 1, 0, 0, 1.0, 0.0);
-    const int mode = Alo ? kTTMSplitTF32 : kTTMStore;
+    const int mode = !Alo ? kTTMStore : (ctx->prec == HOTRG_FP16X3 ? kTTMSplitF16 : kTTMSplitTF32);
     ttm_limits((int64_t)xs * p.E, (int64_t)Db * Db * cb, p.P * ((int64_t)xs * cb * Dc * Dc * Dm) * p.kps);
     LK(1, launch_ttm_r<R>(O1, Ub, A, Alo, t, mode, st), "ttm A2");
   }
@@ -528,7 +534,7 @@ hotrg_status build_B(hotrg_ctx* ctx, const StepPlan& p, const R* Q, const R* Ua,
         {Dm, os[8], 0, o[9]},                   // k
     };
     TTMArgs t = make_ttm(d, Db, os[1], cb, 1, 0, 0, 1.0, 0.0);
-    const int mode = Blo ? kTTMSplitTF32 : kTTMStore;
+    const int mode = !Blo ? kTTMStore : (ctx->prec == HOTRG_FP16X3 ? kTTMSplitF16 : kTTMSplitTF32);
     ttm_limits((int64_t)xs * p.E, (int64_t)Db * Db * cb, p.P * ((int64_t)xs * cb * Dc * Dc * Dm) * p.kps);
     LK(1, launch_ttm_r<R>(O1, Ub, B, Blo, t, mode, st), "ttm B2");
   }
@@ -639,10 +645,15 @@ template <typename R>
 hotrg_status gemm_launch(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R* Blo, const StepPlan& p, R* C,
                          int64_t M, int64_t N, double alpha, double beta, cudaStream_t st) {
   if (ctx->prec == HOTRG_TF32X3) {
-    CK(launch_gemm_tf32x3_v((const float*)A, (const float*)Alo, (const float*)B, (const float*)Blo, p.Kp, p.kps, p.P,
-                            (float*)C, N, M, N, (float)alpha, (float)beta, (int*)(ctx->ws + ctx->L.status), st,
-                            ctx->gemm_variant),
+    CK(launch_gemm_tf32x3_v(A, Alo, B, Blo, p.Kp, p.kps, p.P, (float*)C, N, M, N, (float)alpha, (float)beta,
+                            (int*)(ctx->ws + ctx->L.status), st, ctx->gemm_variant),
        "gemm tf32x3");
+  } else if (ctx->prec == HOTRG_FP16X3) {
+    // operands carry the factor 2^14 each
+    const float unscale = 1.0f / (kF16Scale * kF16Scale);
+    CK(launch_gemm_tf32x3_v(A, Alo, B, Blo, p.Kp, p.kps, p.P, (float*)C, N, M, N, (float)alpha * unscale,
+                            (float)beta, (int*)(ctx->ws + ctx->L.status), st, 2),
+       "gemm f16x3");
   } else {
     if (p.P != 1) return HOTRG_EUNSUPPORTED;
     CK(launch_gemm_simt<R>(A, p.kps, B, p.kps, C, N, M, N, p.K, alpha, beta, st), "gemm simt");
@@ -659,7 +670,8 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
   const int kstep = ctx->k;  // steps done before this one
   int* status = (int*)(ctx->ws + ctx->L.status);
   const int nt = ntensors(ctx->impure_active);
-  const bool split = ctx->prec == HOTRG_TF32X3;
+  const bool split = tc_mode(ctx->prec);
+  const size_t osz = operand_size(ctx->prec);
   const int64_t rowsA = (int64_t)p.xs * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[mu];
   const int64_t rowsB = (int64_t)p.xs2 * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[mu];
   const int ca = p.chi[p.a];
@@ -744,7 +756,8 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
       }
     }
     const bool fp64 = ctx->prec == HOTRG_FP64;
-    LK(1, launch_jacobi(ep, 6, nmax, fp64 ? 1e-10 : 1e-6, status, st, ctx->jacobi_sweeps), "jacobi");
+    LK(1, launch_jacobi(ep, 6, nmax, fp64 ? 1e-10 : 1e-6, status, st, ctx->jacobi_sweeps, fp64 ? 1e-8 : 1e-4),
+       "jacobi");
     SelectPack sp{};
     double* U64 = (double*)(ctx->ws + ctx->L.U64) + (int64_t)bidx * 4 * kMaxGramN * kMaxLeg;
     R* Ur = (R*)(ctx->ws + ctx->L.Ur) + (int64_t)bidx * 4 * kMaxGramN * kMaxLeg;
@@ -776,10 +789,12 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
     // ---------------------------------------------------------------- 3. contraction
     R* O1A = (R*)(sb + sc.O1A);
     R* O1B = (R*)(sb + sc.O1B);
-    R* Abuf = (R*)(sb + sc.A);
-    R* Alob = split ? (R*)(sb + sc.Alo) : nullptr;
-    R* Bbuf = (R*)(sb + sc.B);
-    R* Blob = split ? (R*)(sb + sc.Blo) : nullptr;
+    // operand planes, addressed in bytes (fp16 operands are half the storage type's size)
+    char* Abuf = sb + sc.A;
+    char* Alob = split ? sb + sc.Alo : nullptr;
+    char* Bbuf = sb + sc.B;
+    char* Blob = split ? sb + sc.Blo : nullptr;
+    auto opnd = [&](char* base, int64_t elems) { return base ? (R*)(base + elems * (int64_t)osz) : (R*)nullptr; };
     R* Cbuf = (R*)(sb + sc.C);
     R* O3 = (R*)(sb + sc.O3);
     const int64_t Asz = p.P * rowsA * p.kps, Bsz = p.P * rowsB * p.kps, Csz = rowsA * rowsB;
@@ -793,8 +808,8 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
     // the CUDA-core GEMM at K, so the operand buffers need no clearing.
     auto buildB = [&](int x20, int xs2) -> hotrg_status {
       for (int w = 0; w < nt; ++w) {
-        hotrg_status s = build_B<R>(ctx, p, src[w], Ua, Ub, x20, xs2, O1B, Bbuf + w * Bsz,
-                                    split ? Blob + w * Bsz : nullptr, st);
+        hotrg_status s = build_B<R>(ctx, p, src[w], Ua, Ub, x20, xs2, O1B, opnd(Bbuf, w * Bsz),
+                                    opnd(Blob, w * Bsz), st);
         if (s != HOTRG_OK) return s;
       }
       return HOTRG_OK;
@@ -807,8 +822,8 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
       const int xs = std::min(p.xs, ca - x0);
       const int64_t rA = (int64_t)xs * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[mu];
       for (int w = 0; w < nt; ++w) {
-        hotrg_status s = build_A<R>(ctx, p, src[w], Ua, Ub, x0, xs, O1A, Abuf + w * Asz,
-                                    split ? Alob + w * Asz : nullptr, st);
+        hotrg_status s = build_A<R>(ctx, p, src[w], Ua, Ub, x0, xs, O1A, opnd(Abuf, w * Asz),
+                                    opnd(Alob, w * Asz), st);
         if (s != HOTRG_OK) return s;
       }
       for (int x20 = 0; x20 < ca; x20 += p.xs2) {
@@ -818,10 +833,10 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
           hotrg_status s = buildB(x20, xs2);
           if (s != HOTRG_OK) return s;
         }
-        auto Ap = [&](int w) { return Abuf + w * Asz; };
-        auto Alp = [&](int w) { return split ? Alob + w * Asz : nullptr; };
-        auto Bp = [&](int w) { return Bbuf + w * Bsz; };
-        auto Blp = [&](int w) { return split ? Blob + w * Bsz : nullptr; };
+        auto Ap = [&](int w) { return opnd(Abuf, w * Asz); };
+        auto Alp = [&](int w) { return opnd(Alob, w * Asz); };
+        auto Bp = [&](int w) { return opnd(Bbuf, w * Bsz); };
+        auto Blp = [&](int w) { return opnd(Blob, w * Bsz); };
         hotrg_status s;
         // C_T = A(T) B(T)^T
         s = gemm<R>(ctx, Ap(0), Alp(0), Bp(0), Blp(0), p, Cbuf, rA, rB, 1.0, 0.0, st);
@@ -904,7 +919,7 @@ const char* hotrg_last_error(void) { return g_last_error.c_str(); }
 
 hotrg_status hotrg_create(hotrg_ctx** out, int batch, int dcut_max, int prec, int impure_mask) {
   if (!out || batch < 1 || batch > 4096 || dcut_max < 2 || dcut_max > kMaxLeg) return HOTRG_EINVAL;
-  if (prec != HOTRG_FP64 && prec != HOTRG_FP32 && prec != HOTRG_TF32X3) return HOTRG_EINVAL;
+  if (prec != HOTRG_FP64 && prec != HOTRG_FP32 && prec != HOTRG_TF32X3 && prec != HOTRG_FP16X3) return HOTRG_EINVAL;
   if (impure_mask < 0 || impure_mask > 3 || impure_mask == HOTRG_IMPURE_SIGMASIGMA) return HOTRG_EINVAL;
   hotrg_ctx* c = new hotrg_ctx();
   c->batch = batch;

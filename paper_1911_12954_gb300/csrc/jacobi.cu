@@ -13,8 +13,9 @@
 // above the rounding noise of the Gram matrix: 1e-10 when the tensors are FP64, 1e-6
 // when they are stored in FP32); inside a cluster the
 // basis is built by repeatedly taking the unit vector e_i with the longest projection on
-// the not-yet-covered part of the cluster's eigenspace (lowest i within a relative 1e-8
-// of the longest) and normalising that projection. This gauge depends only on the
+// the not-yet-covered part of the cluster's eigenspace (lowest i within a relative
+// tie_rel of the longest: 1e-8 for FP64 tensors, 1e-4 for FP32-stored ones, whose noise
+// would otherwise break exact symmetric ties at random) and normalising that projection. This gauge depends only on the
 // eigenspaces, so it does not depend on the eigensolver.
 //
 // select_kernel: per transverse direction, the side (nu or nu') with the smaller
@@ -27,7 +28,6 @@
 
 namespace hotrg {
 
-constexpr double kTieRel = 1e-8;
 constexpr int kJT = 256;            // threads per Jacobi CTA
 constexpr int kSmemJacobiN = 96;    // A and V in shared memory up to this n
 
@@ -58,7 +58,8 @@ __device__ double block_sum(double v, double* red) {
 }
 
 __global__ void __launch_bounds__(kJT) jacobi_kernel(const __grid_constant__ EigPack jobs, int use_smem,
-                                                     double cluster_tau, int max_sweeps, int* status) {
+                                                     double cluster_tau, double tie_rel, int max_sweeps,
+                                                     int* status) {
   extern __shared__ double dyn[];
   __shared__ double cs[kMaxGramN / 2 + 1], sn[kMaxGramN / 2 + 1];
   __shared__ int pp[kMaxGramN / 2 + 1], qq[kMaxGramN / 2 + 1];
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(kJT) jacobi_kernel(const __grid_constant__ Eig
         for (int w = 0; w < kJT / 32; ++w) m2 = fmax(m2, red[w]);
         int ip = 0;
         for (int i = 0; i < n; ++i)
-          if (nrm[i] >= (1.0 - kTieRel) * m2) {
+          if (nrm[i] >= (1.0 - tie_rel) * m2) {
             ip = i;
             break;
           }
@@ -247,7 +248,7 @@ void jacobi_prepare() {
 }
 
 cudaError_t launch_jacobi(const EigPack& jobs, int njobs, int nmax, double cluster_tau, int* status,
-                          cudaStream_t st, int max_sweeps) {
+                          cudaStream_t st, int max_sweeps, double tie_rel) {
   const int smem_n = nmax <= kSmemJacobiN ? nmax : 0;
   const size_t smem = (size_t)2 * smem_n * smem_n * sizeof(double);
   static bool attr = false;
@@ -257,7 +258,7 @@ cudaError_t launch_jacobi(const EigPack& jobs, int njobs, int nmax, double clust
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  jacobi_kernel<<<njobs, kJT, smem, st>>>(jobs, smem_n > 0 ? 1 : 0, cluster_tau, max_sweeps, status);
+  jacobi_kernel<<<njobs, kJT, smem, st>>>(jobs, smem_n > 0 ? 1 : 0, cluster_tau, tie_rel, max_sweeps, status);
   return cudaGetLastError();
 }
 

@@ -8,6 +8,7 @@
 //  * init_kernel    : the 4D Ising site tensors T and S (Fig. 1A) and ln c_0.
 //  * sumsq/normalise: c = ||T'||_F in FP64, ln c / 2^k accumulated (ln Z / V), T' /= c.
 //  * trace_kernel   : Tr T (each leg joined to its primed partner), FP64.
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include <type_traits>
@@ -66,6 +67,11 @@ __global__ void __launch_bounds__(256) ttm_kernel(const TI* __restrict__ in, con
         const float hi = tf32_round(v);
         out[o1] = (TO)hi;
         out_lo[o1] = (TO)tf32_round(v - hi);
+      } else if (MODE == kTTMSplitF16) {
+        const float v = (float)acc * kF16Scale;
+        const __half hi = __float2half_rn(v);
+        ((__half*)out)[o1] = hi;
+        ((__half*)out_lo)[o1] = __float2half_rn(v - __half2float(hi));
       } else if (MODE == kTTMAccumulate) {
         out[o1] = (TO)(acc + (Acc)a.beta * (Acc)out[o1]);
       } else {
@@ -135,6 +141,12 @@ __global__ void __launch_bounds__(256) ttm_fiber_kernel(const R* __restrict__ in
           const float hi = tf32_round(v);
           out[o] = (R)hi;
           out_lo[o] = (R)tf32_round(v - hi);
+        } else if (MODE == kTTMSplitF16) {
+          // fp16 hi + lo of 2^14 x: the pair keeps 22 significant bits
+          const float v = (float)acc * kF16Scale;
+          const __half hi = __float2half_rn(v);
+          ((__half*)out)[o] = hi;
+          ((__half*)out_lo)[o] = __float2half_rn(v - __half2float(hi));
         } else {
           out[o] = acc;
         }
@@ -245,9 +257,11 @@ cudaError_t launch_fiber(const R* in, const R* U, R* out, R* out_lo, const Fiber
   }
   if (J <= 16) {
     if (mode == kTTMSplitTF32) ttm_fiber_kernel<R, 16, kTTMSplitTF32><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
+    else if (mode == kTTMSplitF16) ttm_fiber_kernel<R, 16, kTTMSplitF16><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
     else ttm_fiber_kernel<R, 16, kTTMStore><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
   } else {
     if (mode == kTTMSplitTF32) ttm_fiber_kernel<R, 64, kTTMSplitTF32><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
+    else if (mode == kTTMSplitF16) ttm_fiber_kernel<R, 64, kTTMSplitF16><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
     else ttm_fiber_kernel<R, 64, kTTMStore><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
   }
   return cudaGetLastError();
@@ -272,6 +286,9 @@ cudaError_t launch_ttm(const TI* in, const TU* U, TO* out, TO* out_lo, const TTM
       break;
     case kTTMSplitTF32:
       ttm_kernel<TI, TU, TO, kTTMSplitTF32><<<(unsigned)blocks, threads, 0, st>>>(in, U, out, out_lo, a);
+      break;
+    case kTTMSplitF16:
+      ttm_kernel<TI, TU, TO, kTTMSplitF16><<<(unsigned)blocks, threads, 0, st>>>(in, U, out, out_lo, a);
       break;
     default:
       ttm_kernel<TI, TU, TO, kTTMAccumulate><<<(unsigned)blocks, threads, 0, st>>>(in, U, out, out_lo, a);

@@ -15,8 +15,8 @@ import numpy as np
 
 from . import build as _build
 
-FP64, FP32, TF32X3 = 0, 1, 2
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32x3": TF32X3}
+FP64, FP32, TF32X3, FP16X3 = 0, 1, 2, 3
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32x3": TF32X3, "fp16x3": FP16X3}
 IMPURE_NONE, IMPURE_SIGMA, IMPURE_SIGMASIGMA = 0, 1, 2
 OPT_JACOBI_SWEEPS, OPT_GEMM_VARIANT, OPT_GRAPHS = 1, 2, 3
 

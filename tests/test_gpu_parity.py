@@ -84,7 +84,7 @@ def test_single_step_random_tensor_fp64(dims, mu, dcut):
         assert info["eps"][n] == pytest.approx(isos[n].eps, rel=1e-9, abs=1e-13)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 3e-5), ("tf32x3", 3e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp32", 3e-5), ("tf32x3", 3e-5), ("fp16x3", 3e-5)])
 @pytest.mark.parametrize("dims,mu,dcut", [CASES[0], CASES[3], CASES[5]])
 def test_single_step_random_tensor_mixed(prec, tol, dims, mu, dcut):
     T = random_tensor(2000 + sum(dims) * 7 + mu, dims)
@@ -116,7 +116,7 @@ def test_sliced_contraction_matches_unsliced():
     assert np.allclose(small.tensor(), full.tensor(), atol=1e-14)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-14), ("tf32x3", 1e-6)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-14), ("tf32x3", 1e-6), ("fp16x3", 1e-6)])
 def test_two_dimensional_slicing_matches_unsliced(prec, tol):
     """Workspaces between the smallest that works and the unsliced plan make the step
     slice the new X (rows of A) and then also the new X' (rows of B, columns of C); every
@@ -218,7 +218,7 @@ def test_batch_of_temperatures_matches_single_runs():
         assert lnz[j] == pytest.approx(H.run(4, 1 / T, 0.0, 4, 6).lnZ(), rel=1e-10)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("tf32x3", 2e-6)])
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("tf32x3", 2e-6), ("fp16x3", 2e-6)])
 def test_mixed_run_vs_golden(prec, tol):
     """|Delta ln Z/V| of the FP32-storage modes against the FP64 oracle, D_cut = 4, 16^4."""
     gd = _golden("ising4d_T6.65_h0_dcut4_16steps")
@@ -251,14 +251,15 @@ def test_errors_are_reported_not_raised_on_device():
 
 
 # ------------------------------------------------------------------ D_cut = 8, the 1024^4 workload
-def test_dcut8_tf32x3_first_8_steps_vs_golden():
+@pytest.mark.parametrize("prec", ["tf32x3", "fp16x3"])
+def test_dcut8_mixed_first_8_steps_vs_golden(prec):
     """The benchmark's workload (T = 6.65, h = 0, D_cut = 8, towards 1024^4) in the launch
     configuration bench.py times: |Delta ln Z/V| <= 1e-6 against the FP64 oracle over the
     first 8 steps (step 2 cuts through a degenerate eigenvalue cluster)."""
     gd = _golden("ising4d_T6.65_h0_dcut8_8steps")
     cfg = gd["config"]
     sched = [(s["mu"], cfg["dcut"]) for s in gd["steps"]]
-    g = _gpu(batch=1, dcut_max=8, precision="tf32x3", schedule=sched)
+    g = _gpu(batch=1, dcut_max=8, precision=prec, schedule=sched)
     g.init_tensor(gd["beta"], cfg["h"])
     for i, (mu, dc) in enumerate(sched):
         g.step(mu, dc)
@@ -285,7 +286,7 @@ def test_dcut8_fp64_first_4_steps_vs_golden():
             assert info["eps"][int(n)] == pytest.approx((e0, e1), rel=1e-7, abs=1e-12)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("tf32x3", 3e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("tf32x3", 3e-5), ("fp16x3", 3e-5)])
 def test_long_closing_contraction(prec, tol):
     """Uniform bond dimension 9: the closing passes contract D_c^2 = 81 > 64 values per
     output (the register-accumulator fibre kernel); chi = 2 keeps the GEMM small. A
@@ -305,13 +306,14 @@ def test_long_closing_contraction(prec, tol):
 
 
 # ------------------------------------------------------------------ impure tensors in mixed precision
-def test_tf32x3_impure_run_vs_golden():
-    """sigma and sigma-sigma impure tensors through the tensor-core path, D_cut = 4,
+@pytest.mark.parametrize("prec", ["tf32x3", "fp16x3"])
+def test_mixed_impure_run_vs_golden(prec):
+    """sigma and sigma-sigma impure tensors through the tensor-core paths, D_cut = 4,
     h = 1e-5, 12 steps: <sigma>, <sigma sigma> and E/V against the FP64 oracle."""
     gd = _golden("ising4d_T6.65_h1e-5_dcut4_impure_12steps")
     cfg = gd["config"]
     sched = [(s["mu"], cfg["dcut"]) for s in gd["steps"]]
-    g = _gpu(batch=2, dcut_max=cfg["dcut"], precision="tf32x3", impure=3, schedule=sched)
+    g = _gpu(batch=2, dcut_max=cfg["dcut"], precision=prec, impure=3, schedule=sched)
     g.init_tensor([gd["beta"]] * 2, cfg["h"])
     for i, (mu, dc) in enumerate(sched):
         g.step(mu, dc)
