@@ -168,8 +168,10 @@ hotrg_status hotrg_step_flops(const hotrg_ctx* ctx, int dir, int dcut, double* m
 /* Tuning and test options of a context (host-side; take effect from the next step).
  * HOTRG_OPT_JACOBI_SWEEPS: sweep limit of the eigensolver, 1..60 (default 60); reaching it
  *   raises HOTRG_ENOCONV at the next synchronising call (used to test that path).
- * HOTRG_OPT_GEMM_VARIANT: tensor-core GEMM pipeline, 0 = 4 stages of 16-wide k-blocks
- *   (default), 1 = 2 stages of 32-wide k-blocks.
+ * HOTRG_OPT_GEMM_VARIANT: tensor-core GEMM pipeline. TF32X3: 0 = 4 stages of 16-wide
+ *   k-blocks (default), 1 = 2 stages of 32-wide k-blocks. FP16X3: 0 = partial sums promoted
+ *   from the tensor-core accumulator to FP32 registers every 128 k (default), 1 = every 64 k
+ *   (slower, a smaller truncation bias).
  * HOTRG_OPT_GRAPHS: 1 = capture each distinct step (plan, buffer, first step or not) once
  *   into a CUDA graph and replay it (every kernel of the step for every batch element in
  *   one graph launch); needs a non-default stream (hotrg_set_stream). Per-GEMM profiling

@@ -110,8 +110,8 @@ cudaError_t launch_ttm(const TI* in, const TU* U, TO* out, TO* out_lo, const TTM
 
 template <typename R>
 cudaError_t launch_gram(const GramPack& jobs, int njobs, int Rmax, int nchunks, cudaStream_t st);
-cudaError_t launch_gram_reduce(const double* partial, int nchunks, int64_t RR, double* out,
-                               cudaStream_t st);
+cudaError_t launch_gram_reduce(const GramPack& jobs, int njobs, int nchunks, int64_t RRmax, int64_t out_stride,
+                               double* out, cudaStream_t st);
 cudaError_t launch_gram_merge(const double* A1, const double* A2, int Dn, int Dk, double* G,
                               cudaStream_t st);
 cudaError_t launch_jacobi(const EigPack& jobs, int njobs, int nmax, double cluster_tau, int* status,

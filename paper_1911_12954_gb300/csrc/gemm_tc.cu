@@ -10,15 +10,19 @@
 // The tensor cores add each MMA's products into the FP32 accumulator with truncation,
 // so an accumulator that runs over the whole K picks up a bias that grows linearly with
 // K (measured 2.5e-4 relative at K = 32768). The kernel therefore promotes the partial
-// sum of every k-block of 32 (12 MMAs) from TMEM into FP32 registers, where the sums
-// are rounded to nearest: the truncation bias is bounded by one k-block's worth.
+// sum of every chunk of k (32 for tf32; 128, or 64 in the short-chunk variant, for fp16)
+// from TMEM into FP32 registers, where the sums are rounded to nearest: the truncation
+// bias is bounded by one chunk's worth. Each promotion reads the whole 128 x 256 FP32
+// accumulator out of TMEM and holds the MMAs back for a few hundred cycles, so the chunk
+// is as long as the accuracy allows (at D = 8, 64-k chunks cost 17 % of the MMA time and
+// 128-k chunks 7 %).
 //
 // Structure: persistent kernel, one CTA per SM, 10 warps.
 //   warp 0 lane 0 : TMA producer. Per k-block of 32 (one 128-byte swizzle row), four
 //                   tiles (Ahi, Alo: 128x32; Bhi, Blo: 256x32) land in one pipeline stage
 //                   through cp.async.bulk.tensor with 128-byte swizzle.
-//   warp 1 lane 0 : MMA issuer. Per k-block, 4 k-steps x 3 products of
-//                   tcgen05.mma.cta_group::1.kind::tf32 (M=128, N=256, K=8) into one of
+//   warp 1 lane 0 : MMA issuer. Per k-block, k-steps x 3 products of
+//                   tcgen05.mma.cta_group::1.kind::tf32 or kind::f16 (M=128, N=256) into one of
 //                   two TMEM chunk accumulators (2 x 256 of the 512 columns); commits free
 //                   the stage and hand the chunk to the epilogue.
 //   warps 2..9    : promotion + epilogue. Warp w reads TMEM lane quarter w % 4 and column
@@ -45,13 +49,13 @@ constexpr int TMEM_COLS = 2 * BN;                       // two chunk accumulator
 constexpr int GROUP_M = 16;
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
-constexpr int CHUNK_K = 32;                             // k promoted from TMEM to registers at once
 constexpr unsigned long long kWaitNs = 4000000000ull;
 
 // Pipeline variants. One k-block = one swizzle row of ROWB bytes (128 B or 64 B) per
 // operand row; F16 selects fp16 operands (kind::f16, K = 16 per MMA) instead of tf32
-// (kind::tf32, K = 8). Either way an MMA k-step spans 32 bytes of the row.
-template <int ROWB, bool F16>
+// (kind::tf32, K = 8). Either way an MMA k-step spans 32 bytes of the row. CHUNK is the
+// k promoted from TMEM to registers at once.
+template <int ROWB, bool F16, int CHUNK>
 struct Cfg {
   static constexpr bool kF16 = F16;
   static constexpr int ELT = F16 ? 2 : 4;
@@ -61,7 +65,8 @@ struct Cfg {
   static constexpr int A_BYTES = BM * ROWB;
   static constexpr int B_BYTES = BN * ROWB;
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr int KB_PER_CHUNK = (F16 ? 64 : CHUNK_K) / BK;   // k promoted per chunk: 32 (tf32), 64 (f16)
+  static constexpr int KB_PER_CHUNK = CHUNK / BK;
+  static_assert(CHUNK % BK == 0, "a chunk is a whole number of k-blocks");
   static constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
   static constexpr uint64_t LAYOUT = ROWB == 128 ? 2 : 4;         // UMMA swizzle: 128 B or 64 B
   static constexpr uint32_t SBO = 8 * ROWB;                       // 8 rows of one swizzle row
@@ -69,9 +74,10 @@ struct Cfg {
   static constexpr uint32_t IDESC = (1u << 4) | ((F16 ? 0u : 2u) << 7) | ((F16 ? 0u : 2u) << 10) |
                                     ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 };
-using CfgTF32 = Cfg<64, false>;      // default tf32 pipeline: 4 stages of 16-wide k-blocks
-using CfgTF32W = Cfg<128, false>;    // tf32, 2 stages of 32-wide k-blocks
-using CfgF16 = Cfg<64, true>;        // fp16: 4 stages of 32-wide k-blocks
+using CfgTF32 = Cfg<64, false, 32>;     // default tf32 pipeline: 4 stages of 16-wide k-blocks
+using CfgTF32W = Cfg<128, false, 32>;   // tf32, 2 stages of 32-wide k-blocks
+using CfgF16 = Cfg<64, true, 128>;      // fp16: 4 stages of 32-wide k-blocks, 128-k chunks
+using CfgF16S = Cfg<64, true, 64>;      // fp16 with 64-k chunks
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -458,15 +464,19 @@ cudaError_t launch_variant(const void* Ahi, const void* Alo, const void* Bhi, co
 // width Kp (kps = its stride), P panels, K = P Kp. P = 1, kps = ld is the plain row-major
 // K-major layout. variant 0 (default): tf32, k-blocks of 16, 64-byte swizzle, 4 stages;
 // variant 1: tf32, k-blocks of 32, 128-byte swizzle, 2 stages; variant 2: fp16 operands
-// (hi/lo planes of __half), k-blocks of 32, 64-byte swizzle, 4 stages (kps % 8 == 0).
+// (hi/lo planes of __half), k-blocks of 32, 64-byte swizzle, 4 stages, 128-k promotion
+// chunks (kps % 8 == 0); variant 3: as 2 with 64-k chunks.
 cudaError_t launch_gemm_tf32x3_v(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int64_t Kp,
                                  int64_t kps, int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha,
                                  float beta, int* status, cudaStream_t st, int variant) {
   using namespace tc;
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (Kp <= 0 || P <= 0 || M > 0x7fffffff || N > 0x7fffffff || Kp * P > 0x7fffffff) return cudaErrorInvalidValue;
-  if ((kps & (variant == 2 ? 7 : 3)) || kps < Kp) return cudaErrorInvalidValue;
+  const bool f16 = variant == 2 || variant == 3;
+  if ((kps & (f16 ? 7 : 3)) || kps < Kp) return cudaErrorInvalidValue;
   if ((((uintptr_t)Ahi) | ((uintptr_t)Alo) | ((uintptr_t)Bhi) | ((uintptr_t)Blo)) & 15) return cudaErrorInvalidValue;
+  if (variant == 3)
+    return launch_variant<CfgF16S>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
   if (variant == 2)
     return launch_variant<CfgF16>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
   if (variant == 1)
@@ -488,6 +498,8 @@ void gemm_prepare() {
                        (int)CfgTF32W::SMEM_BYTES);
   cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)CfgF16::SMEM_BYTES);
+  cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgF16S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)CfgF16S::SMEM_BYTES);
   done = true;
 }
 

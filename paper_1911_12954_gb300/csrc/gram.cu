@@ -8,14 +8,28 @@
 //   G[(a1 a2),(b1 b2)] = sum_{k,k'} A1[(a1,k),(b1,k')] A2[(a2,k),(b2,k')].
 // gram_kernel computes 64x64 tiles of one half-Gram over one chunk of the summed index
 // (split-K: K = D^6 is long, R = D_l D_mu is short), products in the storage precision
-// accumulated in FP64 per 32-term slice; gram_reduce adds the chunks in a fixed order
-// (deterministic); gram_merge forms G in FP64.
+// summed per 32-term slice, the slice sums accumulated exactly: in FP64 for FP64 tensors,
+// for FP32 ones as an unevaluated pair of floats (hi + lo, Knuth's TwoSum), which carries
+// about 48 bits without the FP64 pipe (a few FP64 operations per clock per SM on this
+// chip, against 128 FP32 FMAs). gram_reduce adds the chunks of every job in a fixed order
+// (deterministic, one launch); gram_merge forms G in FP64.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace hotrg {
 
 constexpr int kGT = 64;   // output tile
 constexpr int kGK = 32;   // k slice held in shared memory
+
+// hi + lo += x exactly up to the rounding of lo (TwoSum of hi and x).
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float t = hi + x;
+  const float bp = t - hi;
+  const float err = (hi - (t - bp)) + (x - bp);
+  hi = t;
+  lo += err;
+}
 
 template <typename R>
 __global__ void __launch_bounds__(256) gram_kernel(const __grid_constant__ GramPack jobs, int Rmax, int nchunks) {
@@ -25,6 +39,7 @@ __global__ void __launch_bounds__(256) gram_kernel(const __grid_constant__ GramP
   const int ti = blockIdx.y / ((Rmax + kGT - 1) / kGT);
   const int tj = blockIdx.y % ((Rmax + kGT - 1) / kGT);
   if (ti >= ntile || tj >= ntile) return;
+  const bool diag = ti == tj;                 // both operand tiles are the same rows
   const R* T = (const R*)jb.T;
   const int64_t kchunk = (jb.K + nchunks - 1) / nchunks;
   const int64_t k0 = blockIdx.x * kchunk;
@@ -44,19 +59,24 @@ __global__ void __launch_bounds__(256) gram_kernel(const __grid_constant__ GramP
     const int j = tj * kGT + (tid - kGT);
     rowj[tid - kGT] = j < Rn ? (j / jb.D2) * jb.s1 + (j % jb.D2) * jb.s2 : -1;
   }
-  double acc[4][4];
+  using Pair = typename std::conditional<sizeof(R) == 8, double, float>::type;
+  Pair acc[4][4], accl[4][4];     // accl: low parts of the float pairs (unused for FP64)
   for (int a = 0; a < 4; ++a)
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int b = 0; b < 4; ++b) acc[a][b] = accl[a][b] = 0;
+  const R(*Xb)[kGT + 1] = diag ? Xi : Xj;
 
   for (int64_t kb = k0; kb < k1; kb += kGK) {
     __syncthreads();
     if (tid < kGK) {
-      int64_t k = kb + tid, off = 0;
-      if (k < k1) {
+      // K = prod of six bond dimensions <= 16^6 < 2^32: the summed index decodes in 32 bits
+      uint32_t k = (uint32_t)(kb + tid);
+      int64_t off = 0;
+      if (kb + tid < k1) {
         for (int d = jb.nrest - 1; d >= 0; --d) {
-          const int64_t i = k % jb.rdims[d];
-          k /= jb.rdims[d];
-          off += i * jb.rst[d];
+          const uint32_t n = (uint32_t)jb.rdims[d];
+          const uint32_t i = k % n;
+          k /= n;
+          off += (int64_t)i * jb.rst[d];
         }
         roff[tid] = off;
       } else {
@@ -67,9 +87,12 @@ __global__ void __launch_bounds__(256) gram_kernel(const __grid_constant__ GramP
     for (int e = tid; e < kGK * kGT; e += 256) {
       const int r = e / kGK, kk = e % kGK;   // consecutive threads: consecutive summed index
       const int64_t ro = roff[kk];
-      const int64_t oi = rowi[r], oj = rowj[r];
+      const int64_t oi = rowi[r];
       Xi[kk][r] = (ro >= 0 && oi >= 0) ? T[oi + ro] : (R)0;
-      Xj[kk][r] = (ro >= 0 && oj >= 0) ? T[oj + ro] : (R)0;
+      if (!diag) {
+        const int64_t oj = rowj[r];
+        Xj[kk][r] = (ro >= 0 && oj >= 0) ? T[oj + ro] : (R)0;
+      }
     }
     __syncthreads();
     R part[4][4];
@@ -79,12 +102,15 @@ __global__ void __launch_bounds__(256) gram_kernel(const __grid_constant__ GramP
     for (int kk = 0; kk < kGK; ++kk) {
       R vi[4], vj[4];
       for (int a = 0; a < 4; ++a) vi[a] = Xi[kk][ty * 4 + a];
-      for (int b = 0; b < 4; ++b) vj[b] = Xj[kk][tx * 4 + b];
+      for (int b = 0; b < 4; ++b) vj[b] = Xb[kk][tx * 4 + b];
       for (int a = 0; a < 4; ++a)
         for (int b = 0; b < 4; ++b) part[a][b] = fma(vi[a], vj[b], part[a][b]);
     }
     for (int a = 0; a < 4; ++a)
-      for (int b = 0; b < 4; ++b) acc[a][b] += (double)part[a][b];
+      for (int b = 0; b < 4; ++b) {
+        if constexpr (sizeof(R) == 8) acc[a][b] += part[a][b];
+        else two_sum_acc(acc[a][b], accl[a][b], part[a][b]);
+      }
   }
   double* out = jb.partial + (int64_t)blockIdx.x * Rn * Rn;
   for (int a = 0; a < 4; ++a) {
@@ -92,7 +118,7 @@ __global__ void __launch_bounds__(256) gram_kernel(const __grid_constant__ GramP
     if (i >= Rn) continue;
     for (int b = 0; b < 4; ++b) {
       const int j = tj * kGT + tx * 4 + b;
-      if (j < Rn) out[(int64_t)i * Rn + j] = acc[a][b];
+      if (j < Rn) out[(int64_t)i * Rn + j] = (double)acc[a][b] + (double)accl[a][b];
     }
   }
 }
@@ -107,20 +133,37 @@ cudaError_t launch_gram(const GramPack& jobs, int njobs, int Rmax, int nchunks, 
 template cudaError_t launch_gram<double>(const GramPack&, int, int, int, cudaStream_t);
 template cudaError_t launch_gram<float>(const GramPack&, int, int, int, cudaStream_t);
 
-// out[e] = sum_c partial[c][e], chunks added in increasing c.
-__global__ void gram_reduce_kernel(const double* __restrict__ partial, int nchunks, int64_t RR,
-                                   double* __restrict__ out) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < RR; e += (int64_t)gridDim.x * blockDim.x) {
+// out_i[e] = sum_c partial_i[c][e] for every job i of the pack, in one launch. A block
+// takes 32 consecutive entries of one job; its 8 warps add interleaved chunk subsets
+// (warp w: chunks c = w mod 8, in increasing c) and the 8 warp sums are added in warp
+// order, so the result does not depend on scheduling.
+__global__ void __launch_bounds__(256) gram_reduce_kernel(const __grid_constant__ GramPack jobs, int nchunks,
+                                                          int64_t out_stride, double* __restrict__ out) {
+  const GramJob& jb = jobs.j[blockIdx.y];
+  const int64_t RR = (int64_t)jb.D1 * jb.D2 * jb.D1 * jb.D2;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __shared__ double red[8][32];
+  for (int64_t e0 = (int64_t)blockIdx.x * 32; e0 < RR; e0 += (int64_t)gridDim.x * 32) {
+    const int64_t e = e0 + lane;
     double s = 0;
-    for (int c = 0; c < nchunks; ++c) s += partial[c * RR + e];
-    out[e] = s;
+    if (e < RR)
+      for (int c = w; c < nchunks; c += 8) s += jb.partial[(int64_t)c * RR + e];
+    red[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && e < RR) {
+      double t = 0;
+      for (int q = 0; q < 8; ++q) t += red[q][lane];
+      out[(int64_t)blockIdx.y * out_stride + e] = t;
+    }
+    __syncthreads();
   }
 }
 
-cudaError_t launch_gram_reduce(const double* partial, int nchunks, int64_t RR, double* out, cudaStream_t st) {
-  int64_t blocks = (RR + 255) / 256;
+cudaError_t launch_gram_reduce(const GramPack& jobs, int njobs, int nchunks, int64_t RRmax, int64_t out_stride,
+                               double* out, cudaStream_t st) {
+  int64_t blocks = (RRmax + 31) / 32;
   if (blocks > 1024) blocks = 1024;
-  gram_reduce_kernel<<<(unsigned)blocks, 256, 0, st>>>(partial, nchunks, RR, out);
+  gram_reduce_kernel<<<dim3((unsigned)blocks, (unsigned)njobs), 256, 0, st>>>(jobs, nchunks, out_stride, out);
   return cudaGetLastError();
 }
 

@@ -251,7 +251,10 @@ StepPlan make_plan(const int D[4], int mu, int dcut, int prec) {
       p.ksuf = q;
     }
     p.Kp = prod;
-    const int64_t al = prec == HOTRG_FP16X3 ? 8 : 4;     // 16-byte TMA rows
+    // tensor-core operands: panel rows start on 128-byte boundaries, so the 64-byte rows the
+    // GEMM's copies fetch never straddle an L2 line (unaligned strides cost D = 10 and 13 a
+    // third of their throughput); CUDA-core operands: 16-byte rows
+    const int64_t al = tc_mode(prec) ? 128 / (int64_t)operand_size(prec) : 4;
     p.kps = (p.Kp + al - 1) / al * al;
     p.P = p.K / p.Kp;
   }
@@ -652,7 +655,7 @@ hotrg_status gemm_launch(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, c
     // operands carry the factor 2^14 each
     const float unscale = 1.0f / (kF16Scale * kF16Scale);
     CK(launch_gemm_tf32x3_v(A, Alo, B, Blo, p.Kp, p.kps, p.P, (float*)C, N, M, N, (float)alpha * unscale,
-                            (float)beta, (int*)(ctx->ws + ctx->L.status), st, 2),
+                            (float)beta, (int*)(ctx->ws + ctx->L.status), st, ctx->gemm_variant == 1 ? 3 : 2),
        "gemm f16x3");
   } else {
     if (p.P != 1) return HOTRG_EUNSUPPORTED;
@@ -718,11 +721,8 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
       }
     }
     LK(1, launch_gram<R>(gp, nj, p.Rmax, p.nchunks, st), "gram");
-    for (int i = 0; i < nj; ++i) {
-      const int R2 = gp.j[i].D1 * gp.j[i].D2;
-      LK(1, launch_gram_reduce(gp.j[i].partial, p.nchunks, (int64_t)R2 * R2, gA + (int64_t)i * p.Rmax * p.Rmax, st),
-         "gram reduce");
-    }
+    LK(1, launch_gram_reduce(gp, nj, p.nchunks, (int64_t)p.Rmax * p.Rmax, (int64_t)p.Rmax * p.Rmax, gA, st),
+       "gram reduce");
     double* G = (double*)(sb + sc.G);
     for (int i = 0; i < 3; ++i) {
       for (int side = 0; side < 2; ++side) {

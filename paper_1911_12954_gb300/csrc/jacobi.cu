@@ -46,6 +46,18 @@ __device__ __forceinline__ void rr_pair(int r, int i, int m, int& p, int& q) {
   }
 }
 
+// e-th entry (row-major) of the upper triangle, diagonal included, of an h x h grid.
+__device__ __forceinline__ void tri_index(int e, int h, int& P, int& Q) {
+  // rows start at s(P) = P h - P (P - 1) / 2; invert with a float square root, then fix up
+  const float b = 2.0f * h + 1.0f;
+  int r = (int)((b - sqrtf(b * b - 8.0f * (float)e)) * 0.5f);
+  r = r < 0 ? 0 : (r > h - 1 ? h - 1 : r);
+  while (r > 0 && r * h - r * (r - 1) / 2 > e) --r;
+  while (r + 1 < h && (r + 1) * h - (r + 1) * r / 2 <= e) ++r;
+  P = r;
+  Q = r + (e - (r * h - r * (r - 1) / 2));
+}
+
 __device__ double block_sum(double v, double* red) {
   for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
   __syncthreads();
@@ -77,7 +89,9 @@ __global__ void __launch_bounds__(kJT) jacobi_kernel(const __grid_constant__ Eig
 
   double fro = 0;
   for (int e = tid; e < n * n; e += kJT) {
-    const double g = jb.G[e];
+    // the upper triangle of G, mirrored (the merged Gram is symmetric up to summation order)
+    const int gi = e / n, gj = e % n;
+    const double g = jb.G[gi <= gj ? e : gj * n + gi];
     A[e] = g;
     V[e] = (e / n == e % n) ? 1.0 : 0.0;
     fro += g * g;
@@ -113,9 +127,13 @@ __global__ void __launch_bounds__(kJT) jacobi_kernel(const __grid_constant__ Eig
         qq[i] = q;
       }
       __syncthreads();
-      // A <- J^T A J, one 2x2 block (pair P rows, pair Q columns) per thread iteration
-      for (int e = tid; e < half * half; e += kJT) {
-        const int P = e / half, Q = e % half;
+      // A <- J^T A J, one 2x2 block (pair P rows, pair Q columns) per thread iteration, for
+      // P <= Q only: the block (Q, P) is written as the transpose, so A stays exactly
+      // symmetric and the FP64 work (the scarce pipe on this chip) is about halved
+      const int ntri = half * (half + 1) / 2;
+      for (int e = tid; e < ntri; e += kJT) {
+        int P, Q;
+        tri_index(e, half, P, Q);
         const double c1 = cs[P], s1 = sn[P], c2 = cs[Q], s2 = sn[Q];
         if (s1 == 0.0 && s2 == 0.0) continue;
         const int p1 = pp[P], q1 = qq[P], p2 = pp[Q], q2 = qq[Q];
@@ -138,6 +156,12 @@ __global__ void __launch_bounds__(kJT) jacobi_kernel(const __grid_constant__ Eig
         if (hq2) A[p1 * n + q2] = nb;
         if (hq1) A[q1 * n + p2] = nc;
         if (hq1 && hq2) A[q1 * n + q2] = nd;
+        if (P != Q) {
+          A[p2 * n + p1] = na;
+          if (hq2) A[q2 * n + p1] = nb;
+          if (hq1) A[p2 * n + q1] = nc;
+          if (hq1 && hq2) A[q2 * n + q1] = nd;
+        }
       }
       // V <- V J
       for (int e = tid; e < n * half; e += kJT) {

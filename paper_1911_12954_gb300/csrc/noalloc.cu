@@ -147,9 +147,7 @@ extern "C" hotrg_status hotrg_isometry_noalloc(const double* T_dev, const int di
     }
   }
   NA_CK(launch_gram<double>(gp, 4, R, (int)nch, st), "gram");
-  for (int i = 0; i < 4; ++i)
-    NA_CK(launch_gram_reduce(gp.j[i].partial, (int)nch, (int64_t)R * R, half + (int64_t)i * kNoAllocR * kNoAllocR, st),
-          "gram reduce");
+  NA_CK(launch_gram_reduce(gp, 4, (int)nch, (int64_t)R * R, (int64_t)kNoAllocR * kNoAllocR, half, st), "gram reduce");
   double* G = (double*)(base + L.G);
   for (int side = 0; side < 2; ++side)
     NA_CK(launch_gram_merge(half + (int64_t)(side * 2) * kNoAllocR * kNoAllocR,

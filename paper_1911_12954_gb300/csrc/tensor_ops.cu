@@ -1,6 +1,6 @@
 // tensor_ops.cu - memory-bound tensor kernels of the HOTRG step.
 //
-//  * ttm_fiber_kernel / ttm_kernel : contraction of one or two legs of a tensor with an isometry
+//  * ttm_short/long_kernel, ttm_kernel : contraction of one or two legs of a tensor with an isometry
 //                     (the half contractions T x U^a x U^b that build the operands of
 //                     the block-spin GEMM, and the closing contractions with U^c,
 //                     Fig. 1C), writing any output leg order, optionally split into
@@ -82,15 +82,16 @@ __global__ void __launch_bounds__(256) ttm_kernel(const TI* __restrict__ in, con
 }
 
 // ---------------------------------------------------------------------------- fiber form
-// The same contraction organised by input fibre: the J contracted entries of one fibre
-// are loaded once into registers and every output of the new index (up to two dims,
-// R <= 256 values, U staged in shared memory) is produced from them. Each input element
-// is read once and each output written once; consecutive threads take consecutive
-// fibres, so reads and writes along the innermost fibre dimension are coalesced. Used
-// whenever J <= 64, which covers every pass of a step with bond dimensions <= 8.
+// The same contraction organised by input fibre: out[f, r] = alpha sum_j U[j, r] in[f, j]
+// with f the multi-index of the untouched legs, j = (j1, j2) the contracted legs and
+// r = (r1, r2) the new ones. One thread per fibre; consecutive threads take consecutive
+// fibres, so reads and writes along the innermost fibre leg are coalesced, every input
+// element is read once and every output written once. U (and the output offsets of the
+// new index) sit in shared memory, read by all lanes of a warp at once (broadcast).
 struct FiberArgs {
   int nf;                       // fibre dims (outermost first)
-  int64_t fdims[kMaxRank], fin[kMaxRank], fout[kMaxRank];
+  int fdims[kMaxRank];
+  int64_t fin[kMaxRank], fout[kMaxRank];
   int64_t nfib;
   int R1, R2;                   // new-index dims
   int64_t ru1, ru2, ro1, ro2;   // their U-column and output strides
@@ -99,107 +100,173 @@ struct FiberArgs {
   double alpha;
 };
 
-template <typename R, int JMAX, int MODE>
-__global__ void __launch_bounds__(256) ttm_fiber_kernel(const R* __restrict__ in, const R* __restrict__ U,
-                                                        R* __restrict__ out, R* __restrict__ out_lo, FiberArgs a) {
-  extern __shared__ __align__(16) unsigned char fsm[];
-  const int J = a.J1 * a.J2, Rn = a.R1 * a.R2;
-  R* Us = (R*)fsm;                                       // [J][Rn]
-  int64_t* joff = (int64_t*)(fsm + (((size_t)J * Rn * sizeof(R) + 15) / 16) * 16);
-  for (int e = threadIdx.x; e < J * Rn; e += blockDim.x) {
-    const int j = e / Rn, r = e % Rn;
-    const int j1 = j / a.J2, j2 = j % a.J2, r1 = r / a.R2, r2 = r % a.R2;
-    Us[e] = U[j1 * a.ju1 + j2 * a.ju2 + r1 * a.ru1 + r2 * a.ru2];
-  }
-  for (int j = threadIdx.x; j < J; j += blockDim.x) joff[j] = (j / a.J2) * a.ji1 + (j % a.J2) * a.ji2;
-  __syncthreads();
-  using Acc = R;
-  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < a.nfib; f += (int64_t)gridDim.x * blockDim.x) {
-    int64_t q = f, io = 0, oo = 0;
-    for (int d = a.nf - 1; d >= 0; --d) {
-      const int64_t n = a.fdims[d];
-      const int64_t i = q % n;
-      q /= n;
-      io += i * a.fin[d];
-      oo += i * a.fout[d];
-    }
-    R x[JMAX];
+constexpr int kShortJ = 16;     // longest contraction of the short form
+constexpr int kShortRB = 32;    // accumulators per block of the new index (short form)
+constexpr int kLongRMax = 16;   // longest new index of the long form
+
+__device__ __forceinline__ void fiber_offsets(const FiberArgs& a, uint32_t f, int64_t& io, int64_t& oo) {
+  io = 0;
+  oo = 0;
 #pragma unroll
-    for (int j = 0; j < JMAX; ++j)
-      if (j < J) x[j] = in[io + joff[j]];
-    for (int r1 = 0; r1 < a.R1; ++r1) {
-      for (int r2 = 0; r2 < a.R2; ++r2) {
-        const int r = r1 * a.R2 + r2;
-        Acc acc = 0;
-#pragma unroll
-        for (int j = 0; j < JMAX; ++j)
-          if (j < J) acc = fma(Us[j * Rn + r], x[j], acc);
-        acc *= (Acc)a.alpha;
-        const int64_t o = oo + r1 * a.ro1 + r2 * a.ro2;
-        if (MODE == kTTMSplitTF32) {
-          const float v = (float)acc;
-          const float hi = tf32_round(v);
-          out[o] = (R)hi;
-          out_lo[o] = (R)tf32_round(v - hi);
-        } else if (MODE == kTTMSplitF16) {
-          // fp16 hi + lo of 2^14 x: the pair keeps 22 significant bits
-          const float v = (float)acc * kF16Scale;
-          const __half hi = __float2half_rn(v);
-          ((__half*)out)[o] = hi;
-          ((__half*)out_lo)[o] = __float2half_rn(v - __half2float(hi));
-        } else {
-          out[o] = acc;
-        }
-      }
+  for (int d = kMaxRank - 1; d >= 0; --d) {   // unrolled: the parameter arrays are indexed statically
+    if (d < a.nf) {
+      const uint32_t n = (uint32_t)a.fdims[d];
+      const uint32_t i = f % n;
+      f /= n;
+      io += (int64_t)i * a.fin[d];
+      oo += (int64_t)i * a.fout[d];
     }
   }
 }
 
-// Fibre form for long contractions (J > 64, as in the closing passes at D >= 9) with a
-// short new index (R <= 32): the outputs of one fibre stay in registers and the J inputs
-// stream through once, each read by one thread with consecutive threads on consecutive
-// fibres.
-template <typename R, int RMAX>
-__global__ void __launch_bounds__(256) ttm_fiber_long_kernel(const R* __restrict__ in, const R* __restrict__ U,
-                                                             R* __restrict__ out, FiberArgs a) {
+template <typename R, int MODE>
+__device__ __forceinline__ void fiber_store(R* out, R* out_lo, int64_t o, R acc) {
+  if (MODE == kTTMSplitTF32) {
+    const float v = (float)acc;
+    const float hi = tf32_round(v);
+    out[o] = (R)hi;
+    out_lo[o] = (R)tf32_round(v - hi);
+  } else if (MODE == kTTMSplitF16) {
+    // fp16 hi + lo of 2^14 x: the pair keeps 22 significant bits
+    const float v = (float)acc * kF16Scale;
+    const __half hi = __float2half_rn(v);
+    ((__half*)out)[o] = hi;
+    ((__half*)out_lo)[o] = __float2half_rn(v - __half2float(hi));
+  } else {
+    out[o] = acc;
+  }
+}
+
+// Short contractions (J <= 16: the half contractions with U^a and U^b). The J inputs of a
+// fibre stay in registers; the new index is produced in blocks of 32 accumulators, each U
+// row of a block read as 16-byte vectors, so an output costs about J FMAs plus its store.
+template <typename R, int MODE>
+__global__ void __launch_bounds__(256) ttm_short_kernel(const R* __restrict__ in, const R* __restrict__ U,
+                                                        R* __restrict__ out, R* __restrict__ out_lo, FiberArgs a) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int J = a.J1 * a.J2, Rn = a.R1 * a.R2;
-  R* Us = (R*)fsm;                                       // [J][Rn]
-  int64_t* joff = (int64_t*)(fsm + (((size_t)J * Rn * sizeof(R) + 15) / 16) * 16);
-  for (int e = threadIdx.x; e < J * Rn; e += blockDim.x) {
-    const int j = e / Rn, r = e % Rn;
-    const int j1 = j / a.J2, j2 = j % a.J2, r1 = r / a.R2, r2 = r % a.R2;
-    Us[e] = U[j1 * a.ju1 + j2 * a.ju2 + r1 * a.ru1 + r2 * a.ru2];
+  const int Rp = (Rn + kShortRB - 1) / kShortRB * kShortRB;
+  R* Us = (R*)fsm;                                       // [J][Rp], zero past Rn
+  int64_t* roff = (int64_t*)(fsm + (size_t)J * Rp * sizeof(R));   // [Rp] output offset of r
+  int64_t* joff = roff + Rp;                             // [J] input offset of j
+  for (int e = threadIdx.x; e < J * Rp; e += blockDim.x) {
+    const int j = e / Rp, r = e % Rp;
+    R v = 0;
+    if (r < Rn) {
+      const int j1 = j / a.J2, j2 = j % a.J2, r1 = r / a.R2, r2 = r % a.R2;
+      v = U[j1 * a.ju1 + j2 * a.ju2 + r1 * a.ru1 + r2 * a.ru2];
+    }
+    Us[e] = v;
   }
+  for (int r = threadIdx.x; r < Rp; r += blockDim.x) roff[r] = r < Rn ? (r / a.R2) * a.ro1 + (r % a.R2) * a.ro2 : 0;
   for (int j = threadIdx.x; j < J; j += blockDim.x) joff[j] = (j / a.J2) * a.ji1 + (j % a.J2) * a.ji2;
   __syncthreads();
+  const R alpha = (R)a.alpha;
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < a.nfib; f += (int64_t)gridDim.x * blockDim.x) {
-    int64_t q = f, io = 0, oo = 0;
-    for (int d = a.nf - 1; d >= 0; --d) {
-      const int64_t n = a.fdims[d];
-      const int64_t i = q % n;
-      q /= n;
-      io += i * a.fin[d];
-      oo += i * a.fout[d];
-    }
-    R acc[RMAX];
+    int64_t io, oo;
+    fiber_offsets(a, (uint32_t)f, io, oo);
+    R x[kShortJ];
 #pragma unroll
-    for (int r = 0; r < RMAX; ++r) acc[r] = 0;
-    for (int j = 0; j < J; ++j) {
-      const R x = in[io + joff[j]];
-      const R* u = Us + j * Rn;
+    for (int j = 0; j < kShortJ; ++j) x[j] = j < J ? in[io + joff[j]] : (R)0;
+    for (int rb = 0; rb < Rn; rb += kShortRB) {
+      R acc[kShortRB];
 #pragma unroll
-      for (int r = 0; r < RMAX; ++r)
-        if (r < Rn) acc[r] = fma(u[r], x, acc[r]);
-    }
+      for (int i = 0; i < kShortRB; ++i) acc[i] = 0;
 #pragma unroll
-    for (int r = 0; r < RMAX; ++r) {
-      if (r >= Rn) break;
-      const int r1 = r / a.R2, r2 = r % a.R2;
-      out[oo + r1 * a.ro1 + r2 * a.ro2] = acc[r] * (R)a.alpha;
+      for (int j = 0; j < kShortJ; ++j) {
+        if (j < J) {
+          const R* u = Us + j * Rp + rb;
+          if constexpr (sizeof(R) == 4) {
+#pragma unroll
+            for (int i = 0; i < kShortRB; i += 4) {
+              const float4 q = *(const float4*)(u + i);
+              acc[i] = fma((R)q.x, x[j], acc[i]);
+              acc[i + 1] = fma((R)q.y, x[j], acc[i + 1]);
+              acc[i + 2] = fma((R)q.z, x[j], acc[i + 2]);
+              acc[i + 3] = fma((R)q.w, x[j], acc[i + 3]);
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < kShortRB; i += 2) {
+              const double2 q = *(const double2*)(u + i);
+              acc[i] = fma((R)q.x, x[j], acc[i]);
+              acc[i + 1] = fma((R)q.y, x[j], acc[i + 1]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < kShortRB; ++i)
+        if (rb + i < Rn) fiber_store<R, MODE>(out, out_lo, oo + roff[rb + i], acc[i] * alpha);
     }
   }
 }
+
+// Long contractions (J > 16 with a short new index, Rn <= 16: the closing passes with U^c).
+// The outputs of a fibre stay in RB registers; its J inputs stream through in (j1, j2)
+// order, eight loads issued before their FMAs so that several are in flight per thread.
+template <typename R, int RB>
+__global__ void __launch_bounds__(256) ttm_long_kernel(const R* __restrict__ in, const R* __restrict__ U,
+                                                       R* __restrict__ out, FiberArgs a) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  const int J = a.J1 * a.J2, Rn = a.R1 * a.R2;
+  R* Us = (R*)fsm;                                       // [J][RB], zero past Rn
+  int64_t* roff = (int64_t*)(fsm + (size_t)J * RB * sizeof(R));   // [RB]
+  for (int e = threadIdx.x; e < J * RB; e += blockDim.x) {
+    const int j = e / RB, r = e % RB;
+    R v = 0;
+    if (r < Rn) {
+      const int j1 = j / a.J2, j2 = j % a.J2, r1 = r / a.R2, r2 = r % a.R2;
+      v = U[j1 * a.ju1 + j2 * a.ju2 + r1 * a.ru1 + r2 * a.ru2];
+    }
+    Us[e] = v;
+  }
+  for (int r = threadIdx.x; r < RB; r += blockDim.x) roff[r] = r < Rn ? (r / a.R2) * a.ro1 + (r % a.R2) * a.ro2 : 0;
+  __syncthreads();
+  const R alpha = (R)a.alpha;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < a.nfib; f += (int64_t)gridDim.x * blockDim.x) {
+    int64_t io, oo;
+    fiber_offsets(a, (uint32_t)f, io, oo);
+    R acc[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) acc[r] = 0;
+    for (int j1 = 0; j1 < a.J1; ++j1) {
+      const R* src = in + io + j1 * a.ji1;
+      const R* u = Us + (size_t)j1 * a.J2 * RB;
+      int j2 = 0;
+      for (; j2 + 8 <= a.J2; j2 += 8) {
+        R xv[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) xv[q] = src[(int64_t)(j2 + q) * a.ji2];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const R* uq = u + (j2 + q) * RB;
+#pragma unroll
+          for (int r = 0; r < RB; ++r) acc[r] = fma(uq[r], xv[q], acc[r]);
+        }
+      }
+      for (; j2 < a.J2; ++j2) {
+        const R xv = src[(int64_t)j2 * a.ji2];
+        const R* uq = u + j2 * RB;
+#pragma unroll
+        for (int r = 0; r < RB; ++r) acc[r] = fma(uq[r], xv, acc[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+      if (r < Rn) out[oo + roff[r]] = acc[r] * alpha;
+  }
+}
+
+inline size_t short_smem(int J, int Rn, size_t rsize) {
+  const size_t Rp = (size_t)(Rn + kShortRB - 1) / kShortRB * kShortRB;
+  return (size_t)J * Rp * rsize + (Rp + (size_t)J) * sizeof(int64_t);
+}
+inline int long_rb(int Rn) { return Rn <= 8 ? 8 : kLongRMax; }
+inline size_t long_smem(int J, int Rn, size_t rsize) {
+  return (size_t)J * long_rb(Rn) * rsize + (size_t)long_rb(Rn) * sizeof(int64_t);
+}
+constexpr size_t kFiberSmemMax = 48 * 1024;
 
 // Converts a TTMArgs into the fibre form when it fits; false otherwise.
 bool to_fiber(const TTMArgs& a, size_t rsize, FiberArgs& f) {
@@ -222,7 +289,7 @@ bool to_fiber(const TTMArgs& a, size_t rsize, FiberArgs& f) {
       }
       ++nr;
     } else {
-      f.fdims[f.nf] = a.dims[i];
+      f.fdims[f.nf] = (int)a.dims[i];
       f.fin[f.nf] = a.in_st[i];
       f.fout[f.nf] = a.out_st[i];
       f.nfib *= a.dims[i];
@@ -237,33 +304,28 @@ bool to_fiber(const TTMArgs& a, size_t rsize, FiberArgs& f) {
   f.ju2 = a.u_sj2;
   f.alpha = a.alpha;
   const int J = a.J1 * a.J2, Rn = f.R1 * f.R2;
-  if (f.nf == 0 || (size_t)J * Rn * rsize > 32768) return false;
-  if (J <= 64) return Rn <= 256;
-  return Rn <= 32;                 // long form
+  if (f.nf == 0 || f.nfib > 0x7fffffffLL) return false;   // fibre index decoded in 32 bits
+  if (J <= kShortJ) return Rn <= 256 && short_smem(J, Rn, rsize) <= kFiberSmemMax;
+  return Rn <= kLongRMax && long_smem(J, Rn, rsize) <= kFiberSmemMax;
 }
 
 template <typename R>
 cudaError_t launch_fiber(const R* in, const R* U, R* out, R* out_lo, const FiberArgs& f, int mode, cudaStream_t st) {
-  const int J = f.J1 * f.J2;
-  const size_t smem = ((size_t)J * f.R1 * f.R2 * sizeof(R) + 15) / 16 * 16 + (size_t)J * sizeof(int64_t);
+  const int J = f.J1 * f.J2, Rn = f.R1 * f.R2;
   int64_t blocks = (f.nfib + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   const unsigned g = (unsigned)blocks;
-  if (J > 64) {                    // long form (plain store only)
+  if (J > kShortJ) {               // long form (plain store only)
     if (mode != kTTMStore) return cudaErrorInvalidValue;
-    if (f.R1 * f.R2 <= 16) ttm_fiber_long_kernel<R, 16><<<g, 256, smem, st>>>(in, U, out, f);
-    else ttm_fiber_long_kernel<R, 32><<<g, 256, smem, st>>>(in, U, out, f);
+    const size_t smem = long_smem(J, Rn, sizeof(R));
+    if (long_rb(Rn) == 8) ttm_long_kernel<R, 8><<<g, 256, smem, st>>>(in, U, out, f);
+    else ttm_long_kernel<R, kLongRMax><<<g, 256, smem, st>>>(in, U, out, f);
     return cudaGetLastError();
   }
-  if (J <= 16) {
-    if (mode == kTTMSplitTF32) ttm_fiber_kernel<R, 16, kTTMSplitTF32><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
-    else if (mode == kTTMSplitF16) ttm_fiber_kernel<R, 16, kTTMSplitF16><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
-    else ttm_fiber_kernel<R, 16, kTTMStore><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
-  } else {
-    if (mode == kTTMSplitTF32) ttm_fiber_kernel<R, 64, kTTMSplitTF32><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
-    else if (mode == kTTMSplitF16) ttm_fiber_kernel<R, 64, kTTMSplitF16><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
-    else ttm_fiber_kernel<R, 64, kTTMStore><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
-  }
+  const size_t smem = short_smem(J, Rn, sizeof(R));
+  if (mode == kTTMSplitTF32) ttm_short_kernel<R, kTTMSplitTF32><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
+  else if (mode == kTTMSplitF16) ttm_short_kernel<R, kTTMSplitF16><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
+  else ttm_short_kernel<R, kTTMStore><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
   return cudaGetLastError();
 }
 
@@ -275,7 +337,7 @@ cudaError_t launch_ttm(const TI* in, const TU* U, TO* out, TO* out_lo, const TTM
   if constexpr (std::is_same<TI, TU>::value && std::is_same<TI, TO>::value) {
     FiberArgs f;
     if (U != nullptr && mode != kTTMAccumulate && to_fiber(a, sizeof(TI), f) &&
-        (f.J1 * f.J2 <= 64 || mode == kTTMStore))
+        (f.J1 * f.J2 <= kShortJ || mode == kTTMStore))
       return launch_fiber<TI>(in, U, out, out_lo, f, mode, st);
   }
   const int64_t blocks = a.outer < 152 * 64 ? a.outer : 152 * 64;

@@ -387,14 +387,16 @@ def test_nonfinite_input_is_rejected_on_the_host():
         g.set_tensor(T)
 
 
-def test_gemm_pipeline_variants_agree():
-    """Both tensor-core pipelines (4 x 16-wide and 2 x 32-wide k-blocks) give the same step."""
+@pytest.mark.parametrize("precision", ["tf32x3", "fp16x3"])
+def test_gemm_pipeline_variants_agree(precision):
+    """Both tensor-core pipelines of a mode give the same step: for tf32x3 4 x 16-wide
+    and 2 x 32-wide k-blocks, for fp16x3 partial sums promoted every 128 k and every 64 k."""
     from paper_1911_12954_gb300 import OPT_GEMM_VARIANT
     dims, mu, dcut = (3, 3, 2, 3), 2, 6
     T = random_tensor(12, dims)
     out = []
     for v in (0, 1):
-        g = _gpu(batch=1, dcut_max=9, precision="tf32x3", schedule=[(mu, dcut)], dims0=dims)
+        g = _gpu(batch=1, dcut_max=9, precision=precision, schedule=[(mu, dcut)], dims0=dims)
         g.set_option(OPT_GEMM_VARIANT, v)
         g.set_tensor(T)
         g.step(mu, dcut)
