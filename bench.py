@@ -61,6 +61,13 @@ def parse_args():
     return p.parse_args()
 
 
+# DRAM bytes (read + write) per launch of the block-spin GEMM, taken from one ncu capture of
+# the same workload with the kernel as built now (profiles/gemm_fp16x3_d6_full.md:
+# dram__bytes_read.sum + dram__bytes_write.sum of the step-4 launch), keyed by (precision,
+# D_cut, temperatures, impure). Workloads without a capture report null.
+GEMM_TRAFFIC = {("fp16x3", 8, 1, False): 270.60e9 + 4.38e9}
+
+
 # --------------------------------------------------------------------------- helpers
 def tensor_peak(precision: str, sustained: bool = True):
     """Dense tensor peak of the GEMM's operand type. fp16 runs at the BF16 rate (the
@@ -183,11 +190,11 @@ class RankSync:
 
 
 # --------------------------------------------------------------------------- CPU oracle sample
-def oracle_sample(dcut: int, seed: int = 8):
+def oracle_sample(dcut: int, seed: int = 8, nx: int = 1):
     """One steady-state step of the FP64 oracle on a seeded tensor of the steady-state
     shape: the HOSVD of all three transverse directions (both sides) and the block-spin
-    contraction restricted to the new x legs X = X' = 0 (isometry U^x cut to its first
-    column), i.e. 1/D_cut^2 of the D^15 product. Returns (flops, seconds)."""
+    contraction restricted to the new x legs X, X' < nx (isometry U^x cut to its first nx
+    columns), i.e. nx^2/D_cut^2 of the D^15 product. Returns (flops, seconds)."""
     import numpy as np
 
     from oracle import hotrg as H
@@ -200,17 +207,17 @@ def oracle_sample(dcut: int, seed: int = 8):
     t0 = time.perf_counter()
     isos = {n: H.isometry(T, T, mu, n, dcut) for n in (1, 2, 3)}
     U = {n: isos[n].U for n in (1, 2, 3)}
-    U[1] = U[1][:, :, :1].copy()
+    U[1] = U[1][:, :, :nx].copy()
     H.coarse_grain(T, T, U, mu)
     dt = time.perf_counter() - t0
     # flops of what ran (2 per multiply-add): 12 half-Grams + the restricted contraction
     E = float(D) ** 8
     R = D * D
     gram = 3 * 4 * 2.0 * R * E
-    rows = 1 * D * D * D * D          # X (1) * Y (chi) * c1 c1' (D^2) * mu1 (D)
+    rows = nx * D * D * D * D         # X (nx) * Y (chi) * c1 c1' (D^2) * mu1 (D)
     K = float(D) ** 5
     main = 2.0 * rows * rows * K
-    builds = 2 * (2.0 * D * 1 * E) + 2 * (2.0 * D * rows * K)     # T x U^x (1 col), x U^y, both sides
+    builds = 2 * (2.0 * D * nx * E) + 2 * (2.0 * D * rows * K)    # T x U^x (nx cols), x U^y, both sides
     close = 2.0 * D * rows * rows + 2.0 * D * D * rows * rows / (D * D) * D
     return gram + main + builds + close, dt
 
@@ -396,16 +403,17 @@ def main():
     # ---------------------------------------------------------------- CPU oracle baseline
     cpu = None
     if args.cpu and rank == 0 and world == 1:
-        f, s = oracle_sample(D)
+        nx = 2 if D >= 8 else 1            # about 10-20 s of host work at D_cut = 8
+        f, s = oracle_sample(D, nx=nx)
         cpu = {"value": f / s / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"one steady-state D_cut={D} step of the FP64 NumPy oracle on a seeded N(0,1) tensor of "
-                         f"shape ({D},)*8: full HOSVD + the block-spin contraction restricted to X = X' = 0 "
-                         f"(1/{D * D} of the D^15 product); {s:.1f} s"}
+                         f"shape ({D},)*8: full HOSVD + the block-spin contraction restricted to X, X' < {nx} "
+                         f"({nx * nx}/{D * D} of the D^15 product); {s:.1f} s"}
 
     peak, peak_src = tensor_peak(args.precision, True)
     peak_burst, _ = tensor_peak(args.precision, False)
     achieved = prof["gemm_flops"] / (prof["gemm_ms"] * 1e-3) / 1e12 if prof["gemm_ms"] > 0 else None
-    traffic = None
+    traffic = GEMM_TRAFFIC.get((args.precision, D, args.batch, bool(impure)))
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -417,9 +425,11 @@ def main():
                                f"{args.warmup + 1}..{nsteps} (steady state)",
                    "dcut": D, "temperatures_per_gpu": args.batch, "impure": bool(impure), "lattice": "1024^4",
                    "precision": f"{args.precision} (fp32 storage)", "cuda_graphs": bool(args.graphs),
-                   "l2": "operands larger than L2 (GEMM A and B: 2 x 4.3 GB per step, hi + lo)"},
+                   "l2": f"operands larger than L2 (GEMM A and B: 2 x "
+                         f"{(4 if args.precision == 'fp16x3' else 8) * D ** 10 / 1e9:.1f} GB per step, hi + lo)"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "algorithmic_bytes": (2 * (4 if args.precision == "fp16x3" else 8) + 4) * float(D) ** 10,
                      "kernel": f"gemm_tf32x3_kernel<{'CfgF16' if args.precision == 'fp16x3' else 'CfgTF32'}> "
                                "(block-spin contraction, 2 M N K algorithmic flops per launch)",
                      "peak_source": peak_src, "launches": prof["gemm_launches"],
