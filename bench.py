@@ -56,6 +56,9 @@ def parse_args():
     p.add_argument("--batch", type=int, default=1, help="temperatures per GPU (evenly spaced in [6.60, 6.72])")
     p.add_argument("--impure", type=int, default=0, help="propagate the sigma and sigma-sigma impure tensors")
     p.add_argument("--graphs", type=int, default=0, help="replay each distinct step as a captured CUDA graph")
+    p.add_argument("--tc", type=int, default=0,
+                   help="instead of the step line: bracket T_c(D_cut) from the X indicator after 40 steps "
+                        "(batched temperatures, --tc rounds) and print that as its own line")
     p.add_argument("--precision", choices=["tf32x3", "fp16x3"], default="fp16x3",
                    help="tensor-core split of the block-spin contraction (default: fp16 hi/lo on kind::f16)")
     return p.parse_args()
@@ -249,6 +252,30 @@ def run_reference(args, rank, world):
 
 
 # --------------------------------------------------------------------------- GPU arm
+def run_tc(args, local):
+    """T_c(D_cut) bracket from the X indicator (Sec. 3.1): rounds of 8 temperatures each, one
+    batched 40-step run (1024^4) per round, starting from [6.0, 7.5]; reports the interval,
+    every round's (T, X) and the wall time, with the clocks seen."""
+    import torch
+
+    from paper_1911_12954_gb300.tc import bracket_tc
+
+    torch.cuda.set_device(local)
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        lo, hi, hist = bracket_tc(args.dcut, 6.0, 7.5, nsteps=40, batch=8, rounds=args.tc, precision=args.precision)
+        secs = time.perf_counter() - t0
+    line = {"metric": f"T_c(D_cut={args.dcut}) bracket from the X indicator, 1024^4 lattice", "value": secs,
+            "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": f"4D Ising HOTRG, h=0, D_cut={args.dcut}, 40 steps (x,y,z,t cycled), "
+                                   f"{args.tc} rounds x 8 temperatures from [6.0, 7.5]"},
+            "tc_bracket": [lo, hi], "tc_mid": 0.5 * (lo + hi),
+            "rounds": [{"T": [float(t) for t in T], "X": [float(x) for x in X]} for T, X in hist],
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", 0))
@@ -256,6 +283,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.tc:
+        return run_tc(args, local) if rank == 0 else 0
 
     import numpy as np
     import torch

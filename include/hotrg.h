@@ -141,6 +141,15 @@ hotrg_status hotrg_impure_magnetization(hotrg_ctx* ctx, double* m);
  * NULL. */
 hotrg_status hotrg_impure_energy(hotrg_ctx* ctx, double* e, double* sigma_sigma);
 
+/* Degeneracy indicator X of the current tensor along direction nu (0..3 = x, y, z, t), per
+ * batch element (host array of length batch): M[i][j] = T with leg nu = i, leg nu' = j and
+ * every other direction traced, X = (Tr M)^2 / Tr(M M). Sec. 3.1 of arXiv:1911.12954 locates
+ * T_c from X (citing Gu and Wen for the definition, restated here): after many steps X is 1
+ * in the symmetric phase and 2 when Z2 is broken. FP64 sums on the device. Valid after any
+ * number of steps (k = 0 included). Synchronises. Errors: EINVAL (nu, NULL), ESTATE (not
+ * initialised), ENONFINITE (Tr(M M) = 0 or a non-finite tensor). */
+hotrg_status hotrg_x_indicator(hotrg_ctx* ctx, int nu, double* X);
+
 /* Record of step `step` (1-based, <= steps done) of batch element b. Synchronises. */
 hotrg_status hotrg_step_info(hotrg_ctx* ctx, int b, int step, hotrg_step_record* rec);
 

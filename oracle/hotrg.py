@@ -80,6 +80,29 @@ def trace(T: np.ndarray) -> float:
     return float(np.einsum(sub + "->", T))
 
 
+def transfer_matrix(T: np.ndarray, nu: int) -> np.ndarray:
+    """M[i, j] = T with leg nu = i, leg nu' = j and every other direction traced (leg
+    joined to its own primed partner): the transfer matrix along nu of the one-site
+    periodic network, so that Tr M = Tr T and Tr(M M) is the two-site network along nu."""
+    d = T.ndim // 2
+    letters = "abcdefghijklmnop"
+    sub = []
+    for n in range(d):
+        sub += ["y", "z"] if n == nu else [letters[n], letters[n]]
+    return np.einsum("".join(sub) + "->yz", T)
+
+
+def x_indicator(T: np.ndarray, nu: int = 0) -> float:
+    """Degeneracy indicator X of the coarse tensor, used in Sec. 3.1 to locate T_c. The
+    paper cites its definition (Gu and Wen) and describes it as counting the degeneracy of
+    the largest components of the local tensor; restated here: X = (Tr M)^2 / Tr(M M) with M
+    the transfer matrix along nu (``transfer_matrix``). For eigenvalues m_i of M,
+    X = (sum m_i)^2 / sum m_i^2: 1 when one dominates (symmetric phase), 2 for two equal
+    ones (the two Z2-broken vacua)."""
+    M = transfer_matrix(T, nu)
+    return float(np.trace(M) ** 2 / np.trace(M @ M))
+
+
 def leg_dims(T: np.ndarray):
     """Bond dimension of each direction (leg 2nu and 2nu+1 share it)."""
     d = T.ndim // 2

@@ -136,6 +136,8 @@ template <typename R>
 cudaError_t launch_scale(R* x, int64_t n, const double* c, cudaStream_t st);
 template <typename R>
 cudaError_t launch_trace(const R* T, int64_t slot, const int* dims, int batch, double* out, cudaStream_t st);
+template <typename R>
+cudaError_t launch_xind(const R* T, int64_t slot, const int* dims, int batch, int nu, double* out, cudaStream_t st);
 constexpr int kNormPartials = 2 * 152;
 
 template <typename R>

@@ -345,7 +345,7 @@ Layout persistent_layout(int batch, int64_t cap, int impure, size_t rs) {
   L.step = take(sizeof(int));
   L.lnz = take(batch * 8);
   L.cval = take(batch * 8);
-  L.trace = take(3 * batch * 8);
+  L.trace = take(4 * batch * 8);   // Tr T, Tr S, Tr M, X indicator
   L.rec = take((size_t)batch * kMaxSteps * sizeof(DevRecord));
   L.beta = take(batch * 8);
   L.hfield = take(batch * 8);
@@ -1194,6 +1194,28 @@ hotrg_status hotrg_lnZ(hotrg_ctx* ctx, double* out) {
     }
   }
   return res;
+}
+
+hotrg_status hotrg_x_indicator(hotrg_ctx* ctx, int nu, double* X) {
+  hotrg_status r = check_ready(ctx);
+  if (r != HOTRG_OK) return r;
+  if (!X || nu < 0 || nu > 3) return HOTRG_EINVAL;
+  if (!ctx->initialised) return HOTRG_ESTATE;
+  double* dx = (double*)(ctx->ws + ctx->L.trace) + 3 * ctx->batch;
+  if (ctx->prec == HOTRG_FP64)
+    LK(1, launch_xind<double>(tensor_ptr<double>(ctx, 0, ctx->cur, 0), ctx->L.cap, ctx->dims, ctx->batch, nu, dx,
+                           ctx->stream),
+       "x indicator");
+  else
+    LK(1, launch_xind<float>(tensor_ptr<float>(ctx, 0, ctx->cur, 0), ctx->L.cap, ctx->dims, ctx->batch, nu, dx,
+                          ctx->stream),
+       "x indicator");
+  hotrg_status s = sync_and_status(ctx);
+  if (s != HOTRG_OK) return s;
+  CK(cudaMemcpy(X, dx, ctx->batch * 8, cudaMemcpyDeviceToHost), "x indicator read");
+  for (int b = 0; b < ctx->batch; ++b)
+    if (!isfinite(X[b])) return HOTRG_ENONFINITE;
+  return HOTRG_OK;
 }
 
 hotrg_status hotrg_impure_magnetization(hotrg_ctx* ctx, double* m) {

@@ -8,6 +8,7 @@
 //  * init_kernel    : the 4D Ising site tensors T and S (Fig. 1A) and ln c_0.
 //  * sumsq/normalise: c = ||T'||_F in FP64, ln c / 2^k accumulated (ln Z / V), T' /= c.
 //  * trace_kernel   : Tr T (each leg joined to its primed partner), FP64.
+//  * xind_kernel    : the degeneracy indicator X = (Tr M)^2 / Tr(M M) of the coarse tensor.
 #include <cuda_fp16.h>
 #include <math.h>
 
@@ -542,5 +543,64 @@ cudaError_t launch_trace(const R* T, int64_t slot, const int* dims, int batch, d
 }
 template cudaError_t launch_trace<double>(const double*, int64_t, const int*, int, double*, cudaStream_t);
 template cudaError_t launch_trace<float>(const float*, int64_t, const int*, int, double*, cudaStream_t);
+
+// ---------------------------------------------------------------------------- X indicator
+// Degeneracy indicator of the coarse tensor (Sec. 3.1 locates T_c with it): M[i][j] = T with
+// leg nu = i, leg nu' = j and each other direction traced, X = (Tr M)^2 / Tr(M M). One block
+// per batch element; one warp per entry of M (lanes stride over the traced directions),
+// FP64 sums.
+template <typename R>
+__global__ void __launch_bounds__(256) xind_kernel(const R* __restrict__ T, int64_t slot, int Dx, int Dy, int Dz,
+                                                   int Dt, int nu, double* out) {
+  const R* t = T + blockIdx.x * slot;
+  const int D[4] = {Dx, Dy, Dz, Dt};
+  int64_t st[8], s = 1;
+  for (int leg = 7; leg >= 0; --leg) {
+    st[leg] = s;
+    s *= D[leg / 2];
+  }
+  int od[3];
+  int64_t ost[3];   // diagonal stride (leg + its primed partner) of the traced directions
+  int q = 0;
+  for (int n = 0; n < 4; ++n)
+    if (n != nu) {
+      od[q] = D[n];
+      ost[q] = st[2 * n] + st[2 * n + 1];
+      ++q;
+    }
+  const int Dn = D[nu];
+  const int64_t nrest = (int64_t)od[0] * od[1] * od[2];
+  __shared__ double M[kMaxLeg * kMaxLeg];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int e = w; e < Dn * Dn; e += nw) {
+    const int i = e / Dn, j = e % Dn;
+    const int64_t base = i * st[2 * nu] + j * st[2 * nu + 1];
+    double acc = 0;
+    for (int64_t r = lane; r < nrest; r += 32) {
+      const int64_t r2 = r % od[2], r1 = (r / od[2]) % od[1], r0 = r / ((int64_t)od[2] * od[1]);
+      acc += (double)t[base + r0 * ost[0] + r1 * ost[1] + r2 * ost[2]];
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (lane == 0) M[e] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0, tr2 = 0;
+    for (int i = 0; i < Dn; ++i) {
+      tr += M[i * Dn + i];
+      for (int j = 0; j < Dn; ++j) tr2 += M[i * Dn + j] * M[j * Dn + i];
+    }
+    out[blockIdx.x] = tr * tr / tr2;
+  }
+}
+
+template <typename R>
+cudaError_t launch_xind(const R* T, int64_t slot, const int* dims, int batch, int nu, double* out, cudaStream_t st) {
+  if (nu < 0 || nu > 3 || dims[nu] > kMaxLeg) return cudaErrorInvalidValue;
+  xind_kernel<R><<<batch, 256, 0, st>>>(T, slot, dims[0], dims[1], dims[2], dims[3], nu, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_xind<double>(const double*, int64_t, const int*, int, int, double*, cudaStream_t);
+template cudaError_t launch_xind<float>(const float*, int64_t, const int*, int, int, double*, cudaStream_t);
 
 }  // namespace hotrg

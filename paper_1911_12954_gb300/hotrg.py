@@ -47,8 +47,8 @@ class Profile(ctypes.Structure):
 _LIB = None
 SYMBOLS = ["hotrg_create", "hotrg_destroy", "hotrg_workspace_size", "hotrg_set_workspace", "hotrg_set_stream",
            "hotrg_init_tensor", "hotrg_set_tensor", "hotrg_step", "hotrg_lnZ", "hotrg_impure_magnetization",
-           "hotrg_impure_energy", "hotrg_step_info", "hotrg_state", "hotrg_copy_tensor", "hotrg_copy_isometry",
-           "hotrg_step_flops", "hotrg_set_option", "hotrg_selftest_wait", "hotrg_profile_enable",
+           "hotrg_impure_energy", "hotrg_x_indicator", "hotrg_step_info", "hotrg_state", "hotrg_copy_tensor",
+           "hotrg_copy_isometry", "hotrg_step_flops", "hotrg_set_option", "hotrg_selftest_wait", "hotrg_profile_enable",
            "hotrg_profile_read", "hotrg_isometry_noalloc",
            "hotrg_status_string", "hotrg_last_error"]
 
@@ -78,6 +78,7 @@ def _lib():
         "hotrg_lnZ": (c_int, [c_void_p, P(c_double)]),
         "hotrg_impure_magnetization": (c_int, [c_void_p, P(c_double)]),
         "hotrg_impure_energy": (c_int, [c_void_p, P(c_double), P(c_double)]),
+        "hotrg_x_indicator": (c_int, [c_void_p, c_int, P(c_double)]),
         "hotrg_step_info": (c_int, [c_void_p, c_int, c_int, P(StepRecord)]),
         "hotrg_state": (c_int, [c_void_p, P(c_int), P(c_int)]),
         "hotrg_copy_tensor": (c_int, [c_void_p, c_int, c_int, P(c_double), c_size_t]),
@@ -210,6 +211,12 @@ class HOTRG:
         ss = np.zeros(self.batch)
         _check(self.lib.hotrg_impure_energy(self.ctx, _dptr(e), _dptr(ss)), "energy")
         return e, ss
+
+    def x_indicator(self, nu: int = 0) -> np.ndarray:
+        """Degeneracy indicator X = (Tr M)^2 / Tr(M M) along nu per batch element."""
+        out = np.zeros(self.batch)
+        _check(self.lib.hotrg_x_indicator(self.ctx, nu, _dptr(out)), "x_indicator")
+        return out
 
     def state(self):
         k = ctypes.c_int()

@@ -75,3 +75,4 @@ def test_flops_formula_steady_state(lib):
     size = ctypes.c_size_t()
     assert lib.hotrg_workspace_size(ctx, 4, HB._iptr(dirs), HB._iptr(dc), None, ctypes.byref(size)) == 0
     lib.hotrg_destroy(ctx)
+

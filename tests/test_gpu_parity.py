@@ -404,6 +404,55 @@ def test_gemm_pipeline_variants_agree(precision):
     assert np.allclose(out[0], out[1], atol=1e-6 * np.abs(out[0]).max())
 
 
+def test_x_indicator_matches_oracle_fp64():
+    """X along every direction after 0, 1 and 16 steps (D_cut = 4, 16^4 lattice) at
+    temperatures in both phases and near T_c, FP64 mode against the oracle's X."""
+    temps = [5.0, 6.65, 9.0]
+    sched = [(i % 4, 4) for i in range(16)]
+    g = _gpu(batch=len(temps), dcut_max=4, precision="fp64", schedule=sched)
+    g.init_tensor([1 / t for t in temps], 0.0)
+    ref = [H.HOTRG.start(4, 1 / t, 0.0) for t in temps]
+    for k, (mu, dc) in enumerate(sched):
+        if k in (0, 1, 16):
+            for nu in range(4):
+                got = g.x_indicator(nu)
+                for b, st in enumerate(ref):
+                    assert got[b] == pytest.approx(H.x_indicator(st.T, nu), rel=1e-9), (k, nu, b)
+        g.step(mu, dc)
+        for st in ref:
+            st.step(mu, dc)
+    for nu in range(4):
+        got = g.x_indicator(nu)
+        for b, st in enumerate(ref):
+            assert got[b] == pytest.approx(H.x_indicator(st.T, nu), rel=1e-9), ("end", nu, b)
+
+
+def test_x_indicator_mixed_precision_phases():
+    """FP16x3 at D_cut = 6 after 16 steps: X within 1e-4 of the FP64 GPU value deep in each
+    phase (T = 5: ~2, T = 9: ~1)."""
+    temps = [5.0, 9.0]
+    sched = [(i % 4, 6) for i in range(16)]
+    out = {}
+    for prec in ("fp64", "fp16x3"):
+        g = _gpu(batch=2, dcut_max=6, precision=prec, schedule=sched)
+        g.init_tensor([1 / t for t in temps], 0.0)
+        for mu, dc in sched:
+            g.step(mu, dc)
+        out[prec] = g.x_indicator(0)
+    assert abs(out["fp64"][0] - 2.0) < 0.01 and abs(out["fp64"][1] - 1.0) < 0.05
+    assert np.allclose(out["fp16x3"], out["fp64"], atol=1e-4)
+
+
+def test_tc_bracket_agrees_with_oracle():
+    """bracket_tc (batched GPU runs, FP64 mode, D_cut = 4, 16 steps) returns an interval whose
+    ends the oracle puts on the two sides of X = 1.5."""
+    from paper_1911_12954_gb300.tc import bracket_tc
+    lo, hi, hist = bracket_tc(4, 6.0, 7.5, nsteps=16, batch=4, rounds=2, precision="fp64")
+    assert 6.0 <= lo < hi <= 7.5 and hi - lo == pytest.approx(1.5 / 9, rel=1e-12)
+    assert H.x_indicator(H.run(4, 1 / lo, 0.0, 4, 16).T) > 1.5
+    assert H.x_indicator(H.run(4, 1 / hi, 0.0, 4, 16).T) <= 1.5
+
+
 def test_cuda_graph_steps_match_eager_steps():
     """Captured-and-replayed steps (one graph launch per step, every batch element and
     impure tensor inside) give bit-identical results to eager launches: 16 steps, so the

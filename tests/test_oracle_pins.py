@@ -322,3 +322,54 @@ def test_lnz_accumulator_weights():
     manual = sum(r.ln_c / 2 ** (i + 1) for i, r in enumerate(st.history))
     c0 = np.linalg.norm(H.ising_tensors(4, BETA_C4D, 0.0)[0])
     assert st.lnz_acc + math.log(7.0) / 2 ** st.k == pytest.approx(math.log(c0) + manual, abs=1e-14)
+
+
+# ---------------------------------------------------------------- X indicator (Sec. 3.1)
+@pytest.mark.parametrize("dims", [(3, 2), (2, 3, 2, 2)])
+def test_x_indicator_vs_two_site_network(dims):
+    """Brute force: Tr(M M) is the periodic two-site network along nu (each other leg
+    closing on itself), contracted as one einsum; Tr M is the one-site trace."""
+    rng = np.random.default_rng(31)
+    d = len(dims)
+    shape = sum(([n, n] for n in dims), [])
+    T = rng.standard_normal(shape)
+    for nu in range(d):
+        ext = [1] * d
+        ext[nu] = 2
+        want = H.trace(T) ** 2 / H.contract_periodic(T, ext)
+        assert H.x_indicator(T, nu) == pytest.approx(want, rel=1e-12)
+
+
+def test_x_indicator_counts_degenerate_leading_states():
+    """X = (sum m)^2 / sum m^2 for the eigenvalues m of the transfer matrix: a tensor whose
+    transfer matrix is diag(1, 1, 0) gives 2, diag(1, 0, 0) gives 1 (all other legs of
+    dimension 1)."""
+    for diag, want in (((1.0, 1.0, 0.0), 2.0), ((1.0, 0.0, 0.0), 1.0), ((1.0, 1.0, 1.0), 3.0)):
+        T = np.diag(diag).reshape(3, 3, 1, 1)
+        assert H.x_indicator(T, 0) == pytest.approx(want, rel=1e-14)
+
+
+def test_x_indicator_brackets_onsager_tc_2d():
+    """2D Ising: bisection on X = 1.5 after 24 steps (a 4096^2 lattice) at D_cut = 12 lands
+    on Onsager's T_c = 2 / ln(1 + sqrt 2) to 5e-4: X is 2 below it and 1 above it."""
+    tc = 2 / math.log(1 + math.sqrt(2))
+    lo, hi = 2.2, 2.35
+    assert H.x_indicator(H.run(2, 1 / lo, 0.0, 12, 24).T) > 1.9
+    assert H.x_indicator(H.run(2, 1 / hi, 0.0, 12, 24).T) < 1.1
+    for _ in range(8):
+        mid = 0.5 * (lo + hi)
+        if H.x_indicator(H.run(2, 1 / mid, 0.0, 12, 24).T) > 1.5:
+            lo = mid
+        else:
+            hi = mid
+    assert abs(0.5 * (lo + hi) - tc) / tc < 5e-4
+
+
+def test_x_indicator_4d_phases():
+    """4D, D_cut = 4, 16 steps (16^4): X near 2 deep in the ordered phase (T = 5), near 1
+    in the symmetric phase (T = 9), in every direction."""
+    lo = H.run(4, 1 / 5.0, 0.0, 4, 16).T
+    hi = H.run(4, 1 / 9.0, 0.0, 4, 16).T
+    for nu in range(4):
+        assert abs(H.x_indicator(lo, nu) - 2.0) < 0.01
+        assert abs(H.x_indicator(hi, nu) - 1.0) < 0.05
