@@ -59,6 +59,14 @@ def parse_args():
     p.add_argument("--tc", type=int, default=0,
                    help="instead of the step line: bracket T_c(D_cut) from the X indicator after 40 steps "
                         "(batched temperatures, --tc rounds) and print that as its own line")
+    p.add_argument("--scan", type=int, default=0,
+                   help="instead of the step line: E/V and <sigma> against T at this many temperatures in "
+                        "[--scan-lo, --scan-hi] (impure tensors, h = 1e-5, 40 steps), printed as its own line")
+    p.add_argument("--scan-lo", type=float, default=6.670)
+    p.add_argument("--scan-hi", type=float, default=6.690)
+    p.add_argument("--scan-h", type=float, default=1e-5, help="field of the scan")
+    p.add_argument("--gemm-variant", type=int, default=0,
+                   help="tensor-core GEMM pipeline option (HOTRG_OPT_GEMM_VARIANT) for every mixed run")
     p.add_argument("--precision", choices=["tf32x3", "fp16x3"], default="fp16x3",
                    help="tensor-core split of the block-spin contraction (default: fp16 hi/lo on kind::f16)")
     return p.parse_args()
@@ -276,6 +284,41 @@ def run_tc(args, local):
     return 0
 
 
+def run_scan(args, local):
+    """Internal energy and magnetisation against temperature (Sec. 3.1, Figs. 5 and 6) for the
+    volumes 2^28 .. 2^40: one batched run of T, S and M at --scan temperatures (field
+    --scan-h); reports the
+    values at volumes 2^28, 2^32, 2^36, 2^40, the largest jumps between adjacent temperatures
+    at 2^40 and the wall time, with the clocks seen."""
+    import numpy as np
+    import torch
+
+    from paper_1911_12954_gb300.tc import largest_jump, observable_scan
+
+    torch.cuda.set_device(local)
+    temps = np.linspace(args.scan_lo, args.scan_hi, args.scan)
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        rows = observable_scan(temps, args.dcut, nsteps=40, h=args.scan_h, precision=args.precision, record_from=28)
+        secs = time.perf_counter() - t0
+    last = rows[-1]
+    ie, de = largest_jump(temps, last["E"])
+    im, dm = largest_jump(temps, last["m"])
+    line = {"metric": f"E/V and <sigma> scan against T, D_cut={args.dcut}, volumes 2^28..2^40", "value": secs,
+            "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": f"4D Ising HOTRG, h={args.scan_h}, D_cut={args.dcut}, 40 steps (x,y,z,t cycled), "
+                                   f"{args.scan} temperatures in [{args.scan_lo}, {args.scan_hi}], pure + sigma + "
+                                   f"sigma-sigma impure tensors in one batch"},
+            "T": [float(t) for t in temps],
+            "volumes": {f"2^{r['k']}": {"E": [float(x) for x in r["E"]], "m": [float(x) for x in r["m"]]}
+                        for r in rows if r["k"] in (28, 32, 36, 40)},
+            "energy_jump_2^40": {"between": [float(temps[ie]), float(temps[ie + 1])], "dE": de},
+            "magnetization_jump_2^40": {"between": [float(temps[im]), float(temps[im + 1])], "dm": dm},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", 0))
@@ -285,11 +328,13 @@ def main():
         return run_reference(args, rank, world)
     if args.tc:
         return run_tc(args, local) if rank == 0 else 0
+    if args.scan:
+        return run_scan(args, local) if rank == 0 else 0
 
     import numpy as np
     import torch
 
-    from paper_1911_12954_gb300 import HOTRG
+    from paper_1911_12954_gb300 import HOTRG, OPT_GEMM_VARIANT
 
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -330,6 +375,7 @@ def main():
     # ---------------------------------------------------------------- mixed precision, timed
     run = HOTRG(batch=args.batch, dcut_max=D, precision=args.precision, impure=impure, schedule=sched,
                 graphs=bool(args.graphs))
+    run.set_option(OPT_GEMM_VARIANT, args.gemm_variant)
     run.init_tensor(betas, hfield)
     for i in range(args.warmup):
         run.step(*sched[i])
@@ -360,6 +406,7 @@ def main():
     nver = 8 if D <= 8 else 3
     # the first temperature of this rank's workload, with its field and impure tensors
     ver = HOTRG(batch=1, dcut_max=D, precision=args.precision, impure=impure, schedule=sched[:nver])
+    ver.set_option(OPT_GEMM_VARIANT, args.gemm_variant)
     ver.init_tensor(beta, hfield)
     mixed_lnz = []
     for i in range(nver):
@@ -407,6 +454,7 @@ def main():
     if args.e2e and args.batch == 1 and not impure:
         full = [(i % 4, D) for i in range(LATTICE_STEPS)]
         job = HOTRG(batch=1, dcut_max=D, precision=args.precision, schedule=full)
+        job.set_option(OPT_GEMM_VARIANT, args.gemm_variant)
         bh = torch.tensor([beta], dtype=torch.float64).pin_memory()
         hh = torch.tensor([H_WORK], dtype=torch.float64).pin_memory()
         job.init_tensor(bh.numpy(), hh.numpy())           # warm the job once
@@ -432,7 +480,7 @@ def main():
     # ---------------------------------------------------------------- CPU oracle baseline
     cpu = None
     if args.cpu and rank == 0 and world == 1:
-        nx = 2 if D >= 8 else 1            # about 10-20 s of host work at D_cut = 8
+        nx = 3 if D >= 8 else 1            # about 15-25 s of host work at D_cut = 8
         f, s = oracle_sample(D, nx=nx)
         cpu = {"value": f / s / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"one steady-state D_cut={D} step of the FP64 NumPy oracle on a seeded N(0,1) tensor of "
@@ -453,7 +501,7 @@ def main():
                                + f", D_cut={D}, 1024^4 lattice schedule (x,y,z,t cycled); timed steps "
                                f"{args.warmup + 1}..{nsteps} (steady state)",
                    "dcut": D, "temperatures_per_gpu": args.batch, "impure": bool(impure), "lattice": "1024^4",
-                   "precision": f"{args.precision} (fp32 storage)", "cuda_graphs": bool(args.graphs),
+                   "precision": f"{args.precision} (fp32 storage)", "cuda_graphs": bool(args.graphs), "gemm_variant": args.gemm_variant,
                    "l2": f"operands larger than L2 (GEMM A and B: 2 x "
                          f"{(4 if args.precision == 'fp16x3' else 8) * D ** 10 / 1e9:.1f} GB per step, hi + lo)"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

@@ -78,6 +78,7 @@ using CfgTF32 = Cfg<64, false, 32>;     // default tf32 pipeline: 4 stages of 16
 using CfgTF32W = Cfg<128, false, 32>;   // tf32, 2 stages of 32-wide k-blocks
 using CfgF16 = Cfg<64, true, 128>;      // fp16: 4 stages of 32-wide k-blocks, 128-k chunks
 using CfgF16S = Cfg<64, true, 64>;      // fp16 with 64-k chunks
+using CfgF16L = Cfg<64, true, 256>;     // fp16 with 256-k chunks
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -465,16 +466,18 @@ cudaError_t launch_variant(const void* Ahi, const void* Alo, const void* Bhi, co
 // K-major layout. variant 0 (default): tf32, k-blocks of 16, 64-byte swizzle, 4 stages;
 // variant 1: tf32, k-blocks of 32, 128-byte swizzle, 2 stages; variant 2: fp16 operands
 // (hi/lo planes of __half), k-blocks of 32, 64-byte swizzle, 4 stages, 128-k promotion
-// chunks (kps % 8 == 0); variant 3: as 2 with 64-k chunks.
+// chunks (kps % 8 == 0); variant 3: as 2 with 64-k chunks; variant 4: as 2 with 256-k chunks.
 cudaError_t launch_gemm_tf32x3_v(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int64_t Kp,
                                  int64_t kps, int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha,
                                  float beta, int* status, cudaStream_t st, int variant) {
   using namespace tc;
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (Kp <= 0 || P <= 0 || M > 0x7fffffff || N > 0x7fffffff || Kp * P > 0x7fffffff) return cudaErrorInvalidValue;
-  const bool f16 = variant == 2 || variant == 3;
+  const bool f16 = variant >= 2 && variant <= 4;
   if ((kps & (f16 ? 7 : 3)) || kps < Kp) return cudaErrorInvalidValue;
   if ((((uintptr_t)Ahi) | ((uintptr_t)Alo) | ((uintptr_t)Bhi) | ((uintptr_t)Blo)) & 15) return cudaErrorInvalidValue;
+  if (variant == 4)
+    return launch_variant<CfgF16L>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
   if (variant == 3)
     return launch_variant<CfgF16S>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
   if (variant == 2)
@@ -500,6 +503,8 @@ void gemm_prepare() {
                        (int)CfgF16::SMEM_BYTES);
   cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgF16S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)CfgF16S::SMEM_BYTES);
+  cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgF16L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)CfgF16L::SMEM_BYTES);
   done = true;
 }
 

@@ -655,7 +655,8 @@ hotrg_status gemm_launch(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, c
     // operands carry the factor 2^14 each
     const float unscale = 1.0f / (kF16Scale * kF16Scale);
     CK(launch_gemm_tf32x3_v(A, Alo, B, Blo, p.Kp, p.kps, p.P, (float*)C, N, M, N, (float)alpha * unscale,
-                            (float)beta, (int*)(ctx->ws + ctx->L.status), st, ctx->gemm_variant == 1 ? 3 : 2),
+                            (float)beta, (int*)(ctx->ws + ctx->L.status), st,
+                            ctx->gemm_variant == 1 ? 3 : (ctx->gemm_variant == 2 ? 4 : 2)),
        "gemm f16x3");
   } else {
     if (p.P != 1) return HOTRG_EUNSUPPORTED;
@@ -1321,7 +1322,7 @@ hotrg_status hotrg_set_option(hotrg_ctx* ctx, int option, int value) {
       ctx->drop_graphs();
       return HOTRG_OK;
     case HOTRG_OPT_GEMM_VARIANT:
-      if (value < 0 || value > 1) return HOTRG_EINVAL;
+      if (value < 0 || value > (ctx->prec == HOTRG_FP16X3 ? 2 : 1)) return HOTRG_EINVAL;
       ctx->gemm_variant = value;
       ctx->drop_graphs();
       return HOTRG_OK;

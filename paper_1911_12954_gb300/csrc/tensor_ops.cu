@@ -120,6 +120,7 @@ __device__ __forceinline__ void fiber_offsets(const FiberArgs& a, uint32_t f, in
   }
 }
 
+// acc already carries the 2^14 factor in kTTMSplitF16 mode (folded into U by the caller)
 template <typename R, int MODE>
 __device__ __forceinline__ void fiber_store(R* out, R* out_lo, int64_t o, R acc) {
   if (MODE == kTTMSplitTF32) {
@@ -129,7 +130,7 @@ __device__ __forceinline__ void fiber_store(R* out, R* out_lo, int64_t o, R acc)
     out_lo[o] = (R)tf32_round(v - hi);
   } else if (MODE == kTTMSplitF16) {
     // fp16 hi + lo of 2^14 x: the pair keeps 22 significant bits
-    const float v = (float)acc * kF16Scale;
+    const float v = (float)acc;
     const __half hi = __float2half_rn(v);
     ((__half*)out)[o] = hi;
     ((__half*)out_lo)[o] = __float2half_rn(v - __half2float(hi));
@@ -150,12 +151,14 @@ __global__ void __launch_bounds__(256) ttm_short_kernel(const R* __restrict__ in
   R* Us = (R*)fsm;                                       // [J][Rp], zero past Rn
   int64_t* roff = (int64_t*)(fsm + (size_t)J * Rp * sizeof(R));   // [Rp] output offset of r
   int64_t* joff = roff + Rp;                             // [J] input offset of j
+  // the fp16 split's 2^14 (exact, a power of two) is folded into U
+  const R uscale = MODE == kTTMSplitF16 ? (R)kF16Scale : (R)1;
   for (int e = threadIdx.x; e < J * Rp; e += blockDim.x) {
     const int j = e / Rp, r = e % Rp;
     R v = 0;
     if (r < Rn) {
       const int j1 = j / a.J2, j2 = j % a.J2, r1 = r / a.R2, r2 = r % a.R2;
-      v = U[j1 * a.ju1 + j2 * a.ju2 + r1 * a.ru1 + r2 * a.ru2];
+      v = U[j1 * a.ju1 + j2 * a.ju2 + r1 * a.ru1 + r2 * a.ru2] * uscale;
     }
     Us[e] = v;
   }
@@ -163,6 +166,7 @@ __global__ void __launch_bounds__(256) ttm_short_kernel(const R* __restrict__ in
   for (int j = threadIdx.x; j < J; j += blockDim.x) joff[j] = (j / a.J2) * a.ji1 + (j % a.J2) * a.ji2;
   __syncthreads();
   const R alpha = (R)a.alpha;
+  const bool scaled = a.alpha != 1.0;
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < a.nfib; f += (int64_t)gridDim.x * blockDim.x) {
     int64_t io, oo;
     fiber_offsets(a, (uint32_t)f, io, oo);
@@ -198,7 +202,83 @@ __global__ void __launch_bounds__(256) ttm_short_kernel(const R* __restrict__ in
       }
 #pragma unroll
       for (int i = 0; i < kShortRB; ++i)
-        if (rb + i < Rn) fiber_store<R, MODE>(out, out_lo, oo + roff[rb + i], acc[i] * alpha);
+        if (rb + i < Rn) fiber_store<R, MODE>(out, out_lo, oo + roff[rb + i], scaled ? acc[i] * alpha : acc[i]);
+    }
+  }
+}
+
+// The fp16 split of a short contraction, two fibres per thread: when the innermost fibre leg
+// has output stride 1 and an even extent (and every other output stride is even), fibres
+// 2f and 2f + 1 are neighbours in the output, so their hi (and lo) values go out as one
+// 4-byte half2: a warp store fills a 128-byte line and each U row read serves two fibres.
+template <typename R>
+__global__ void __launch_bounds__(256) ttm_pair_f16_kernel(const R* __restrict__ in, const R* __restrict__ U,
+                                                           R* __restrict__ out, R* __restrict__ out_lo, FiberArgs a) {
+  constexpr int RB = 16;
+  extern __shared__ __align__(16) unsigned char fsm[];
+  const int J = a.J1 * a.J2, Rn = a.R1 * a.R2;
+  const int Rp = (Rn + kShortRB - 1) / kShortRB * kShortRB;
+  R* Us = (R*)fsm;                                       // [J][Rp], zero past Rn, times 2^14
+  int64_t* roff = (int64_t*)(fsm + (size_t)J * Rp * sizeof(R));
+  int64_t* joff = roff + Rp;
+  for (int e = threadIdx.x; e < J * Rp; e += blockDim.x) {
+    const int j = e / Rp, r = e % Rp;
+    R v = 0;
+    if (r < Rn) {
+      const int j1 = j / a.J2, j2 = j % a.J2, r1 = r / a.R2, r2 = r % a.R2;
+      v = U[j1 * a.ju1 + j2 * a.ju2 + r1 * a.ru1 + r2 * a.ru2] * (R)kF16Scale;
+    }
+    Us[e] = v;
+  }
+  for (int r = threadIdx.x; r < Rp; r += blockDim.x) roff[r] = r < Rn ? (r / a.R2) * a.ro1 + (r % a.R2) * a.ro2 : 0;
+  for (int j = threadIdx.x; j < J; j += blockDim.x) joff[j] = (j / a.J2) * a.ji1 + (j % a.J2) * a.ji2;
+  __syncthreads();
+  const int64_t step_in = a.fin[a.nf - 1];     // input offset from fibre 2f to 2f + 1
+  const int64_t npair = a.nfib / 2;
+  __half* hi_out = (__half*)out;
+  __half* lo_out = (__half*)out_lo;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < npair; f += (int64_t)gridDim.x * blockDim.x) {
+    int64_t io, oo;
+    fiber_offsets(a, (uint32_t)(2 * f), io, oo);   // oo is even: a 4-byte aligned half2 slot
+    R x0[kShortJ], x1[kShortJ];
+#pragma unroll
+    for (int j = 0; j < kShortJ; ++j) {
+      x0[j] = j < J ? in[io + joff[j]] : (R)0;
+      x1[j] = j < J ? in[io + step_in + joff[j]] : (R)0;
+    }
+    for (int rb = 0; rb < Rn; rb += RB) {
+      R a0[RB], a1[RB];
+#pragma unroll
+      for (int i = 0; i < RB; ++i) a0[i] = a1[i] = 0;
+#pragma unroll
+      for (int j = 0; j < kShortJ; ++j) {
+        if (j < J) {
+          const R* u = Us + j * Rp + rb;
+#pragma unroll
+          for (int i = 0; i < RB; i += 4) {
+            const float4 q = *(const float4*)(u + i);
+            a0[i] = fmaf(q.x, x0[j], a0[i]);
+            a0[i + 1] = fmaf(q.y, x0[j], a0[i + 1]);
+            a0[i + 2] = fmaf(q.z, x0[j], a0[i + 2]);
+            a0[i + 3] = fmaf(q.w, x0[j], a0[i + 3]);
+            a1[i] = fmaf(q.x, x1[j], a1[i]);
+            a1[i + 1] = fmaf(q.y, x1[j], a1[i + 1]);
+            a1[i + 2] = fmaf(q.z, x1[j], a1[i + 2]);
+            a1[i + 3] = fmaf(q.w, x1[j], a1[i + 3]);
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        if (rb + i < Rn) {
+          const int64_t o = oo + roff[rb + i];
+          const __half h0 = __float2half_rn(a0[i]), h1 = __float2half_rn(a1[i]);
+          const __half l0 = __float2half_rn(a0[i] - __half2float(h0));
+          const __half l1 = __float2half_rn(a1[i] - __half2float(h1));
+          *(__half2*)(hi_out + o) = __halves2half2(h0, h1);
+          *(__half2*)(lo_out + o) = __halves2half2(l0, l1);
+        }
+      }
     }
   }
 }
@@ -259,6 +339,87 @@ __global__ void __launch_bounds__(256) ttm_long_kernel(const R* __restrict__ in,
   }
 }
 
+// The long form four fibres per thread: when the innermost fibre leg has input and output
+// stride 1 and an extent divisible by 4 (every other stride a multiple of 4), fibres 4f..4f+3
+// are neighbours in both tensors, so each contracted index is one 16-byte load and each
+// output one 16-byte store.
+template <int RB>
+__global__ void __launch_bounds__(256) ttm_long4_kernel(const float* __restrict__ in, const float* __restrict__ U,
+                                                        float* __restrict__ out, FiberArgs a) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  const int J = a.J1 * a.J2, Rn = a.R1 * a.R2;
+  float* Us = (float*)fsm;                               // [J][RB], zero past Rn
+  int64_t* roff = (int64_t*)(fsm + (size_t)J * RB * sizeof(float));
+  for (int e = threadIdx.x; e < J * RB; e += blockDim.x) {
+    const int j = e / RB, r = e % RB;
+    float v = 0;
+    if (r < Rn) {
+      const int j1 = j / a.J2, j2 = j % a.J2, r1 = r / a.R2, r2 = r % a.R2;
+      v = U[j1 * a.ju1 + j2 * a.ju2 + r1 * a.ru1 + r2 * a.ru2];
+    }
+    Us[e] = v;
+  }
+  for (int r = threadIdx.x; r < RB; r += blockDim.x) roff[r] = r < Rn ? (r / a.R2) * a.ro1 + (r % a.R2) * a.ro2 : 0;
+  __syncthreads();
+  const float alpha = (float)a.alpha;
+  const int64_t nquad = a.nfib / 4;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nquad; f += (int64_t)gridDim.x * blockDim.x) {
+    int64_t io, oo;
+    fiber_offsets(a, (uint32_t)(4 * f), io, oo);   // both multiples of 4: 16-byte aligned
+    float4 acc[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int j1 = 0; j1 < a.J1; ++j1) {
+      const float* src = in + io + j1 * a.ji1;
+      const float* u = Us + (size_t)j1 * a.J2 * RB;
+      int j2 = 0;
+      for (; j2 + 4 <= a.J2; j2 += 4) {
+        float4 xv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) xv[q] = *(const float4*)(src + (int64_t)(j2 + q) * a.ji2);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float* uq = u + (j2 + q) * RB;
+#pragma unroll
+          for (int r = 0; r < RB; ++r) {
+            const float w = uq[r];
+            acc[r].x = fmaf(w, xv[q].x, acc[r].x);
+            acc[r].y = fmaf(w, xv[q].y, acc[r].y);
+            acc[r].z = fmaf(w, xv[q].z, acc[r].z);
+            acc[r].w = fmaf(w, xv[q].w, acc[r].w);
+          }
+        }
+      }
+      for (; j2 < a.J2; ++j2) {
+        const float4 xv = *(const float4*)(src + (int64_t)j2 * a.ji2);
+        const float* uq = u + j2 * RB;
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+          const float w = uq[r];
+          acc[r].x = fmaf(w, xv.x, acc[r].x);
+          acc[r].y = fmaf(w, xv.y, acc[r].y);
+          acc[r].z = fmaf(w, xv.z, acc[r].z);
+          acc[r].w = fmaf(w, xv.w, acc[r].w);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+      if (r < Rn)
+        *(float4*)(out + oo + roff[r]) =
+            make_float4(acc[r].x * alpha, acc[r].y * alpha, acc[r].z * alpha, acc[r].w * alpha);
+  }
+}
+
+// Fibres 4f..4f+3 are neighbours with 16-byte aligned starts in input and output.
+inline bool quadable(const FiberArgs& f, const void* in, const void* out) {
+  if (f.nf < 1 || f.fin[f.nf - 1] != 1 || f.fout[f.nf - 1] != 1 || (f.fdims[f.nf - 1] & 3)) return false;
+  for (int d = 0; d < f.nf - 1; ++d)
+    if ((f.fin[d] & 3) || (f.fout[d] & 3)) return false;
+  if ((f.ji1 & 3) || (f.ji2 & 3) || (f.ro1 & 3) || (f.ro2 & 3)) return false;
+  return ((((uintptr_t)in) | ((uintptr_t)out)) & 15) == 0;
+}
+
 inline size_t short_smem(int J, int Rn, size_t rsize) {
   const size_t Rp = (size_t)(Rn + kShortRB - 1) / kShortRB * kShortRB;
   return (size_t)J * Rp * rsize + (Rp + (size_t)J) * sizeof(int64_t);
@@ -310,6 +471,16 @@ bool to_fiber(const TTMArgs& a, size_t rsize, FiberArgs& f) {
   return Rn <= kLongRMax && long_smem(J, Rn, rsize) <= kFiberSmemMax;
 }
 
+// Fibres 2f, 2f + 1 share a 4-byte aligned half2 slot: innermost fibre leg of even extent and
+// output stride 1, every other output stride (fibre legs and new index) even, planes 4-byte aligned.
+inline bool pairable(const FiberArgs& f, const void* out, const void* out_lo) {
+  if (f.nf < 1 || f.fout[f.nf - 1] != 1 || (f.fdims[f.nf - 1] & 1)) return false;
+  for (int d = 0; d < f.nf - 1; ++d)
+    if (f.fout[d] & 1) return false;
+  if ((f.ro1 & 1) || (f.ro2 & 1)) return false;
+  return ((((uintptr_t)out) | ((uintptr_t)out_lo)) & 3) == 0;
+}
+
 template <typename R>
 cudaError_t launch_fiber(const R* in, const R* U, R* out, R* out_lo, const FiberArgs& f, int mode, cudaStream_t st) {
   const int J = f.J1 * f.J2, Rn = f.R1 * f.R2;
@@ -319,11 +490,28 @@ cudaError_t launch_fiber(const R* in, const R* U, R* out, R* out_lo, const Fiber
   if (J > kShortJ) {               // long form (plain store only)
     if (mode != kTTMStore) return cudaErrorInvalidValue;
     const size_t smem = long_smem(J, Rn, sizeof(R));
+    if constexpr (sizeof(R) == 4) {
+      if (quadable(f, in, out)) {
+        int64_t qblocks = (f.nfib / 4 + 255) / 256;
+        if (qblocks > 152 * 16) qblocks = 152 * 16;
+        if (long_rb(Rn) == 8) ttm_long4_kernel<8><<<(unsigned)qblocks, 256, smem, st>>>(in, U, out, f);
+        else ttm_long4_kernel<kLongRMax><<<(unsigned)qblocks, 256, smem, st>>>(in, U, out, f);
+        return cudaGetLastError();
+      }
+    }
     if (long_rb(Rn) == 8) ttm_long_kernel<R, 8><<<g, 256, smem, st>>>(in, U, out, f);
     else ttm_long_kernel<R, kLongRMax><<<g, 256, smem, st>>>(in, U, out, f);
     return cudaGetLastError();
   }
   const size_t smem = short_smem(J, Rn, sizeof(R));
+  if constexpr (sizeof(R) == 4) {
+    if (mode == kTTMSplitF16 && f.alpha == 1.0 && pairable(f, out, out_lo)) {
+      int64_t pblocks = (f.nfib / 2 + 255) / 256;
+      if (pblocks > 152 * 16) pblocks = 152 * 16;
+      ttm_pair_f16_kernel<R><<<(unsigned)pblocks, 256, smem, st>>>(in, U, out, out_lo, f);
+      return cudaGetLastError();
+    }
+  }
   if (mode == kTTMSplitTF32) ttm_short_kernel<R, kTTMSplitTF32><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
   else if (mode == kTTMSplitF16) ttm_short_kernel<R, kTTMSplitF16><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
   else ttm_short_kernel<R, kTTMStore><<<g, 256, smem, st>>>(in, U, out, out_lo, f);

@@ -453,6 +453,24 @@ def test_tc_bracket_agrees_with_oracle():
     assert H.x_indicator(H.run(4, 1 / hi, 0.0, 4, 16).T) <= 1.5
 
 
+def test_observable_scan_matches_oracle():
+    """observable_scan (one batched impure run, FP64 mode, D_cut = 4, h = 1e-5): E/V, <sigma>
+    and ln Z/V recorded after steps 10..12 equal the oracle's at each temperature."""
+    from paper_1911_12954_gb300.tc import observable_scan
+    temps = [6.0, 7.0]
+    rows = observable_scan(temps, 4, nsteps=12, h=1e-5, precision="fp64", record_from=10)
+    assert [r["k"] for r in rows] == [10, 11, 12]
+    for b, t in enumerate(temps):
+        st = H.HOTRG.start(4, 1 / t, 1e-5, impure=True)
+        for k in range(12):
+            st.step(k % 4, 4)
+            if k + 1 >= 10:
+                r = rows[k + 1 - 10]
+                assert r["E"][b] == pytest.approx(st.energy(), rel=1e-9, abs=1e-12)
+                assert r["m"][b] == pytest.approx(st.magnetization(), rel=1e-9, abs=1e-12)
+                assert r["lnZ"][b] == pytest.approx(st.lnZ(), rel=1e-12)
+
+
 def test_cuda_graph_steps_match_eager_steps():
     """Captured-and-replayed steps (one graph launch per step, every batch element and
     impure tensor inside) give bit-identical results to eager launches: 16 steps, so the

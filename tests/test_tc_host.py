@@ -33,3 +33,12 @@ def test_tc_bracket_rounds_narrow_the_interval(monkeypatch):
     assert lo < 6.6503 <= hi
     assert hi - lo == pytest.approx(0.1 / 4 ** 3, rel=1e-9)
     assert len(calls) == 3 and all(len(c) == 5 for c in calls)
+
+
+def test_largest_jump():
+    """The adjacent pair with the largest change, signed; argument checks."""
+    from paper_1911_12954_gb300.tc import largest_jump
+    i, d = largest_jump([1.0, 2.0, 3.0, 4.0], [-1.00, -1.01, -0.95, -0.949])
+    assert i == 1 and d == pytest.approx(0.06)
+    with pytest.raises(ValueError):
+        largest_jump([2.0, 1.0], [0.0, 1.0])
