@@ -3,7 +3,10 @@
 //
 // jacobi_kernel: one CTA per matrix. Cyclic two-sided Jacobi in round-robin (tournament)
 // order: each round rotates n/2 disjoint index pairs at once, so every 2x2 block of A is
-// updated by exactly one thread and the rounds need only block barriers. A pair is
+// updated by exactly one thread and the rounds need only block barriers. The tournament runs
+// separately inside each connected component of A's nonzero pattern (exact zeros between
+// components stay exact zeros), which quarters the work when the Gram matrix splits by Z2
+// charge. A pair is
 // rotated when |a_pq| > max(1e-18 ||G||_F, 2^-52 sqrt|a_pp a_qq|); a sweep without
 // rotations ends the loop, and max_sweeps sweeps (kJacobiMaxSweeps unless the context
 // overrides it) raise the no-convergence status
@@ -73,12 +76,20 @@ __global__ void __launch_bounds__(kJT) jacobi_kernel(const __grid_constant__ Eig
                                                      double cluster_tau, double tie_rel, int max_sweeps,
                                                      int* status) {
   extern __shared__ double dyn[];
-  __shared__ double cs[kMaxGramN / 2 + 1], sn[kMaxGramN / 2 + 1];
-  __shared__ int pp[kMaxGramN / 2 + 1], qq[kMaxGramN / 2 + 1];
+  // one slot per rotation pair of a round: at most n (ceil(m_c / 2) <= m_c per component)
+  __shared__ double cs[kMaxGramN], sn[kMaxGramN];
+  __shared__ int pp[kMaxGramN], qq[kMaxGramN];
   __shared__ double lam[kMaxGramN], nrm[kMaxGramN];
   __shared__ int perm[kMaxGramN], cstart[kMaxGramN + 1];
   __shared__ double red[kJT / 32];
   __shared__ int rotated, ncl, pivot;
+  __shared__ int comp[kMaxGramN];          // component label: its smallest index
+  __shared__ int mem[kMaxGramN];           // indices grouped by component
+  __shared__ int cbeg[kMaxGramN + 1];      // component c: mem[cbeg[c] .. cbeg[c + 1])
+  __shared__ int poff[kMaxGramN + 1];      // first pair slot of component c
+  __shared__ int toff[kMaxGramN + 1];      // first 2x2 block of component c
+  __shared__ int voff[kMaxGramN + 1];      // first V-update item of component c
+  __shared__ int ncomp, rmax, changed;
   __shared__ double pivval;
 
   const EigJob& jb = jobs.j[blockIdx.x];
@@ -99,45 +110,98 @@ __global__ void __launch_bounds__(kJT) jacobi_kernel(const __grid_constant__ Eig
   fro = sqrt(block_sum(fro, red));
   const double tol_abs = 1e-18 * fro;
   const double tol_rel = 2.220446049250313e-16;
-  const int m = (n % 2 == 0) ? n : n + 1;
-  const int half = m / 2;
+
+  // ---- connected components of the nonzero pattern of A. A rotation of a pair inside one
+  // component leaves the entries between components exactly zero (and the rows of V outside
+  // the component too), so each component is diagonalised by its own round-robin tournament
+  // and the rest is skipped, exactly. With h = 0 the Gram matrices of the Ising tensors split
+  // this way by the Z2 charge of the fused index (two halves: a quarter of the FP64 work);
+  // a connected matrix takes the plain tournament, operation for operation.
+  for (int i = tid; i < n; i += kJT) comp[i] = i;
+  while (true) {
+    __syncthreads();
+    if (tid == 0) changed = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += kJT) {
+      int lab = comp[i];
+      for (int j = 0; j < n; ++j)
+        if (A[i * n + j] != 0.0 && comp[j] < lab) lab = comp[j];
+      if (lab < comp[i]) {
+        comp[i] = lab;
+        changed = 1;
+      }
+    }
+    __syncthreads();
+    if (!changed) break;
+  }
+  if (tid == 0) {
+    // components in the order of their smallest member; members in increasing index
+    int nc = 0;
+    for (int i = 0; i < n; ++i)
+      if (comp[i] == i) perm[i] = nc++;   // perm: label -> component number (scratch here)
+    for (int c = 0; c <= nc; ++c) cbeg[c] = 0;
+    for (int i = 0; i < n; ++i) ++cbeg[perm[comp[i]] + 1];
+    for (int c = 0; c < nc; ++c) cbeg[c + 1] += cbeg[c];
+    for (int c = 0; c < nc; ++c) cstart[c] = cbeg[c];   // fill cursor (scratch here)
+    for (int i = 0; i < n; ++i) mem[cstart[perm[comp[i]]]++] = i;
+    poff[0] = toff[0] = voff[0] = 0;
+    int rm = 1;
+    for (int c = 0; c < nc; ++c) {
+      const int mc = cbeg[c + 1] - cbeg[c], mp = mc + (mc & 1), np = mp / 2;
+      poff[c + 1] = poff[c] + np;
+      toff[c + 1] = toff[c] + np * (np + 1) / 2;
+      voff[c + 1] = voff[c] + mc * np;
+      rm = max(rm, mp - 1);
+    }
+    ncomp = nc;
+    rmax = rm;
+  }
+  __syncthreads();
+  const int nc = ncomp, npairs = poff[nc], nblk = toff[nc], nvu = voff[nc], rounds = rmax;
 
   int sweep = 0;
   for (; sweep < max_sweeps && n > 1; ++sweep) {
     if (tid == 0) rotated = 0;
     __syncthreads();
-    for (int r = 0; r < m - 1; ++r) {
-      for (int i = tid; i < half; i += kJT) {
-        int p, q;
-        rr_pair(r, i, m, p, q);
-        double c = 1.0, s = 0.0;
-        if (q < n) {
+    for (int r = 0; r < rounds; ++r) {
+      for (int sl = tid; sl < npairs; sl += kJT) {
+        int c = 0;
+        while (poff[c + 1] <= sl) ++c;
+        const int mc = cbeg[c + 1] - cbeg[c], mp = mc + (mc & 1);
+        int lp, lq;
+        rr_pair(r % (mp - 1), sl - poff[c], mp, lp, lq);
+        const int p = mem[cbeg[c] + lp], q = lq < mc ? mem[cbeg[c] + lq] : -1;
+        double cr = 1.0, sr = 0.0;
+        if (q >= 0) {
           const double apq = A[p * n + q], app = A[p * n + p], aqq = A[q * n + q];
           if (fabs(apq) > fmax(tol_abs, tol_rel * sqrt(fabs(app * aqq)))) {
             const double tau = (aqq - app) / (2.0 * apq);
             const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
+            cr = 1.0 / sqrt(1.0 + t * t);
+            sr = t * cr;
             rotated = 1;
           }
         }
-        cs[i] = c;
-        sn[i] = s;
-        pp[i] = p;
-        qq[i] = q;
+        cs[sl] = cr;
+        sn[sl] = sr;
+        pp[sl] = p;
+        qq[sl] = q;
       }
       __syncthreads();
-      // A <- J^T A J, one 2x2 block (pair P rows, pair Q columns) per thread iteration, for
-      // P <= Q only: the block (Q, P) is written as the transpose, so A stays exactly
-      // symmetric and the FP64 work (the scarce pipe on this chip) is about halved
-      const int ntri = half * (half + 1) / 2;
-      for (int e = tid; e < ntri; e += kJT) {
+      // A <- J^T A J, one 2x2 block (pair P rows, pair Q columns) per thread iteration, P and Q
+      // of one component, P <= Q only: the block (Q, P) is written as the transpose, so A
+      // stays exactly symmetric and the FP64 work (the scarce pipe on this chip) is halved
+      for (int e = tid; e < nblk; e += kJT) {
+        int c = 0;
+        while (toff[c + 1] <= e) ++c;
         int P, Q;
-        tri_index(e, half, P, Q);
+        tri_index(e - toff[c], poff[c + 1] - poff[c], P, Q);
+        P += poff[c];
+        Q += poff[c];
         const double c1 = cs[P], s1 = sn[P], c2 = cs[Q], s2 = sn[Q];
         if (s1 == 0.0 && s2 == 0.0) continue;
         const int p1 = pp[P], q1 = qq[P], p2 = pp[Q], q2 = qq[Q];
-        const bool hq1 = q1 < n, hq2 = q2 < n;
+        const bool hq1 = q1 >= 0, hq2 = q2 >= 0;
         const double a = A[p1 * n + p2];
         const double b = hq2 ? A[p1 * n + q2] : 0.0;
         const double cc = hq1 ? A[q1 * n + p2] : 0.0;
@@ -147,32 +211,35 @@ __global__ void __launch_bounds__(kJT) jacobi_kernel(const __grid_constant__ Eig
         const double rc = s1 * a + c1 * cc, rd = s1 * b + c1 * d;
         // columns
         double na = c2 * ra - s2 * rb, nb = s2 * ra + c2 * rb;
-        double nc = c2 * rc - s2 * rd, nd = s2 * rc + c2 * rd;
+        double nc2 = c2 * rc - s2 * rd, nd = s2 * rc + c2 * rd;
         if (P == Q && s1 != 0.0) {
           nb = 0.0;
-          nc = 0.0;
+          nc2 = 0.0;
         }
         A[p1 * n + p2] = na;
         if (hq2) A[p1 * n + q2] = nb;
-        if (hq1) A[q1 * n + p2] = nc;
+        if (hq1) A[q1 * n + p2] = nc2;
         if (hq1 && hq2) A[q1 * n + q2] = nd;
         if (P != Q) {
           A[p2 * n + p1] = na;
           if (hq2) A[q2 * n + p1] = nb;
-          if (hq1) A[p2 * n + q1] = nc;
+          if (hq1) A[p2 * n + q1] = nc2;
           if (hq1 && hq2) A[q2 * n + q1] = nd;
         }
       }
-      // V <- V J
-      for (int e = tid; e < n * half; e += kJT) {
-        const int row = e / half, Q = e % half;
-        const double s = sn[Q];
-        if (s == 0.0) continue;
-        const double c = cs[Q];
+      // V <- V J, rows of the pair's component only (the others are zero in its columns)
+      for (int e = tid; e < nvu; e += kJT) {
+        int c = 0;
+        while (voff[c + 1] <= e) ++c;
+        const int np = poff[c + 1] - poff[c], t = e - voff[c];
+        const int row = mem[cbeg[c] + t / np], Q = poff[c] + t % np;
+        const double sv = sn[Q];
+        if (sv == 0.0) continue;
+        const double cv = cs[Q];
         const int p = pp[Q], q = qq[Q];
         const double vp = V[row * n + p], vq = V[row * n + q];
-        V[row * n + p] = c * vp - s * vq;
-        V[row * n + q] = s * vp + c * vq;
+        V[row * n + p] = cv * vp - sv * vq;
+        V[row * n + q] = sv * vp + cv * vq;
       }
       __syncthreads();
     }
