@@ -84,6 +84,48 @@ def test_single_step_random_tensor_fp64(dims, mu, dcut):
         assert info["eps"][n] == pytest.approx(isos[n].eps, rel=1e-9, abs=1e-13)
 
 
+def _z2_tensor(seed, dims):
+    """A random tensor with the Z2 structure of the h = 0 Ising tensors: index i of a leg has
+    charge i mod 2 and every entry of odd total charge is exactly zero."""
+    T = random_tensor(seed, dims)
+    shape = T.shape
+    parity = np.zeros(shape, dtype=np.int64)
+    for leg, n in enumerate(shape):
+        idx = (np.arange(n) % 2).reshape([n if l == leg else 1 for l in range(len(shape))])
+        parity = parity + idx
+    T[parity % 2 == 1] = 0.0
+    return T
+
+
+@pytest.mark.parametrize("dims,sched", [((4, 2, 3, 2), [(0, 6), (3, 6)]), ((3, 2, 4, 2), [(2, 5), (0, 5)])])
+def test_z2_structured_steps_fp64(dims, sched):
+    """Two steps from a Z2-structured random tensor (the Gram matrices split into charge
+    blocks, so the eigensolver runs one tournament per block): tensors, isometries, records
+    and ln c equal the oracle's, and the entries the oracle's tensor has at rounding level
+    (below 1e-11 of its largest; its eigh mixes the charge sectors at ~1e-14 here, the
+    structural entries are above 1e-7) are exact zeros on the GPU."""
+    T = _z2_tensor(77 + sum(dims), dims)
+    ref = H.HOTRG.from_tensor(T)
+    g = _gpu(batch=1, dcut_max=max(max(dims), 6), precision="fp64", schedule=sched, dims0=dims)
+    g.set_tensor(T)
+    for k, (mu, dcut) in enumerate(sched, 1):
+        trans = [n for n in range(4) if n != mu]
+        dims_k = ref.history[-1].dims_out if ref.history else dims
+        isos = {n: H.isometry(ref.T, ref.T, mu, n, dcut) for n in trans}
+        ref.step(mu, dcut)
+        g.step(mu, dcut)
+        Tg = g.tensor()
+        scale = np.abs(ref.T).max()
+        assert np.allclose(Tg, ref.T, rtol=0, atol=1e-12 * scale), k
+        assert np.all(Tg[np.abs(ref.T) < 1e-11 * scale] == 0.0), k
+        info = g.step_info(k)
+        assert info["ln_c"] == pytest.approx(ref.history[-1].ln_c, abs=1e-12)
+        for n in trans:
+            Ug = g.isometry(n, dold=dims_k[n], chi=isos[n].chi)
+            assert np.allclose(Ug, isos[n].U, atol=1e-11), (k, n)
+            assert info["eps"][n] == pytest.approx(isos[n].eps, rel=1e-9, abs=1e-13)
+
+
 @pytest.mark.parametrize("prec,tol", [("fp32", 3e-5), ("tf32x3", 3e-5), ("fp16x3", 3e-5)])
 @pytest.mark.parametrize("dims,mu,dcut", [CASES[0], CASES[3], CASES[5]])
 def test_single_step_random_tensor_mixed(prec, tol, dims, mu, dcut):
