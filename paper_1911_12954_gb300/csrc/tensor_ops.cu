@@ -1,10 +1,12 @@
 // tensor_ops.cu - memory-bound tensor kernels of the HOTRG step.
 //
-//  * ttm_short/long_kernel, ttm_kernel : contraction of one or two legs of a tensor with an isometry
-//                     (the half contractions T x U^a x U^b that build the operands of
-//                     the block-spin GEMM, and the closing contractions with U^c,
-//                     Fig. 1C), writing any output leg order, optionally split into
-//                     tf32 hi + lo for the tensor-core path.
+//  * ttm_short / ttm_pair_f16 / ttm_long / ttm_long4 kernels, ttm_kernel: contraction of one
+//                     or two legs of a tensor with an isometry (the half contractions
+//                     T x U^a x U^b that build the operands of the block-spin GEMM, and the
+//                     closing contractions with U^c, Fig. 1C), writing any output leg order,
+//                     optionally split into fp16 (or tf32) hi + lo planes for the tensor-core
+//                     path; one, two or four fibres per thread, the generic ttm_kernel for
+//                     shapes the fibre forms do not take.
 //  * init_kernel    : the 4D Ising site tensors T and S (Fig. 1A) and ln c_0.
 //  * sumsq/normalise: c = ||T'||_F in FP64, ln c / 2^k accumulated (ln Z / V), T' /= c.
 //  * trace_kernel   : Tr T (each leg joined to its primed partner), FP64.
