@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(256) gram_kernel(const __grid_constant__ GramP
       }
     }
     __syncthreads();
+    if (diag && ty > tx) continue;   // mirrored from the thread (tx, ty) at the end
     R part[4][4];
     for (int a = 0; a < 4; ++a)
       for (int b = 0; b < 4; ++b) part[a][b] = 0;
@@ -112,13 +113,19 @@ __global__ void __launch_bounds__(256) gram_kernel(const __grid_constant__ GramP
         else two_sum_acc(acc[a][b], accl[a][b], part[a][b]);
       }
   }
+  // on a diagonal tile only the blocks ty <= tx were summed; the block (ty, tx) also gives
+  // (tx, ty) as its transpose (the same products in the same order: bit-identical)
+  if (diag && ty > tx) return;
   double* out = jb.partial + (int64_t)blockIdx.x * Rn * Rn;
   for (int a = 0; a < 4; ++a) {
     const int i = ti * kGT + ty * 4 + a;
     if (i >= Rn) continue;
     for (int b = 0; b < 4; ++b) {
       const int j = tj * kGT + tx * 4 + b;
-      if (j < Rn) out[(int64_t)i * Rn + j] = (double)acc[a][b] + (double)accl[a][b];
+      if (j >= Rn) continue;
+      const double v = (double)acc[a][b] + (double)accl[a][b];
+      out[(int64_t)i * Rn + j] = v;
+      if (diag && ty < tx) out[(int64_t)j * Rn + i] = v;
     }
   }
 }
