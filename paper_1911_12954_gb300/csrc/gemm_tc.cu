@@ -1,11 +1,12 @@
-// gemm_tc.cu - tcgen05 / TMEM / TMA GEMM for the block-spin contraction (TF32x3 mode).
+// gemm_tc.cu - tcgen05 / TMEM / TMA GEMM for the block-spin contraction (FP16x3 and TF32x3).
 //
 // C[m][n] = alpha * sum_k (Ahi Bhi + Ahi Blo + Alo Bhi)[m,n,k] + beta * C[m][n]
-// with A = Ahi + Alo and B = Bhi + Blo, each part a tf32 value stored in an FP32 word,
-// both operands K-major ([rows][ld] with ld % 4 == 0). This is the O(D^15) block-spin
-// contraction of the HOTRG step, where Sec. 2 of arXiv:1911.12954 places the D^(4d-1)
-// cost of the method, carried out on the 5th-generation tensor cores with FP32
-// accumulation; the dropped Alo Blo term is below 2^-21 of each product.
+// with A = Ahi + Alo and B = Bhi + Blo: either fp16 planes (hi, lo of 2^14 x; kind::f16,
+// the default) or tf32 values stored in FP32 words (kind::tf32), both operands K-major in
+// K panels (see tma_load). This is the O(D^15) block-spin contraction of the HOTRG step,
+// where Sec. 2 of arXiv:1911.12954 places the D^(4d-1) cost of the method, carried out on
+// the 5th-generation tensor cores with FP32 accumulation; the dropped Alo Blo term is below
+// 2^-21 of each product.
 //
 // The tensor cores add each MMA's products into the FP32 accumulator with truncation,
 // so an accumulator that runs over the whole K picks up a bias that grows linearly with
@@ -18,9 +19,9 @@
 // 128-k chunks 7 %).
 //
 // Structure: persistent kernel, one CTA per SM, 10 warps.
-//   warp 0 lane 0 : TMA producer. Per k-block of 32 (one 128-byte swizzle row), four
-//                   tiles (Ahi, Alo: 128x32; Bhi, Blo: 256x32) land in one pipeline stage
-//                   through cp.async.bulk.tensor with 128-byte swizzle.
+//   warp 0 lane 0 : TMA producer. Per k-block (one swizzle row of 64 bytes: 32 fp16 or 16
+//                   tf32 values), four tiles (Ahi, Alo: 128 rows; Bhi, Blo: 256 rows) land
+//                   in one pipeline stage through cp.async.bulk.tensor (3D, K panels).
 //   warp 1 lane 0 : MMA issuer. Per k-block, k-steps x 3 products of
 //                   tcgen05.mma.cta_group::1.kind::tf32 or kind::f16 (M=128, N=256) into one of
 //                   two TMEM chunk accumulators (2 x 256 of the 512 columns); commits free
