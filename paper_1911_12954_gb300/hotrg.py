@@ -121,7 +121,7 @@ class HOTRG:
     ----------
     batch : number of independent runs (temperatures).
     dcut_max : largest bond dimension (2..16).
-    precision : "fp64", "fp32" or "tf32x3".
+    precision : "fp64", "fp32", "tf32x3" or "fp16x3" (the fastest mixed mode).
     impure : 0, IMPURE_SIGMA or IMPURE_SIGMA | IMPURE_SIGMASIGMA.
     schedule : list of (dir, dcut) used to size the workspace (None: steady state at
         dcut_max), dims0 : starting bond dimensions for set_tensor runs.
