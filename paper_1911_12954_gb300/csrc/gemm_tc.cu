@@ -146,6 +146,25 @@ __device__ __forceinline__ void tma_load(const CUtensorMap* map, uint64_t* bar, 
       : "memory");
 }
 
+// The same load delivered to the same shared-memory offset (and completing the same mbarrier
+// offset) in every CTA of the cluster named by ctaMask.
+__device__ __forceinline__ void tma_load_mc(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y, int z,
+                                            uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(su32(dst)),
+      "l"((uint64_t)map), "r"(su32(bar)), "r"(x), "r"(y), "r"(z), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
 // K-major operand in the canonical swizzled layout TMA writes: rows of one swizzle width,
 // 8-row groups SBO bytes apart.
 template <class C>
@@ -180,6 +199,14 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
                : "memory");
 }
+// Arrives (once the MMAs issued so far have completed) on the mbarrier at this offset in
+// every CTA of the cluster named by ctaMask.
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                   su32(bar)),
+               "h"(mask)
+               : "memory");
+}
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -198,17 +225,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& tm, int& tn) {
-  const int per_group = GROUP_M * tiles_n;
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int group, int& tm, int& tn) {
+  const int per_group = group * tiles_n;
   const int g = t / per_group;
-  const int first_m = g * GROUP_M;
-  const int gm = min(GROUP_M, tiles_m - first_m);
+  const int first_m = g * group;
+  const int gm = min(group, tiles_m - first_m);
   const int r = t - g * per_group;
   tm = first_m + r % gm;
   tn = r / gm;
 }
 
-template <class CF>
+// CL = 2: clusters of two CTAs on vertically adjacent tiles (same N tile, M tiles 2g and
+// 2g + 1). Each CTA loads its own A tile and one half of the shared B tile, multicast into
+// both CTAs, so B is read from L2 once per pair; a stage is refilled only after both CTAs'
+// MMAs have read it (their commits arrive on both CTAs' empty barriers).
+template <class CF, int CL>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                        const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
@@ -227,8 +258,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint32_t* tmem_slot = (uint32_t*)(drain + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rm = CL == 2 ? (int)cluster_rank() : 0;    // this CTA's M tile within the pair
+  const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
   const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
-  const int ntiles = tiles_m * tiles_n;
+  const int tiles_mg = (tiles_m + CL - 1) / CL;          // M tiles per cluster group
+  const int ntiles = tiles_mg * tiles_n;
   const int nkbp = (Kp + BK - 1) / BK;   // k-blocks per panel (the last one zero-filled past Kp)
   const int nkb = P * nkbp;
   const int nchunk = (nkb + KPC - 1) / KPC;
@@ -236,7 +270,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], CL);      // the MMA commits of every CTA that reads this stage
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&cfull[a], 1);
@@ -252,7 +286,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   fence_before();
-  __syncthreads();
+  if (CL == 2) cluster_sync_all();   // the partner's barriers exist before any multicast
+  else __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -266,9 +301,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t ph = 0;
     int issued[STAGES] = {};
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      int tm, tn;
-      tile_coords(t, tiles_m, tiles_n, tm, tn);
+    for (int t = cid; t < ntiles && ok; t += ncl) {
+      int tg, tn;
+      tile_coords(t, tiles_mg, tiles_n, GROUP_M / CL, tg, tn);
+      const int tm = tg * CL + rm;
       for (int kb = 0; kb < nkb; ++kb) {
         if (!mbar_wait(&empty[s], ph ^ 1, status)) {
           ok = false;
@@ -276,11 +312,17 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         uint8_t* st = smem + s * STAGE_BYTES;
         const int pn = kb / nkbp, kx = (kb - pn * nkbp) * BK;
-        mbar_expect_tx(&full[s], STAGE_BYTES);
+        mbar_expect_tx(&full[s], STAGE_BYTES);   // own A + both halves of B
         tma_load(&mAhi, &full[s], st, kx, tm * BM, pn);
         tma_load(&mAlo, &full[s], st + A_BYTES, kx, tm * BM, pn);
-        tma_load(&mBhi, &full[s], st + 2 * A_BYTES, kx, tn * BN, pn);
-        tma_load(&mBlo, &full[s], st + 2 * A_BYTES + B_BYTES, kx, tn * BN, pn);
+        if (CL == 2) {
+          const int half = B_BYTES / 2, yb = tn * BN + rm * (BN / 2);
+          tma_load_mc(&mBhi, &full[s], st + 2 * A_BYTES + rm * half, kx, yb, pn, 3);
+          tma_load_mc(&mBlo, &full[s], st + 2 * A_BYTES + B_BYTES + rm * half, kx, yb, pn, 3);
+        } else {
+          tma_load(&mBhi, &full[s], st + 2 * A_BYTES, kx, tn * BN, pn);
+          tma_load(&mBlo, &full[s], st + 2 * A_BYTES + B_BYTES, kx, tn * BN, pn);
+        }
         ++issued[s];
         if (++s == STAGES) {
           s = 0;
@@ -296,7 +338,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     int s = 0, cb = 0;
     uint32_t ph = 0, cph = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    for (int t = cid; t < ntiles && ok; t += ncl) {
       for (int kb = 0; kb < nkb; ++kb) {
         const bool first = kb % KPC == 0;
         const bool last = kb % KPC == KPC - 1 || kb == nkb - 1;
@@ -316,7 +358,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           mma<CF>(d, ahi + off, blo + off, 1);
           mma<CF>(d, ahi + off, bhi + off, 1);
         }
-        mma_commit(&empty[s]);
+        if (CL == 2) mma_commit_mc(&empty[s], 3);
+        else mma_commit(&empty[s]);
         if (last) {
           mma_commit(&cfull[cb]);
           if (++cb == 2) {
@@ -342,9 +385,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     int cb = 0;
     uint32_t cph = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      int tm, tn;
-      tile_coords(t, tiles_m, tiles_n, tm, tn);
+    for (int t = cid; t < ntiles && ok; t += ncl) {
+      int tg, tn;
+      tile_coords(t, tiles_mg, tiles_n, GROUP_M / CL, tg, tn);
+      const int tm = tg * CL + rm;
       float acc[BN / 2];
 #pragma unroll
       for (int j = 0; j < BN / 2; ++j) acc[j] = 0.f;
@@ -397,6 +441,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   fence_before();
   __syncthreads();
+  // neither CTA leaves while the partner may still multicast into it or arrive on its barriers
+  if (CL == 2) cluster_sync_all();
   if (warp == 0) {
     __syncwarp();
     fence_after();
@@ -432,13 +478,41 @@ bool make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t Kp, int64
   return r == CUDA_SUCCESS;
 }
 
+// Grid of the 2-CTA cluster variant: twice the number of two-CTA clusters that can be
+// resident at once (every SM that can pair up), found once per kernel before any capture.
 template <class CF>
+int cluster_grid() {
+  static int grid = -1;
+  if (grid >= 0) return grid;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(2 * 64);
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = CF::SMEM_BYTES;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaFuncSetAttribute(gemm_tf32x3_kernel<CF, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)CF::SMEM_BYTES) != cudaSuccess ||
+      cudaOccupancyMaxActiveClusters(&n, gemm_tf32x3_kernel<CF, 2>, &cfg) != cudaSuccess)
+    n = 0;
+  cudaGetLastError();
+  grid = 2 * n;
+  return grid;
+}
+
+template <class CF, int CL>
 cudaError_t launch_variant(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int64_t Kp,
                            int64_t kps, int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha,
                            float beta, int* status, cudaStream_t st) {
   CUtensorMap mAhi, mAlo, mBhi, mBlo;
+  // with CL = 2 each CTA copies half of the B tile (BN / 2 rows) into both CTAs
   if (!make_map<CF>(&mAhi, Ahi, M, Kp, kps, P, BM) || !make_map<CF>(&mAlo, Alo, M, Kp, kps, P, BM) ||
-      !make_map<CF>(&mBhi, Bhi, N, Kp, kps, P, BN) || !make_map<CF>(&mBlo, Blo, N, Kp, kps, P, BN))
+      !make_map<CF>(&mBhi, Bhi, N, Kp, kps, P, BN / CL) || !make_map<CF>(&mBlo, Blo, N, Kp, kps, P, BN / CL))
     return cudaErrorInvalidValue;
   static int sms = 0;
   static bool attr = false;
@@ -448,16 +522,37 @@ cudaError_t launch_variant(const void* Ahi, const void* Alo, const void* Bhi, co
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(gemm_tf32x3_kernel<CF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(gemm_tf32x3_kernel<CF, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)CF::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
-  const int grid = (int)(tiles < sms ? tiles : sms);
-  gemm_tf32x3_kernel<CF><<<grid, THREADS, CF::SMEM_BYTES, st>>>(mAhi, mAlo, mBhi, mBlo, C, ldc, (int)M, (int)N,
-                                                               (int)Kp, (int)P, alpha, beta, status);
-  return cudaGetLastError();
+  const int64_t tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
+  if (CL == 1) {
+    const int64_t tiles = tiles_m * tiles_n;
+    const int grid = (int)(tiles < sms ? tiles : sms);
+    gemm_tf32x3_kernel<CF, CL><<<grid, THREADS, CF::SMEM_BYTES, st>>>(mAhi, mAlo, mBhi, mBlo, C, ldc, (int)M, (int)N,
+                                                                     (int)Kp, (int)P, alpha, beta, status);
+    return cudaGetLastError();
+  }
+  int grid = cluster_grid<CF>();
+  if (grid < 2) return cudaErrorInvalidConfiguration;
+  const int64_t pairs = (tiles_m + 1) / 2 * tiles_n;
+  if (grid / 2 > pairs) grid = (int)(2 * pairs);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = CF::SMEM_BYTES;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, gemm_tf32x3_kernel<CF, CL>, mAhi, mAlo, mBhi, mBlo, C, ldc, (int)M, (int)N, (int)Kp,
+                            (int)P, alpha, beta, status);
 }
 
 }  // namespace tc
@@ -467,25 +562,28 @@ cudaError_t launch_variant(const void* Ahi, const void* Alo, const void* Bhi, co
 // K-major layout. variant 0 (default): tf32, k-blocks of 16, 64-byte swizzle, 4 stages;
 // variant 1: tf32, k-blocks of 32, 128-byte swizzle, 2 stages; variant 2: fp16 operands
 // (hi/lo planes of __half), k-blocks of 32, 64-byte swizzle, 4 stages, 128-k promotion
-// chunks (kps % 8 == 0); variant 3: as 2 with 64-k chunks; variant 4: as 2 with 256-k chunks.
+// chunks (kps % 8 == 0); variant 3: as 2 with 64-k chunks; variant 4: as 2 with 256-k chunks;
+// variant 5: as 2 in clusters of two CTAs sharing (multicasting) the B tile.
 cudaError_t launch_gemm_tf32x3_v(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int64_t Kp,
                                  int64_t kps, int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha,
                                  float beta, int* status, cudaStream_t st, int variant) {
   using namespace tc;
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (Kp <= 0 || P <= 0 || M > 0x7fffffff || N > 0x7fffffff || Kp * P > 0x7fffffff) return cudaErrorInvalidValue;
-  const bool f16 = variant >= 2 && variant <= 4;
+  const bool f16 = variant >= 2 && variant <= 5;
   if ((kps & (f16 ? 7 : 3)) || kps < Kp) return cudaErrorInvalidValue;
   if ((((uintptr_t)Ahi) | ((uintptr_t)Alo) | ((uintptr_t)Bhi) | ((uintptr_t)Blo)) & 15) return cudaErrorInvalidValue;
+  if (variant == 5)
+    return launch_variant<CfgF16, 2>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
   if (variant == 4)
-    return launch_variant<CfgF16L>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
+    return launch_variant<CfgF16L, 1>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
   if (variant == 3)
-    return launch_variant<CfgF16S>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
+    return launch_variant<CfgF16S, 1>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
   if (variant == 2)
-    return launch_variant<CfgF16>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
+    return launch_variant<CfgF16, 1>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
   if (variant == 1)
-    return launch_variant<CfgTF32W>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
-  return launch_variant<CfgTF32>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
+    return launch_variant<CfgTF32W, 1>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
+  return launch_variant<CfgTF32, 1>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
 }
 
 // Sets the kernels' shared-memory attributes and caches the SM count ahead of time, so no
@@ -496,16 +594,17 @@ void gemm_prepare() {
   if (done) return;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return;
-  cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgTF32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)CfgTF32::SMEM_BYTES);
-  cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgTF32W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgTF32W, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)CfgTF32W::SMEM_BYTES);
-  cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgF16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)CfgF16::SMEM_BYTES);
-  cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgF16S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgF16S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)CfgF16S::SMEM_BYTES);
-  cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgF16L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgF16L, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)CfgF16L::SMEM_BYTES);
+  cluster_grid<CfgF16>();   // sets the cluster kernel's attribute and caches its grid
   done = true;
 }
 

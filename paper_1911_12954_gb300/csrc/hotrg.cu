@@ -644,6 +644,10 @@ hotrg_status gemm(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R*
   return HOTRG_OK;
 }
 
+// FP16X3 pipelines by option value: 0 = two-CTA clusters sharing the B tile, 128-k promotion
+// chunks; 1 = one CTA, 64-k chunks; 2 = one CTA, 256-k chunks; 3 = one CTA, 128-k chunks.
+constexpr int kF16Variant[4] = {5, 3, 4, 2};
+
 template <typename R>
 hotrg_status gemm_launch(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R* Blo, const StepPlan& p, R* C,
                          int64_t M, int64_t N, double alpha, double beta, cudaStream_t st) {
@@ -655,8 +659,7 @@ hotrg_status gemm_launch(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, c
     // operands carry the factor 2^14 each
     const float unscale = 1.0f / (kF16Scale * kF16Scale);
     CK(launch_gemm_tf32x3_v(A, Alo, B, Blo, p.Kp, p.kps, p.P, (float*)C, N, M, N, (float)alpha * unscale,
-                            (float)beta, (int*)(ctx->ws + ctx->L.status), st,
-                            ctx->gemm_variant == 1 ? 3 : (ctx->gemm_variant == 2 ? 4 : 2)),
+                            (float)beta, (int*)(ctx->ws + ctx->L.status), st, kF16Variant[ctx->gemm_variant]),
        "gemm f16x3");
   } else {
     if (p.P != 1) return HOTRG_EUNSUPPORTED;
@@ -1322,7 +1325,7 @@ hotrg_status hotrg_set_option(hotrg_ctx* ctx, int option, int value) {
       ctx->drop_graphs();
       return HOTRG_OK;
     case HOTRG_OPT_GEMM_VARIANT:
-      if (value < 0 || value > (ctx->prec == HOTRG_FP16X3 ? 2 : 1)) return HOTRG_EINVAL;
+      if (value < 0 || value > (ctx->prec == HOTRG_FP16X3 ? 3 : 1)) return HOTRG_EINVAL;
       ctx->gemm_variant = value;
       ctx->drop_graphs();
       return HOTRG_OK;

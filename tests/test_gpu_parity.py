@@ -429,21 +429,26 @@ def test_nonfinite_input_is_rejected_on_the_host():
         g.set_tensor(T)
 
 
-@pytest.mark.parametrize("precision", ["tf32x3", "fp16x3"])
-def test_gemm_pipeline_variants_agree(precision):
-    """Both tensor-core pipelines of a mode give the same step: for tf32x3 4 x 16-wide
-    and 2 x 32-wide k-blocks, for fp16x3 partial sums promoted every 128 k and every 64 k."""
+@pytest.mark.parametrize("precision,variants", [("tf32x3", (0, 1)), ("fp16x3", (0, 1, 2, 3))])
+def test_gemm_pipeline_variants_agree(precision, variants):
+    """The tensor-core pipelines of a mode give the same step: for tf32x3 4 x 16-wide and
+    2 x 32-wide k-blocks; for fp16x3 two-CTA clusters sharing the B tile and single CTAs
+    promoting every 64, 256 and 128 k. The cluster pipeline and the single-CTA one with the
+    same chunk issue the same MMAs in the same order: bit-identical."""
     from paper_1911_12954_gb300 import OPT_GEMM_VARIANT
     dims, mu, dcut = (3, 3, 2, 3), 2, 6
     T = random_tensor(12, dims)
     out = []
-    for v in (0, 1):
+    for v in variants:
         g = _gpu(batch=1, dcut_max=9, precision=precision, schedule=[(mu, dcut)], dims0=dims)
         g.set_option(OPT_GEMM_VARIANT, v)
         g.set_tensor(T)
         g.step(mu, dcut)
         out.append(g.tensor())
-    assert np.allclose(out[0], out[1], atol=1e-6 * np.abs(out[0]).max())
+    for o in out[1:]:
+        assert np.allclose(out[0], o, atol=1e-6 * np.abs(out[0]).max())
+    if precision == "fp16x3":
+        assert np.array_equal(out[0], out[3])
 
 
 def test_x_indicator_matches_oracle_fp64():
