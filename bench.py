@@ -75,8 +75,9 @@ def parse_args():
 # DRAM bytes (read + write) per launch of the block-spin GEMM, taken from one ncu capture of
 # the same workload with the kernel as built now (profiles/gemm_fp16x3_d6_full.md:
 # dram__bytes_read.sum + dram__bytes_write.sum of the step-4 launch), keyed by (precision,
-# D_cut, temperatures, impure). Workloads without a capture report null.
-GEMM_TRAFFIC = {("fp16x3", 8, 1, False): 270.60e9 + 4.38e9}
+# GEMM option, D_cut, temperatures, impure). Workloads without a capture report null.
+GEMM_TRAFFIC = {("fp16x3", 0, 8, 1, False): 134.62e9 + 4.51e9,   # two-CTA clusters (default)
+                ("fp16x3", 3, 8, 1, False): 270.60e9 + 4.38e9}   # one CTA per tile
 
 
 # --------------------------------------------------------------------------- helpers
@@ -490,7 +491,7 @@ def main():
     peak, peak_src = tensor_peak(args.precision, True)
     peak_burst, _ = tensor_peak(args.precision, False)
     achieved = prof["gemm_flops"] / (prof["gemm_ms"] * 1e-3) / 1e12 if prof["gemm_ms"] > 0 else None
-    traffic = GEMM_TRAFFIC.get((args.precision, D, args.batch, bool(impure)))
+    traffic = GEMM_TRAFFIC.get((args.precision, args.gemm_variant, D, args.batch, bool(impure)))
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -507,8 +508,10 @@ def main():
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "algorithmic_bytes": (2 * (4 if args.precision == "fp16x3" else 8) + 4) * float(D) ** 10,
-                     "kernel": f"gemm_tf32x3_kernel<{'CfgF16' if args.precision == 'fp16x3' else 'CfgTF32'}> "
-                               "(block-spin contraction, 2 M N K algorithmic flops per launch)",
+                     "kernel": ("gemm_tf32x3_kernel<CfgF16, 2> (two-CTA clusters sharing B)"
+                                if args.precision == "fp16x3" and args.gemm_variant == 0 else
+                                f"gemm_tf32x3_kernel<{'CfgF16' if args.precision == 'fp16x3' else 'CfgTF32'}, 1>")
+                               + " (block-spin contraction, 2 M N K algorithmic flops per launch)",
                      "peak_source": peak_src, "launches": prof["gemm_launches"],
                      "avg_launch_ms": prof["gemm_ms"] / max(1, prof["gemm_launches"]),
                      "tensor_pipe_flops_frac": (3 * achieved / peak) if achieved else None,
