@@ -518,14 +518,16 @@ def test_observable_scan_matches_oracle():
                 assert r["lnZ"][b] == pytest.approx(st.lnZ(), rel=1e-12)
 
 
-def test_cuda_graph_steps_match_eager_steps():
+@pytest.mark.parametrize("precision", ["tf32x3", "fp16x3"])
+def test_cuda_graph_steps_match_eager_steps(precision):
     """Captured-and-replayed steps (one graph launch per step, every batch element and
-    impure tensor inside) give bit-identical results to eager launches: 16 steps, so the
-    four steady-state graphs are each replayed several times."""
+    impure tensor inside; for fp16x3 the GEMM is a two-CTA cluster launch) give bit-identical
+    results to eager launches: 16 steps, so the four steady-state graphs are each replayed
+    several times."""
     sched = [(i % 4, 4) for i in range(16)]
     out = []
     for graphs in (False, True):
-        g = _gpu(batch=2, dcut_max=4, precision="tf32x3", impure=3, schedule=sched, graphs=graphs)
+        g = _gpu(batch=2, dcut_max=4, precision=precision, impure=3, schedule=sched, graphs=graphs)
         g.init_tensor([1 / 6.65, 1 / 6.70], 1e-5)
         rows = []
         for mu, dc in sched:
