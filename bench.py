@@ -234,6 +234,20 @@ def oracle_sample(dcut: int, seed: int = 8, nx: int = 1):
     return gram + main + builds + close, dt
 
 
+def workload_config(args, world):
+    """The workload part of a bench line's config, identical for the GPU and reference arms."""
+    D = args.dcut
+    nsteps = args.warmup + args.steps
+    hfield = 1e-5 if args.impure else H_WORK
+    workload = ((f"4D Ising HOTRG, T={T_WORK}, h={H_WORK}" if args.batch == 1 else
+                 f"4D Ising HOTRG, {args.batch * world} temperatures in [6.60, 6.72], h={hfield}")
+                + (", pure + sigma + sigma-sigma impure tensors" if args.impure else "")
+                + f", D_cut={D}, 1024^4 lattice schedule (x,y,z,t cycled); timed steps "
+                f"{args.warmup + 1}..{nsteps} (steady state)")
+    return {"workload": workload, "dcut": D, "temperatures_per_gpu": args.batch, "impure": bool(args.impure),
+            "lattice": "1024^4"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -252,8 +266,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"4D Ising HOTRG step, D_cut={args.dcut}, steady state (1024^4 schedule)",
-                       "dcut": args.dcut, "sample": "bounded oracle sample, see cpu_baseline"},
+            "config": workload_config(args, world),
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -496,12 +509,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": (f"4D Ising HOTRG, T={T_WORK}, h={H_WORK}" if args.batch == 1 else
-                                f"4D Ising HOTRG, {args.batch * world} temperatures in [6.60, 6.72], h={hfield}")
-                               + (", pure + sigma + sigma-sigma impure tensors" if impure else "")
-                               + f", D_cut={D}, 1024^4 lattice schedule (x,y,z,t cycled); timed steps "
-                               f"{args.warmup + 1}..{nsteps} (steady state)",
-                   "dcut": D, "temperatures_per_gpu": args.batch, "impure": bool(impure), "lattice": "1024^4",
+        "config": {**workload_config(args, world),
                    "precision": f"{args.precision} (fp32 storage)", "cuda_graphs": bool(args.graphs), "gemm_variant": args.gemm_variant,
                    "l2": f"operands larger than L2 (GEMM A and B: 2 x "
                          f"{(4 if args.precision == 'fp16x3' else 8) * D ** 10 / 1e9:.1f} GB per step, hi + lo)"},
