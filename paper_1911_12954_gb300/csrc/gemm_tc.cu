@@ -573,8 +573,13 @@ cudaError_t launch_gemm_tf32x3_v(const void* Ahi, const void* Alo, const void* B
   const bool f16 = variant >= 2 && variant <= 5;
   if ((kps & (f16 ? 7 : 3)) || kps < Kp) return cudaErrorInvalidValue;
   if ((((uintptr_t)Ahi) | ((uintptr_t)Alo) | ((uintptr_t)Bhi) | ((uintptr_t)Blo)) & 15) return cudaErrorInvalidValue;
-  if (variant == 5)
-    return launch_variant<CfgF16, 2>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
+  if (variant == 5) {
+    // a device (or partition) that cannot co-schedule two-CTA clusters runs the same sums on
+    // single CTAs
+    if (cluster_grid<CfgF16>() >= 2)
+      return launch_variant<CfgF16, 2>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
+    return launch_variant<CfgF16, 1>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
+  }
   if (variant == 4)
     return launch_variant<CfgF16L, 1>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
   if (variant == 3)
