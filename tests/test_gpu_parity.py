@@ -347,6 +347,31 @@ def test_long_closing_contraction(prec, tol):
     assert g.step_info(1)["ln_c"] == pytest.approx(ref.history[0].ln_c, abs=max(tol, 1e-10))
 
 
+@pytest.mark.parametrize("dims", [(11, 2, 2, 2), (16, 2, 2, 2)])
+def test_large_gram_matrices_fp64(dims):
+    """Transverse bond dimension 11 and 16: Gram matrices of side 121 and 256 (the largest the
+    library takes), beyond what the eigensolver keeps in shared memory, so A and V live in
+    its global workspace. One truncating step (D_cut = 6) in FP64 against the oracle: the
+    tensor, the isometries, the discarded sums and the sides taken."""
+    mu, dcut = 1, 6
+    T = decaying_tensor(123, dims, 0.7)
+    ref = H.HOTRG.from_tensor(T)
+    trans = [n for n in range(4) if n != mu]
+    isos = {n: H.isometry(ref.T, ref.T, mu, n, dcut) for n in trans}
+    ref.step(mu, dcut)
+    g = _gpu(batch=1, dcut_max=16, precision="fp64", schedule=[(mu, dcut)], dims0=dims)
+    g.set_tensor(T)
+    g.step(mu, dcut)
+    Tg = g.tensor()
+    assert np.allclose(Tg, ref.T, rtol=0, atol=1e-12 * np.abs(ref.T).max())
+    info = g.step_info(1)
+    for n in trans:
+        Ug = g.isometry(n, dold=dims[n], chi=isos[n].chi)
+        assert np.allclose(Ug, isos[n].U, atol=1e-11), n
+        assert info["primed"][n] == int(isos[n].primed)
+        assert info["eps"][n] == pytest.approx(isos[n].eps, rel=1e-9, abs=1e-13)
+
+
 # ------------------------------------------------------------------ impure tensors in mixed precision
 @pytest.mark.parametrize("prec", ["tf32x3", "fp16x3"])
 def test_mixed_impure_run_vs_golden(prec):
