@@ -175,9 +175,13 @@ __global__ void __launch_bounds__(kJT) jacobi_kernel(const __grid_constant__ Eig
         if (q >= 0) {
           const double apq = A[p * n + q], app = A[p * n + p], aqq = A[q * n + q];
           if (fabs(apq) > fmax(tol_abs, tol_rel * sqrt(fabs(app * aqq)))) {
+            // tan of the rotation angle, the smaller root of t^2 + 2 tau t - 1 = 0; one
+            // division, one square root and one reciprocal square root on the round's
+            // critical path (tau^2 would overflow beyond 1e154: t -> 1 / (2 tau) there)
             const double tau = (aqq - app) / (2.0 * apq);
-            const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
-            cr = 1.0 / sqrt(1.0 + t * t);
+            const double at = fabs(tau);
+            const double t = at > 1e150 ? 0.5 / tau : (tau >= 0 ? 1.0 : -1.0) / (at + sqrt(fma(tau, tau, 1.0)));
+            cr = rsqrt(fma(t, t, 1.0));
             sr = t * cr;
             rotated = 1;
           }
