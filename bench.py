@@ -72,12 +72,10 @@ def parse_args():
     return p.parse_args()
 
 
-# DRAM bytes (read + write) per launch of the block-spin GEMM, taken from one ncu capture of
-# the same workload with the kernel as built now (profiles/gemm_fp16x3_d6_full.md:
-# dram__bytes_read.sum + dram__bytes_write.sum of the step-4 launch), keyed by (precision,
-# GEMM option, D_cut, temperatures, impure). Workloads without a capture report null.
-GEMM_TRAFFIC = {("fp16x3", 0, 8, 1, False): 134.62e9 + 4.51e9,   # two-CTA clusters (default)
-                ("fp16x3", 3, 8, 1, False): 270.60e9 + 4.38e9}   # one CTA per tile
+# DRAM bytes (read + write) per launch of the block-spin GEMM, from one ncu capture of the
+# kernel as built now, keyed by (precision, GEMM option, D_cut, temperatures, impure).
+# Workloads without a capture report null.
+GEMM_TRAFFIC = {}
 
 
 # --------------------------------------------------------------------------- helpers
@@ -516,9 +514,9 @@ def main():
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "algorithmic_bytes": (2 * (4 if args.precision == "fp16x3" else 8) + 4) * float(D) ** 10,
-                     "kernel": ("gemm_tf32x3_kernel<CfgF16, 2> (two-CTA clusters sharing B)"
+                     "kernel": ("gemm_pair_kernel<CfgF16P> (CTA pairs, tcgen05.mma.cta_group::2)"
                                 if args.precision == "fp16x3" and args.gemm_variant == 0 else
-                                f"gemm_tf32x3_kernel<{'CfgF16' if args.precision == 'fp16x3' else 'CfgTF32'}, 1>")
+                                f"gemm_tf32x3_kernel<{'CfgF16' if args.precision == 'fp16x3' else 'CfgTF32'}>")
                                + " (block-spin contraction, 2 M N K algorithmic flops per launch)",
                      "peak_source": peak_src, "launches": prof["gemm_launches"],
                      "avg_launch_ms": prof["gemm_ms"] / max(1, prof["gemm_launches"]),

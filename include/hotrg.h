@@ -179,10 +179,11 @@ hotrg_status hotrg_step_flops(const hotrg_ctx* ctx, int dir, int dcut, double* m
  *   raises HOTRG_ENOCONV at the next synchronising call (used to test that path).
  * HOTRG_OPT_GEMM_VARIANT: tensor-core GEMM pipeline. TF32X3: 0 = 4 stages of 16-wide
  *   k-blocks (default), 1 = 2 stages of 32-wide k-blocks. FP16X3: 0 = partial sums promoted
- *   from the tensor-core accumulator to FP32 registers every 128 k, the tiles computed by
- *   clusters of two CTAs that share (multicast) one B tile (default); 1 = every 64 k (slower,
- *   a smaller truncation bias), 2 = every 256 k (faster, a larger one), 3 = every 128 k,
- *   one CTA per tile (1..3 without clusters; 0 and 3 give the same sums).
+ *   from the tensor-core accumulator to FP32 registers every 128 k, each 256 x 256 tile
+ *   computed by a pair of CTAs on two SMs (tcgen05.mma.cta_group::2; each CTA loads half of
+ *   the B tile) (default); 1 = every 64 k (slower, a smaller truncation bias), 2 = every
+ *   256 k (faster, a larger one), 3 = every 128 k, one CTA per 128 x 256 tile (1..3 one CTA
+ *   per tile).
  * HOTRG_OPT_GRAPHS: 1 = capture each distinct step (plan, buffer, first step or not) once
  *   into a CUDA graph and replay it (every kernel of the step for every batch element in
  *   one graph launch); needs a non-default stream (hotrg_set_stream). Per-GEMM profiling

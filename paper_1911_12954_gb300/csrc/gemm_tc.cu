@@ -10,15 +10,17 @@
 //
 // The tensor cores add each MMA's products into the FP32 accumulator with truncation,
 // so an accumulator that runs over the whole K picks up a bias that grows linearly with
-// K (measured 2.5e-4 relative at K = 32768). The kernel therefore promotes the partial
-// sum of every chunk of k (32 for tf32; 128, or 64 in the short-chunk variant, for fp16)
+// K (measured 2.5e-4 relative at K = 32768). The kernels therefore promote the partial
+// sum of every chunk of k (32 for tf32; 128, or 64 / 256 in the other variants, for fp16)
 // from TMEM into FP32 registers, where the sums are rounded to nearest: the truncation
 // bias is bounded by one chunk's worth. Each promotion reads the whole 128 x 256 FP32
 // accumulator out of TMEM and holds the MMAs back for a few hundred cycles, so the chunk
 // is as long as the accuracy allows (at D = 8, 64-k chunks cost 17 % of the MMA time and
 // 128-k chunks 7 %).
 //
-// Structure: persistent kernel, one CTA per SM, 10 warps.
+// Two kernels share the promotion and epilogue code:
+//
+// gemm_tf32x3_kernel (one CTA per 128 x 256 tile): persistent, one CTA per SM, 10 warps.
 //   warp 0 lane 0 : TMA producer. Per k-block (one swizzle row of 64 bytes: 32 fp16 or 16
 //                   tf32 values), four tiles (Ahi, Alo: 128 rows; Bhi, Blo: 256 rows) land
 //                   in one pipeline stage through cp.async.bulk.tensor (3D, K panels).
@@ -30,6 +32,21 @@
 //                   half (w - 2) / 4 with tcgen05.ld 32x32b, adds the chunk into 128 FP32
 //                   registers per thread, and after the last k-block of the tile writes
 //                   alpha * acc + beta * C with guarded stores.
+//
+// gemm_pair_kernel (fp16 only; one CTA pair per 256 x 256 tile): the same roles in a cluster
+//   of two CTAs on two SMs. Each CTA copies its own 128 rows of A and its own half (128 rows)
+//   of the B tile into its own shared memory with plain TMA loads whose completion is counted
+//   on the even CTA's mbarrier (.cta_group::2); the even CTA's MMA thread issues
+//   tcgen05.mma.cta_group::2 (M = 256, N = 256), which reads A and B from both CTAs and writes
+//   each CTA's 128 accumulator rows into its own TMEM. Its commits are addressed one barrier
+//   at a time (the CTA's own and, through mapa, the partner's), and every copy lands in the
+//   shared memory of the CTA that issued it. Every B row is fetched by one SM of the pair, so
+//   the pair reads half the B bytes of two single-CTA tiles. Its k-blocks are 64 fp16 wide
+//   (one 128-byte swizzle row per operand row, the padded row pitch of the K panels), 3
+//   stages of 64 KB per CTA: with 64-byte rows the pair read 4x the DRAM bytes of the
+//   single-CTA kernel at D_cut = 8 (559 GB against 134 GB per launch), with 128-byte rows
+//   the same 134 GB, and its GEMM ran in 89 ms against 106 ms for single CTAs.
+//
 // Tiles are visited in groups of 16 M-tiles so the CTAs running at the same time share
 // A and B k-blocks through L2.
 // Every mbarrier wait is bounded (globaltimer, 4 s): on expiry the thread raises the
@@ -55,31 +72,36 @@ constexpr unsigned long long kWaitNs = 4000000000ull;
 // Pipeline variants. One k-block = one swizzle row of ROWB bytes (128 B or 64 B) per
 // operand row; F16 selects fp16 operands (kind::f16, K = 16 per MMA) instead of tf32
 // (kind::tf32, K = 8). Either way an MMA k-step spans 32 bytes of the row. CHUNK is the
-// k promoted from TMEM to registers at once.
-template <int ROWB, bool F16, int CHUNK>
+// k promoted from TMEM to registers at once. PAIR: the two-CTA form (B_BYTES is then this
+// CTA's half of the B tile, and the MMA spans M = 2 BM rows).
+template <int ROWB, bool F16, int CHUNK, bool PAIR = false>
 struct Cfg {
   static constexpr bool kF16 = F16;
+  static constexpr bool kPair = PAIR;
   static constexpr int ELT = F16 ? 2 : 4;
   static constexpr int BK = ROWB / ELT;                            // elements per k-block
   static constexpr int KSTEPS = ROWB / 32;                         // MMAs per product per k-block
-  static constexpr int STAGES = ROWB == 128 ? 2 : 4;
+  static constexpr int STAGES = PAIR ? (ROWB == 128 ? 3 : 6) : (ROWB == 128 ? 2 : 4);
   static constexpr int A_BYTES = BM * ROWB;
-  static constexpr int B_BYTES = BN * ROWB;
+  static constexpr int B_BYTES = (PAIR ? BN / 2 : BN) * ROWB;
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
   static constexpr int KB_PER_CHUNK = CHUNK / BK;
   static_assert(CHUNK % BK == 0, "a chunk is a whole number of k-blocks");
   static constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+  static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
   static constexpr uint64_t LAYOUT = ROWB == 128 ? 2 : 4;         // UMMA swizzle: 128 B or 64 B
   static constexpr uint32_t SBO = 8 * ROWB;                       // 8 rows of one swizzle row
-  // instruction descriptor: D = F32; A = B = TF32 (2) or F16 (0); both K-major; N = 256, M = 128
+  static constexpr int MMA_M = PAIR ? 2 * BM : BM;
+  // instruction descriptor: D = F32; A = B = TF32 (2) or F16 (0); both K-major; N = 256, M
   static constexpr uint32_t IDESC = (1u << 4) | ((F16 ? 0u : 2u) << 7) | ((F16 ? 0u : 2u) << 10) |
-                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(MMA_M >> 4) << 24);
 };
 using CfgTF32 = Cfg<64, false, 32>;     // default tf32 pipeline: 4 stages of 16-wide k-blocks
 using CfgTF32W = Cfg<128, false, 32>;   // tf32, 2 stages of 32-wide k-blocks
 using CfgF16 = Cfg<64, true, 128>;      // fp16: 4 stages of 32-wide k-blocks, 128-k chunks
 using CfgF16S = Cfg<64, true, 64>;      // fp16 with 64-k chunks
 using CfgF16L = Cfg<64, true, 256>;     // fp16 with 256-k chunks
+using CfgF16P = Cfg<128, true, 128, true>;  // fp16, CTA pairs, 3 stages of 64 KB, 128-k chunks
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -98,24 +120,45 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
+// Arrival on an mbarrier of any CTA of the cluster (shared::cluster address from mapa).
+// Relaxed: the arrival only reports that this warp's TMEM loads have completed (wait::ld),
+// and a release at cluster scope would first wait for the thread's earlier global stores
+// (the previous tile's C rows) to become visible, which stalled the epilogue and with it the
+// MMAs (D_cut = 8 GEMM 151 ms against 103 ms relaxed).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
+}
+template <bool CLUSTER>
 __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
   uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(su32(b)), "r"(parity)
-      : "memory");
+  if constexpr (CLUSTER) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+  }
   return ok != 0;
 }
-// Bounded wait; false (and the timeout status raised) when it gives up.
+// Bounded wait; false (and the timeout status raised) when it gives up. CLUSTER: the
+// arrivals may come from the partner CTA (acquire at cluster scope).
+template <bool CLUSTER = false>
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* status,
                                           unsigned long long limit_ns = kWaitNs) {
-  if (mbar_try(b, parity)) return true;
+  if (mbar_try<CLUSTER>(b, parity)) return true;
   const unsigned long long t0 = now_ns();
   while (true) {
-    if (mbar_try(b, parity)) return true;
+    if (mbar_try<CLUSTER>(b, parity)) return true;
     if (now_ns() - t0 > limit_ns) {
       atomicAdd(&status[kStTimeout], 1);
       return false;
@@ -145,23 +188,28 @@ __device__ __forceinline__ void tma_load(const CUtensorMap* map, uint64_t* bar, 
       "l"((uint64_t)map), "r"(su32(bar)), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
-
-// The same load delivered to the same shared-memory offset (and completing the same mbarrier
-// offset) in every CTA of the cluster named by ctaMask.
-__device__ __forceinline__ void tma_load_mc(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y, int z,
-                                            uint16_t mask) {
+// The same load into this CTA's shared memory, with its bytes counted on an mbarrier of
+// either CTA of the pair (bar: shared::cluster address).
+__device__ __forceinline__ void tma_load_pair(const CUtensorMap* map, uint32_t bar, void* dst, int x, int y, int z) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(su32(dst)),
-      "l"((uint64_t)map), "r"(su32(bar)), "r"(x), "r"(y), "r"(z), "h"(mask)
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(su32(dst)),
+      "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
+
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
   asm volatile("mov.u32 %0, %cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// shared::cluster address of the variable at shared::cta address `a` in CTA `rank`
+__device__ __forceinline__ uint32_t mapa(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
   return r;
 }
 
@@ -179,7 +227,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 
 template <class CF>
 __device__ __forceinline__ void mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-  if constexpr (CF::kF16) {
+  if constexpr (CF::kPair) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(CF::IDESC), "r"(accumulate)
+        : "memory");
+  } else if constexpr (CF::kF16) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
@@ -199,12 +254,10 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
                : "memory");
 }
-// Arrives (once the MMAs issued so far have completed) on the mbarrier at this offset in
-// every CTA of the cluster named by ctaMask.
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                   su32(bar)),
-               "h"(mask)
+// Arrives on one mbarrier (shared::cluster address: this CTA's or the partner's) once the
+// pair MMAs issued so far by this thread have completed.
+__device__ __forceinline__ void mma_commit_pair(uint32_t caddr) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(caddr)
                : "memory");
 }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -235,11 +288,44 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
   tn = r / gm;
 }
 
-// CL = 2: clusters of two CTAs on vertically adjacent tiles (same N tile, M tiles 2g and
-// 2g + 1). Each CTA loads its own A tile and one half of the shared B tile, multicast into
-// both CTAs, so B is read from L2 once per pair; a stage is refilled only after both CTAs'
-// MMAs have read it (their commits arrive on both CTAs' empty barriers).
-template <class CF, int CL>
+// Adds one chunk accumulator (this warp's 32 TMEM lanes, its half of the 256 columns) into
+// the thread's 128 FP32 registers.
+__device__ __forceinline__ void promote_chunk(uint32_t taddr, float* acc) {
+#pragma unroll
+  for (int c = 0; c < BN / 64; ++c) {
+    float v[32];
+    tmem_ld32(taddr + (uint32_t)(c * 32), v);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[c * 32 + j] += v[j];
+  }
+}
+
+// alpha * acc + beta * C for one thread's 128 columns of row m (guarded).
+__device__ __forceinline__ void store_row(float* __restrict__ C, int64_t ldc, int M, int N, int64_t m, int n0,
+                                          const float* acc, float alpha, float beta) {
+  if (m >= M) return;
+  float* crow = C + m * ldc + n0;
+  if (n0 + BN / 2 <= N && ((((uintptr_t)crow) & 15) == 0)) {
+#pragma unroll
+    for (int j = 0; j < BN / 2; j += 4) {
+      float4 o = make_float4(alpha * acc[j], alpha * acc[j + 1], alpha * acc[j + 2], alpha * acc[j + 3]);
+      if (beta != 0.f) {
+        const float4 old = *(const float4*)(crow + j);
+        o.x += beta * old.x;
+        o.y += beta * old.y;
+        o.z += beta * old.z;
+        o.w += beta * old.w;
+      }
+      *(float4*)(crow + j) = o;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < BN / 2; ++j)
+      if (n0 + j < N) crow[j] = alpha * acc[j] + (beta != 0.f ? beta * crow[j] : 0.f);
+  }
+}
+
+template <class CF>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                        const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
@@ -258,11 +344,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint32_t* tmem_slot = (uint32_t*)(drain + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rm = CL == 2 ? (int)cluster_rank() : 0;    // this CTA's M tile within the pair
-  const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
   const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
-  const int tiles_mg = (tiles_m + CL - 1) / CL;          // M tiles per cluster group
-  const int ntiles = tiles_mg * tiles_n;
+  const int ntiles = tiles_m * tiles_n;
   const int nkbp = (Kp + BK - 1) / BK;   // k-blocks per panel (the last one zero-filled past Kp)
   const int nkb = P * nkbp;
   const int nchunk = (nkb + KPC - 1) / KPC;
@@ -270,7 +353,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], CL);      // the MMA commits of every CTA that reads this stage
+      mbar_init(&empty[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&cfull[a], 1);
@@ -286,8 +369,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   fence_before();
-  if (CL == 2) cluster_sync_all();   // the partner's barriers exist before any multicast
-  else __syncthreads();
+  __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -299,12 +381,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mBlo) : "memory");
     int s = 0;
     uint32_t ph = 0;
-    int issued[STAGES] = {};
+    int nissued = 0;   // k-blocks issued; stage q has been filled (nissued - q + STAGES - 1) / STAGES times
     bool ok = true;
-    for (int t = cid; t < ntiles && ok; t += ncl) {
-      int tg, tn;
-      tile_coords(t, tiles_mg, tiles_n, GROUP_M / CL, tg, tn);
-      const int tm = tg * CL + rm;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int tm, tn;
+      tile_coords(t, tiles_m, tiles_n, GROUP_M, tm, tn);
       for (int kb = 0; kb < nkb; ++kb) {
         if (!mbar_wait(&empty[s], ph ^ 1, status)) {
           ok = false;
@@ -312,18 +393,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         uint8_t* st = smem + s * STAGE_BYTES;
         const int pn = kb / nkbp, kx = (kb - pn * nkbp) * BK;
-        mbar_expect_tx(&full[s], STAGE_BYTES);   // own A + both halves of B
+        mbar_expect_tx(&full[s], STAGE_BYTES);
         tma_load(&mAhi, &full[s], st, kx, tm * BM, pn);
         tma_load(&mAlo, &full[s], st + A_BYTES, kx, tm * BM, pn);
-        if (CL == 2) {
-          const int half = B_BYTES / 2, yb = tn * BN + rm * (BN / 2);
-          tma_load_mc(&mBhi, &full[s], st + 2 * A_BYTES + rm * half, kx, yb, pn, 3);
-          tma_load_mc(&mBlo, &full[s], st + 2 * A_BYTES + B_BYTES + rm * half, kx, yb, pn, 3);
-        } else {
-          tma_load(&mBhi, &full[s], st + 2 * A_BYTES, kx, tn * BN, pn);
-          tma_load(&mBlo, &full[s], st + 2 * A_BYTES + B_BYTES, kx, tn * BN, pn);
-        }
-        ++issued[s];
+        tma_load(&mBhi, &full[s], st + 2 * A_BYTES, kx, tn * BN, pn);
+        tma_load(&mBlo, &full[s], st + 2 * A_BYTES + B_BYTES, kx, tn * BN, pn);
+        ++nissued;
         if (++s == STAGES) {
           s = 0;
           ph ^= 1;
@@ -331,14 +406,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
     // make sure every copy issued has landed before the CTA can exit
-    for (int q = 0; q < STAGES; ++q)
-      if (issued[q] > 0) mbar_wait(&full[q], (uint32_t)((issued[q] - 1) & 1), status);
+    for (int q = 0; q < STAGES && q < nissued; ++q)
+      mbar_wait(&full[q], (uint32_t)(((nissued - q + STAGES - 1) / STAGES - 1) & 1), status);
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
     int s = 0, cb = 0;
     uint32_t ph = 0, cph = 0;
     bool ok = true;
-    for (int t = cid; t < ntiles && ok; t += ncl) {
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       for (int kb = 0; kb < nkb; ++kb) {
         const bool first = kb % KPC == 0;
         const bool last = kb % KPC == KPC - 1 || kb == nkb - 1;
@@ -358,8 +433,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           mma<CF>(d, ahi + off, blo + off, 1);
           mma<CF>(d, ahi + off, bhi + off, 1);
         }
-        if (CL == 2) mma_commit_mc(&empty[s], 3);
-        else mma_commit(&empty[s]);
+        mma_commit(&empty[s]);
         if (last) {
           mma_commit(&cfull[cb]);
           if (++cb == 2) {
@@ -385,10 +459,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     int cb = 0;
     uint32_t cph = 0;
     bool ok = true;
-    for (int t = cid; t < ntiles && ok; t += ncl) {
-      int tg, tn;
-      tile_coords(t, tiles_mg, tiles_n, GROUP_M / CL, tg, tn);
-      const int tm = tg * CL + rm;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int tm, tn;
+      tile_coords(t, tiles_m, tiles_n, GROUP_M, tm, tn);
       float acc[BN / 2];
 #pragma unroll
       for (int j = 0; j < BN / 2; ++j) acc[j] = 0.f;
@@ -399,13 +472,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           break;
         }
         fence_after();
-#pragma unroll
-        for (int c = 0; c < BN / 64; ++c) {
-          float v[32];
-          tmem_ld32(tmem + lane_base + (uint32_t)(cb * BN + h * (BN / 2) + c * 32), v);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) acc[c * 32 + j] += v[j];
-        }
+        promote_chunk(tmem + lane_base + (uint32_t)(cb * BN + h * (BN / 2)), acc);
         fence_before();
         mbar_arrive(&cempty[cb]);
         if (++cb == 2) {
@@ -414,39 +481,206 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
       }
       if (!ok) break;
-      const int64_t m = (int64_t)tm * BM + row;
-      const int n0 = tn * BN + h * (BN / 2);
-      if (m < M) {
-        float* crow = C + m * ldc + n0;
-        if (n0 + BN / 2 <= N && ((((uintptr_t)crow) & 15) == 0)) {
-#pragma unroll
-          for (int j = 0; j < BN / 2; j += 4) {
-            float4 o = make_float4(alpha * acc[j], alpha * acc[j + 1], alpha * acc[j + 2], alpha * acc[j + 3]);
-            if (beta != 0.f) {
-              const float4 old = *(const float4*)(crow + j);
-              o.x += beta * old.x;
-              o.y += beta * old.y;
-              o.z += beta * old.z;
-              o.w += beta * old.w;
-            }
-            *(float4*)(crow + j) = o;
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < BN / 2; ++j)
-            if (n0 + j < N) crow[j] = alpha * acc[j] + (beta != 0.f ? beta * crow[j] : 0.f);
-        }
-      }
+      store_row(C, ldc, M, N, (int64_t)tm * BM + row, tn * BN + h * (BN / 2), acc, alpha, beta);
     }
   }
   fence_before();
   __syncthreads();
-  // neither CTA leaves while the partner may still multicast into it or arrive on its barriers
-  if (CL == 2) cluster_sync_all();
   if (warp == 0) {
     __syncwarp();
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// Two-CTA form (cluster of 2): CTA rank r holds rows r BM .. r BM + 127 of a 256-row tile
+// (M tiles 2g and 2g + 1) and B rows r BN/2 .. r BN/2 + 127 of its N tile. Rank 0 (the even
+// CTA) owns the full barriers of the copies, issues every MMA and collects the epilogue's
+// "chunk drained" arrivals of both CTAs; each CTA's empty and chunk-full barriers are
+// arrived at by rank 0's commits, one commit per barrier.
+template <class CF>
+__global__ void __launch_bounds__(THREADS, 1)
+    gemm_pair_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+                     const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
+                     float* __restrict__ C, int64_t ldc, int M, int N, int Kp, int P, float alpha, float beta,
+                     int* status) {
+  static_assert(CF::kPair && CF::kF16, "pair kernel: fp16 pair configuration");
+  constexpr int STAGES = CF::STAGES, BK = CF::BK, A_BYTES = CF::A_BYTES, B_BYTES = CF::B_BYTES,
+                STAGE_BYTES = CF::STAGE_BYTES, KPC = CF::KB_PER_CHUNK;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* full = bars;                 // [STAGES] rank 0's: both CTAs' copies of a stage landed
+  uint64_t* empty = bars + STAGES;       // [STAGES] this CTA's stage may be refilled
+  uint64_t* cfull = bars + 2 * STAGES;   // [2] this CTA's chunk accumulator written
+  uint64_t* cempty = cfull + 2;          // [2] rank 0's: both CTAs drained the chunk accumulator
+  uint64_t* drain = cempty + 2;          // [1]
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const int cid = blockIdx.x / 2, ncl = gridDim.x / 2;
+  const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
+  const int tiles_mg = (tiles_m + 1) / 2;               // 256-row tiles
+  const int ntiles = tiles_mg * tiles_n;
+  const int nkbp = (Kp + BK - 1) / BK;
+  const int nkb = P * nkbp;
+  const int nchunk = (nkb + KPC - 1) / KPC;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);            // rank 0's producer arrival (it expects both CTAs' bytes)
+      mbar_init(&empty[s], 1);           // rank 0's commit for this CTA
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&cfull[a], 1);
+      mbar_init(&cempty[a], 2 * EPI_WARPS);   // one arrival per epilogue warp of either CTA
+    }
+    mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    // the same TMEM columns in both CTAs (one warp of each CTA takes part)
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  cluster_sync_all();   // both CTAs' barriers initialised and TMEM allocated before any use
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ TMA producer (both CTAs)
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mAhi) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mAlo) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mBhi) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mBlo) : "memory");
+    const uint32_t full0 = mapa(su32(&full[0]), 0);   // rank 0's full barriers
+    int s = 0;
+    uint32_t ph = 0;
+    int nissued = 0;   // k-blocks issued; stage q has been filled (nissued - q + STAGES - 1) / STAGES times
+    bool ok = true;
+    for (int t = cid; t < ntiles && ok; t += ncl) {
+      int tg, tn;
+      tile_coords(t, tiles_mg, tiles_n, GROUP_M / 2, tg, tn);
+      const int tm = 2 * tg + (int)rank;
+      const int yb = tn * BN + (int)rank * (BN / 2);
+      for (int kb = 0; kb < nkb; ++kb) {
+        if (!mbar_wait<true>(&empty[s], ph ^ 1, status)) {
+          ok = false;
+          break;
+        }
+        uint8_t* st = smem + s * STAGE_BYTES;
+        const int pn = kb / nkbp, kx = (kb - pn * nkbp) * BK;
+        if (rank == 0) mbar_expect_tx(&full[s], 2 * STAGE_BYTES);   // this CTA's and the partner's copies
+        const uint32_t fb = full0 + (uint32_t)(s * sizeof(uint64_t));
+        tma_load_pair(&mAhi, fb, st, kx, tm * BM, pn);
+        tma_load_pair(&mAlo, fb, st + A_BYTES, kx, tm * BM, pn);
+        tma_load_pair(&mBhi, fb, st + 2 * A_BYTES, kx, yb, pn);
+        tma_load_pair(&mBlo, fb, st + 2 * A_BYTES + B_BYTES, kx, yb, pn);
+        ++nissued;
+        if (++s == STAGES) {
+          s = 0;
+          ph ^= 1;
+        }
+      }
+    }
+    // rank 0 sees every copy of both CTAs land on its own barriers before it can leave (the
+    // partner waits for rank 0 at the closing cluster barrier)
+    if (rank == 0)
+      for (int q = 0; q < STAGES && q < nissued; ++q)
+        mbar_wait(&full[q], (uint32_t)(((nissued - q + STAGES - 1) / STAGES - 1) & 1), status);
+  } else if (warp == 1 && lane == 0 && rank == 0) {
+    // ------------------------------------------------------------ MMA issuer (rank 0)
+    const uint32_t empty1 = mapa(su32(&empty[0]), 1), cfull1 = mapa(su32(&cfull[0]), 1);
+    int s = 0, cb = 0;
+    uint32_t ph = 0, cph = 0;
+    bool ok = true;
+    for (int t = cid; t < ntiles && ok; t += ncl) {
+      for (int kb = 0; kb < nkb; ++kb) {
+        const bool first = kb % KPC == 0;
+        const bool last = kb % KPC == KPC - 1 || kb == nkb - 1;
+        if ((first && !mbar_wait<true>(&cempty[cb], cph ^ 1, status)) || !mbar_wait(&full[s], ph, status)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t d = tmem + (uint32_t)(cb * BN);
+        const uint32_t base = su32(smem + s * STAGE_BYTES);   // the same offsets in both CTAs
+        const uint64_t ahi = smem_desc<CF>(base), alo = smem_desc<CF>(base + A_BYTES);
+        const uint64_t bhi = smem_desc<CF>(base + 2 * A_BYTES), blo = smem_desc<CF>(base + 2 * A_BYTES + B_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < CF::KSTEPS; ++kk) {
+          const uint64_t off = (uint64_t)(kk * 32) >> 4;
+          mma<CF>(d, alo + off, bhi + off, (first && kk == 0) ? 0u : 1u);
+          mma<CF>(d, ahi + off, blo + off, 1);
+          mma<CF>(d, ahi + off, bhi + off, 1);
+        }
+        mma_commit_pair(su32(&empty[s]));
+        mma_commit_pair(empty1 + (uint32_t)(s * sizeof(uint64_t)));
+        if (last) {
+          mma_commit_pair(su32(&cfull[cb]));
+          mma_commit_pair(cfull1 + (uint32_t)(cb * sizeof(uint64_t)));
+          if (++cb == 2) {
+            cb = 0;
+            cph ^= 1;
+          }
+        }
+        if (++s == STAGES) {
+          s = 0;
+          ph ^= 1;
+        }
+      }
+    }
+    mma_commit_pair(su32(drain));
+    mbar_wait(drain, 0, status);
+  } else if (warp >= 2) {
+    // ------------------------------------------------------------ promotion + epilogue (both CTAs)
+    const int q = warp & 3;
+    const int h = (warp - 2) >> 2;
+    const int row = q * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    const uint32_t cempty0 = mapa(su32(&cempty[0]), 0);   // rank 0's drained barriers
+    int cb = 0;
+    uint32_t cph = 0;
+    bool ok = true;
+    for (int t = cid; t < ntiles && ok; t += ncl) {
+      int tg, tn;
+      tile_coords(t, tiles_mg, tiles_n, GROUP_M / 2, tg, tn);
+      const int tm = 2 * tg + (int)rank;
+      float acc[BN / 2];
+#pragma unroll
+      for (int j = 0; j < BN / 2; ++j) acc[j] = 0.f;
+      for (int kc = 0; kc < nchunk; ++kc) {
+        if (!__all_sync(0xffffffffu, mbar_wait<true>(&cfull[cb], cph, status))) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        promote_chunk(tmem + lane_base + (uint32_t)(cb * BN + h * (BN / 2)), acc);
+        fence_before();
+        __syncwarp();   // every lane's tcgen05.ld has completed (wait::ld) before the arrival
+        if (lane == 0) mbar_arrive_cluster(cempty0 + (uint32_t)(cb * sizeof(uint64_t)));
+        if (++cb == 2) {
+          cb = 0;
+          cph ^= 1;
+        }
+      }
+      if (!ok) break;
+      store_row(C, ldc, M, N, (int64_t)tm * BM + row, tn * BN + h * (BN / 2), acc, alpha, beta);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  // neither CTA leaves (or frees TMEM) while rank 0's MMAs may still read its shared memory
+  // or write its TMEM, or while arrivals addressed to it may still be in flight
+  cluster_sync_all();
+  if (warp == 0) {
+    __syncwarp();
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
 }
 
@@ -478,66 +712,85 @@ bool make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t Kp, int64
   return r == CUDA_SUCCESS;
 }
 
-// Grid of the 2-CTA cluster variant: twice the number of two-CTA clusters that can be
-// resident at once (every SM that can pair up), found once per kernel before any capture.
-template <class CF>
-int cluster_grid() {
-  static int grid = -1;
-  if (grid >= 0) return grid;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 2;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(2 * 64);
-  cfg.blockDim = dim3(THREADS);
-  cfg.dynamicSmemBytes = CF::SMEM_BYTES;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
+// Per-device launch set-up (SM count, shared-memory attributes, pair grid), done once per
+// device while it is current and before any launch on it, so that no launch inside a stream
+// capture does host-side set-up and a process driving several devices sets each one up.
+constexpr int kMaxDevices = 64;
+struct DeviceSetup {
+  bool done = false;
+  int sms = 0;
+  int pair_grid = 0;   // 2 x the two-CTA clusters that can be resident at once (0: none)
+};
+DeviceSetup g_setup[kMaxDevices];
+
+const DeviceSetup* device_setup() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  DeviceSetup& d = g_setup[dev];
+  if (d.done) return &d;
+  if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return nullptr;
+  bool ok = cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)CfgTF32::SMEM_BYTES) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgTF32W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)CfgTF32W::SMEM_BYTES) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)CfgF16::SMEM_BYTES) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgF16S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)CfgF16S::SMEM_BYTES) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgF16L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)CfgF16L::SMEM_BYTES) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return nullptr;
+  }
   int n = 0;
-  if (cudaFuncSetAttribute(gemm_tf32x3_kernel<CF, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)CF::SMEM_BYTES) != cudaSuccess ||
-      cudaOccupancyMaxActiveClusters(&n, gemm_tf32x3_kernel<CF, 2>, &cfg) != cudaSuccess)
-    n = 0;
+  if (cudaFuncSetAttribute(gemm_pair_kernel<CfgF16P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)CfgF16P::SMEM_BYTES) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * 64);
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = CfgF16P::SMEM_BYTES;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&n, gemm_pair_kernel<CfgF16P>, &cfg) != cudaSuccess) n = 0;
+  }
   cudaGetLastError();
-  grid = 2 * n;
-  return grid;
+  d.pair_grid = 2 * n;
+  d.done = true;
+  return &d;
 }
 
-template <class CF, int CL>
-cudaError_t launch_variant(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int64_t Kp,
-                           int64_t kps, int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha,
-                           float beta, int* status, cudaStream_t st) {
+template <class CF>
+cudaError_t launch_single(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int64_t Kp,
+                          int64_t kps, int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha,
+                          float beta, int* status, cudaStream_t st, const DeviceSetup& dv) {
   CUtensorMap mAhi, mAlo, mBhi, mBlo;
-  // with CL = 2 each CTA copies half of the B tile (BN / 2 rows) into both CTAs
   if (!make_map<CF>(&mAhi, Ahi, M, Kp, kps, P, BM) || !make_map<CF>(&mAlo, Alo, M, Kp, kps, P, BM) ||
-      !make_map<CF>(&mBhi, Bhi, N, Kp, kps, P, BN / CL) || !make_map<CF>(&mBlo, Blo, N, Kp, kps, P, BN / CL))
+      !make_map<CF>(&mBhi, Bhi, N, Kp, kps, P, BN) || !make_map<CF>(&mBlo, Blo, N, Kp, kps, P, BN))
     return cudaErrorInvalidValue;
-  static int sms = 0;
-  static bool attr = false;
-  if (!attr) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(gemm_tf32x3_kernel<CF, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)CF::SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  const int64_t tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
-  if (CL == 1) {
-    const int64_t tiles = tiles_m * tiles_n;
-    const int grid = (int)(tiles < sms ? tiles : sms);
-    gemm_tf32x3_kernel<CF, CL><<<grid, THREADS, CF::SMEM_BYTES, st>>>(mAhi, mAlo, mBhi, mBlo, C, ldc, (int)M, (int)N,
-                                                                     (int)Kp, (int)P, alpha, beta, status);
-    return cudaGetLastError();
-  }
-  int grid = cluster_grid<CF>();
-  if (grid < 2) return cudaErrorInvalidConfiguration;
-  const int64_t pairs = (tiles_m + 1) / 2 * tiles_n;
+  const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  const int grid = (int)(tiles < dv.sms ? tiles : dv.sms);
+  gemm_tf32x3_kernel<CF><<<grid, THREADS, CF::SMEM_BYTES, st>>>(mAhi, mAlo, mBhi, mBlo, C, ldc, (int)M, (int)N,
+                                                               (int)Kp, (int)P, alpha, beta, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int64_t Kp, int64_t kps,
+                        int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha, float beta, int* status,
+                        cudaStream_t st, const DeviceSetup& dv) {
+  using CF = CfgF16P;
+  CUtensorMap mAhi, mAlo, mBhi, mBlo;
+  // each CTA copies its own 128 rows of A and its own 128-row half of the B tile
+  if (!make_map<CF>(&mAhi, Ahi, M, Kp, kps, P, BM) || !make_map<CF>(&mAlo, Alo, M, Kp, kps, P, BM) ||
+      !make_map<CF>(&mBhi, Bhi, N, Kp, kps, P, BN / 2) || !make_map<CF>(&mBlo, Blo, N, Kp, kps, P, BN / 2))
+    return cudaErrorInvalidValue;
+  const int64_t pairs = ((M + 2 * BM - 1) / (2 * BM)) * ((N + BN - 1) / BN);
+  int grid = dv.pair_grid;
   if (grid / 2 > pairs) grid = (int)(2 * pairs);
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
@@ -551,7 +804,7 @@ cudaError_t launch_variant(const void* Ahi, const void* Alo, const void* Bhi, co
   cfg.stream = st;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, gemm_tf32x3_kernel<CF, CL>, mAhi, mAlo, mBhi, mBlo, C, ldc, (int)M, (int)N, (int)Kp,
+  return cudaLaunchKernelEx(&cfg, gemm_pair_kernel<CF>, mAhi, mAlo, mBhi, mBlo, C, ldc, (int)M, (int)N, (int)Kp,
                             (int)P, alpha, beta, status);
 }
 
@@ -563,7 +816,7 @@ cudaError_t launch_variant(const void* Ahi, const void* Alo, const void* Bhi, co
 // variant 1: tf32, k-blocks of 32, 128-byte swizzle, 2 stages; variant 2: fp16 operands
 // (hi/lo planes of __half), k-blocks of 32, 64-byte swizzle, 4 stages, 128-k promotion
 // chunks (kps % 8 == 0); variant 3: as 2 with 64-k chunks; variant 4: as 2 with 256-k chunks;
-// variant 5: as 2 in clusters of two CTAs sharing (multicasting) the B tile.
+// variant 5: fp16 in CTA pairs (tcgen05.mma.cta_group::2, 256 x 256 tiles), 128-k chunks.
 cudaError_t launch_gemm_tf32x3_v(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int64_t Kp,
                                  int64_t kps, int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha,
                                  float beta, int* status, cudaStream_t st, int variant) {
@@ -573,45 +826,30 @@ cudaError_t launch_gemm_tf32x3_v(const void* Ahi, const void* Alo, const void* B
   const bool f16 = variant >= 2 && variant <= 5;
   if ((kps & (f16 ? 7 : 3)) || kps < Kp) return cudaErrorInvalidValue;
   if ((((uintptr_t)Ahi) | ((uintptr_t)Alo) | ((uintptr_t)Bhi) | ((uintptr_t)Blo)) & 15) return cudaErrorInvalidValue;
+  const DeviceSetup* dv = device_setup();
+  if (!dv) return cudaErrorInitializationError;
   if (variant == 5) {
-    // a device (or partition) that cannot co-schedule two-CTA clusters runs the same sums on
-    // single CTAs
-    if (cluster_grid<CfgF16>() >= 2)
-      return launch_variant<CfgF16, 2>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
-    return launch_variant<CfgF16, 1>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
+    // a device (or partition) that cannot co-schedule two-CTA clusters runs the same
+    // products on single CTAs
+    if (dv->pair_grid >= 2)
+      return launch_pair(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st, *dv);
+    return launch_single<CfgF16>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st, *dv);
   }
   if (variant == 4)
-    return launch_variant<CfgF16L, 1>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
+    return launch_single<CfgF16L>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st, *dv);
   if (variant == 3)
-    return launch_variant<CfgF16S, 1>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
+    return launch_single<CfgF16S>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st, *dv);
   if (variant == 2)
-    return launch_variant<CfgF16, 1>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
+    return launch_single<CfgF16>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st, *dv);
   if (variant == 1)
-    return launch_variant<CfgTF32W, 1>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
-  return launch_variant<CfgTF32, 1>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st);
+    return launch_single<CfgTF32W>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st, *dv);
+  return launch_single<CfgTF32>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st, *dv);
 }
 
-// Sets the kernels' shared-memory attributes and caches the SM count ahead of time, so no
-// first launch does host-side set-up (which must not happen inside a stream capture).
-void gemm_prepare() {
-  using namespace tc;
-  static bool done = false;
-  if (done) return;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return;
-  cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgTF32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)CfgTF32::SMEM_BYTES);
-  cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgTF32W, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)CfgTF32W::SMEM_BYTES);
-  cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgF16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)CfgF16::SMEM_BYTES);
-  cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgF16S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)CfgF16S::SMEM_BYTES);
-  cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgF16L, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)CfgF16L::SMEM_BYTES);
-  cluster_grid<CfgF16>();   // sets the cluster kernel's attribute and caches its grid
-  done = true;
-}
+// Sets the kernels' shared-memory attributes and caches the SM count and pair grid of the
+// current device ahead of time, so no first launch does host-side set-up (which must not
+// happen inside a stream capture).
+void gemm_prepare() { tc::device_setup(); }
 
 cudaError_t launch_wait_selftest(int* status, unsigned long long limit_ns, cudaStream_t st) {
   tc::wait_selftest_kernel<<<1, 32, 0, st>>>(status, limit_ns);

@@ -644,8 +644,9 @@ hotrg_status gemm(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R*
   return HOTRG_OK;
 }
 
-// FP16X3 pipelines by option value: 0 = two-CTA clusters sharing the B tile, 128-k promotion
-// chunks; 1 = one CTA, 64-k chunks; 2 = one CTA, 256-k chunks; 3 = one CTA, 128-k chunks.
+// FP16X3 pipelines by option value: 0 = CTA pairs (tcgen05.mma.cta_group::2, 256 x 256 tiles),
+// 128-k promotion chunks; 1 = one CTA, 64-k chunks; 2 = one CTA, 256-k chunks; 3 = one CTA,
+// 128-k chunks.
 constexpr int kF16Variant[4] = {5, 3, 4, 2};
 
 template <typename R>

@@ -457,9 +457,10 @@ def test_nonfinite_input_is_rejected_on_the_host():
 @pytest.mark.parametrize("precision,variants", [("tf32x3", (0, 1)), ("fp16x3", (0, 1, 2, 3))])
 def test_gemm_pipeline_variants_agree(precision, variants):
     """The tensor-core pipelines of a mode give the same step: for tf32x3 4 x 16-wide and
-    2 x 32-wide k-blocks; for fp16x3 two-CTA clusters sharing the B tile and single CTAs
-    promoting every 64, 256 and 128 k. The cluster pipeline and the single-CTA one with the
-    same chunk issue the same MMAs in the same order: bit-identical."""
+    2 x 32-wide k-blocks; for fp16x3 CTA pairs (cta_group::2, 256 x 256 tiles) and single
+    CTAs promoting every 64, 256 and 128 k. The pair pipeline and the single-CTA one with the
+    same chunk issue the same products in the same k order into the same 128-row accumulator
+    per SM: bit-identical."""
     from paper_1911_12954_gb300 import OPT_GEMM_VARIANT
     dims, mu, dcut = (3, 3, 2, 3), 2, 6
     T = random_tensor(12, dims)
@@ -546,7 +547,7 @@ def test_observable_scan_matches_oracle():
 @pytest.mark.parametrize("precision", ["tf32x3", "fp16x3"])
 def test_cuda_graph_steps_match_eager_steps(precision):
     """Captured-and-replayed steps (one graph launch per step, every batch element and
-    impure tensor inside; for fp16x3 the GEMM is a two-CTA cluster launch) give bit-identical
+    impure tensor inside; for fp16x3 the GEMM is a CTA-pair cluster launch) give bit-identical
     results to eager launches: 16 steps, so the four steady-state graphs are each replayed
     several times."""
     sched = [(i % 4, 4) for i in range(16)]
