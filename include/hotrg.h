@@ -232,10 +232,12 @@ hotrg_status hotrg_profile_read(hotrg_ctx* ctx, hotrg_profile* out);
  * It allocates nothing: all intermediates live in one fixed device array of 8 MiB
  * inside the library, held by every GPU that loads the library until the process
  * exits. Limit: every bond dimension <= 8 (larger ones return HOTRG_EINVAL with the
- * reason in hotrg_last_error). The first call on a device looks up that array's device
- * address (make it before any stream capture). Calls share the array, so calls that
- * overlap on the GPU race; each call clears the status words it uses.
- * Errors: EINVAL, ECUDA, ENOCONV. */
+ * reason in hotrg_last_error); any dcut >= 1 (chi <= D_nu^2 <= 64). The first call on a
+ * device looks up that array's device address (make it before any stream capture). Calls
+ * share the array, so calls that overlap on the GPU race; each call clears the status
+ * words it uses. A NaN or infinity in T_dev gives HOTRG_ENONFINITE (U_dev and eps_dev
+ * then hold no usable values).
+ * Errors: EINVAL, ECUDA, ENOCONV, ENONFINITE. */
 hotrg_status hotrg_isometry_noalloc(const double* T_dev, const int dims[4], int mu, int nu, int dcut,
                                     double* U_dev, double* eps_dev, int* primed_dev, void* stream);
 

@@ -18,6 +18,13 @@
 // All calls share the array and it keeps the previous call's contents: the call clears
 // the status words it counts into, and calls that overlap on the GPU (two streams, two
 // host threads) race on it.
+//
+// Limits: bond dimensions up to 8 (the Gram matrices are then at most 64 x 64 and fit the
+// array); any dcut >= 1 (chi = min(D_nu^2, dcut) <= 64 columns, which the candidate and
+// output regions are sized for). A tensor with a NaN or infinity gives non-finite Gram
+// eigenvalues, which the call reports as HOTRG_ENONFINITE.
+#include <math.h>
+
 #include <string>
 
 #include "common.cuh"
@@ -57,9 +64,9 @@ constexpr NoAllocLayout layout() {
   L.lam = o;     o = up256(o + (size_t)2 * kNoAllocN * sizeof(double));
   L.eps = o;     o = up256(o + 2 * sizeof(double));
   L.degen = o;   o = up256(o + 2 * sizeof(int));
-  L.Ucand = o;   o = up256(o + (size_t)2 * kNoAllocN * kMaxLeg * sizeof(double));
+  L.Ucand = o;   o = up256(o + (size_t)2 * kNoAllocN * kNoAllocN * sizeof(double));   // chi <= n
   L.recs = o;    o = up256(o + sizeof(DevRecord));
-  L.U64r = o;    o = up256(o + (size_t)kNoAllocN * kMaxLeg * sizeof(double));
+  L.U64r = o;    o = up256(o + (size_t)kNoAllocN * kNoAllocN * sizeof(double));
   L.total = o;
   return L;
 }
@@ -164,7 +171,7 @@ extern "C" hotrg_status hotrg_isometry_noalloc(const double* T_dev, const int di
     j.lam = (double*)(base + L.lam) + side * kNoAllocN;
     j.eps = (double*)(base + L.eps) + side;
     j.degenerate = (int*)(base + L.degen) + side;
-    j.U = (double*)(base + L.Ucand) + (int64_t)side * kNoAllocN * kMaxLeg;
+    j.U = (double*)(base + L.Ucand) + (int64_t)side * kNoAllocN * kNoAllocN;
   }
   NA_CK(launch_jacobi(ep, 2, n, 1e-10, status, st), "jacobi");
   SelectPack sp{};
@@ -189,9 +196,17 @@ extern "C" hotrg_status hotrg_isometry_noalloc(const double* T_dev, const int di
   sj.nu = nu;
   NA_CK(launch_select<double>(sp, 1, 1e-9, st), "select");
   int host_status[kStWords];
+  double host_lam[2 * kNoAllocN];
   NA_CK(cudaMemcpyAsync(host_status, status, sizeof(host_status), cudaMemcpyDeviceToHost, st), "status read");
+  NA_CK(cudaMemcpyAsync(host_lam, base + L.lam, sizeof(host_lam), cudaMemcpyDeviceToHost, st), "spectrum read");
   NA_CK(cudaStreamSynchronize(st), "sync");
 #undef NA_CK
+  // a NaN or infinity anywhere in T reaches a diagonal entry of a Gram matrix, which no
+  // rotation clears: the spectra show it
+  for (int side = 0; side < 2; ++side)
+    for (int i = 0; i < n; ++i)
+      if (!isfinite(host_lam[side * kNoAllocN + i]))
+        return fail(HOTRG_ENONFINITE, "hotrg_isometry_noalloc: non-finite Gram spectrum (NaN or infinity in T)");
   if (host_status[kStNoConv]) return fail(HOTRG_ENOCONV, "hotrg_isometry_noalloc: Jacobi sweep limit reached");
   return HOTRG_OK;
 }

@@ -310,12 +310,15 @@ def test_dcut8_mixed_first_8_steps_vs_golden(prec):
         assert list(g.step_info(i + 1)["dims"]) == ref["dims"]
 
 
-def test_dcut8_fp64_first_4_steps_vs_golden():
-    """FP64 GPU path on the D_cut = 8 workload through the first steady-state step
-    (step 4: every bond dimension 8, a 7e13-flop contraction): 1e-10 relative."""
+def test_dcut8_fp64_first_8_steps_vs_golden():
+    """FP64 GPU path on the D_cut = 8 workload (T = 6.65, h = 0, towards 1024^4) over the
+    first 8 steps, the oracle's stored values: ln Z/V and ln c to 1e-10 relative after
+    every step, the discarded sums of both sides of every transverse direction to 1e-7.
+    Steps 4..8 each run a 7e13-flop FP64 contraction (about a minute each)."""
     gd = _golden("ising4d_T6.65_h0_dcut8_8steps")
     cfg = gd["config"]
-    sched = [(s["mu"], cfg["dcut"]) for s in gd["steps"][:4]]
+    sched = [(s["mu"], cfg["dcut"]) for s in gd["steps"][:8]]
+    assert len(sched) == 8
     g = _gpu(batch=1, dcut_max=8, precision="fp64", schedule=sched)
     g.init_tensor(gd["beta"], cfg["h"])
     for i, (mu, dc) in enumerate(sched):
@@ -326,6 +329,34 @@ def test_dcut8_fp64_first_4_steps_vs_golden():
         assert info["ln_c"] == pytest.approx(ref["ln_c"], rel=1e-10)
         for n, (e0, e1) in ref["eps"].items():
             assert info["eps"][int(n)] == pytest.approx((e0, e1), rel=1e-7, abs=1e-12)
+
+
+def test_fp16x3_step_legs8_elementwise_vs_oracle():
+    """One FP16x3 step on a seeded decaying tensor with bond dimensions (8, 8, 7, 8), cut 4,
+    element by element against the oracle's coarse_grain with the oracle's isometries:
+    |T'_gpu - T'_oracle| <= 3e-5 max|T'_oracle|. The block-spin product is the benchmarked
+    kernel at scale: M = N = 6272 rows (49 M tiles of 128, so the last CTA pair has one
+    tile past the end and its partner a ragged 256-row tile), K = 32768 in 8 panels of
+    4096, 625 pair tiles over the 76 CTA pairs (more than eight waves)."""
+    dims, mu, dcut = (8, 8, 7, 8), 0, 4
+    T = decaying_tensor(31, dims)
+    T = T / np.linalg.norm(T)
+    g = _gpu(batch=1, dcut_max=8, precision="fp16x3", schedule=[(mu, dcut)], dims0=dims)
+    g.set_tensor(T)
+    main, _ = g.step_flops(mu, dcut)
+    assert main == pytest.approx(2.0 * 6272 ** 2 * 32768, rel=1e-12)
+    g.step(mu, dcut)
+    got = g.tensor()
+    isos = {n: H.isometry(T, T, mu, n, dcut) for n in (1, 2, 3)}
+    for iso in isos.values():
+        lam = iso.spectrum
+        # the kept subspace is unique well above the FP32 noise of the mixed-mode Gram
+        assert not iso.degenerate_cut and lam[iso.chi - 1] - lam[iso.chi] > 1e-4 * lam[0]
+    ref = H.coarse_grain(T, T, {n: iso.U for n, iso in isos.items()}, mu)
+    ref = ref / np.linalg.norm(ref)
+    assert got.shape == ref.shape
+    err = np.abs(got - ref).max()
+    assert err <= 3e-5 * np.abs(ref).max(), err
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("tf32x3", 3e-5), ("fp16x3", 3e-5)])
