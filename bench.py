@@ -65,6 +65,9 @@ def parse_args():
     p.add_argument("--scan-lo", type=float, default=6.670)
     p.add_argument("--scan-hi", type=float, default=6.690)
     p.add_argument("--scan-h", type=float, default=1e-5, help="field of the scan")
+    p.add_argument("--autotune", type=int, default=1,
+                   help="take each step's closing direction and GEMM pipeline from the autotuner (the "
+                        "steady-state shapes are tuned after the warm-up steps, outside the timed region)")
     p.add_argument("--gemm-variant", type=int, default=0,
                    help="tensor-core GEMM pipeline option (HOTRG_OPT_GEMM_VARIANT) for every mixed run")
     p.add_argument("--precision", choices=["tf32x3", "fp16x3"], default="fp16x3",
@@ -95,6 +98,15 @@ def tensor_peak(precision: str, sustained: bool = True):
     except Exception:
         b = 1700.0 if sustained else 1900.0
         return b * r, f"fallback bf16 {b / 1000:.1f} PF " + rname
+
+
+def kernel_name(precision: str, option: int) -> str:
+    """The block-spin GEMM kernel a HOTRG_OPT_GEMM_VARIANT value runs."""
+    if precision == "fp16x3":
+        return {0: "gemm_pair_kernel<CfgF16P> (CTA pairs, tcgen05.mma.cta_group::2)",
+                1: "gemm_tf32x3_kernel<CfgF16S>", 2: "gemm_tf32x3_kernel<CfgF16L>",
+                3: "gemm_tf32x3_kernel<CfgF16>"}[option]
+    return {0: "gemm_tf32x3_kernel<CfgTF32>", 1: "gemm_tf32x3_kernel<CfgTF32W>"}.get(option, "gemm_simt_kernel")
 
 
 class ClockSampler:
@@ -386,11 +398,15 @@ def main():
 
     # ---------------------------------------------------------------- mixed precision, timed
     run = HOTRG(batch=args.batch, dcut_max=D, precision=args.precision, impure=impure, schedule=sched,
-                graphs=bool(args.graphs))
+                graphs=bool(args.graphs), autotune=bool(args.autotune))
     run.set_option(OPT_GEMM_VARIANT, args.gemm_variant)
     run.init_tensor(betas, hfield)
     for i in range(args.warmup):
         run.step(*sched[i])
+    if args.autotune:
+        # the timed steps' shapes (steady state after the warm-up) are timed and cached here
+        for d in sorted({mu for mu, _ in sched[args.warmup:nsteps]}):
+            run.autotune(d, D)
     barrier()
     flops = 0.0
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -404,6 +420,9 @@ def main():
         barrier()
     prof = run.profile_read()
     run.profile(False)
+    plans = [{"step": k, **{f: run.step_info(k)[f] for f in ("mu", "closing", "gemm_option", "tuned")}}
+             for k in range(args.warmup + 1, nsteps + 1)]
+    tune = run.tune_stats()
     value, ms_max = sync.throughput(flops, start.elapsed_time(stop))
     lnz_run = [float(x) for x in run.lnZ()]
     obs = {}
@@ -465,12 +484,13 @@ def main():
     e2e = None
     if args.e2e and args.batch == 1 and not impure:
         full = [(i % 4, D) for i in range(LATTICE_STEPS)]
-        job = HOTRG(batch=1, dcut_max=D, precision=args.precision, schedule=full)
+        job = HOTRG(batch=1, dcut_max=D, precision=args.precision, schedule=full, autotune=bool(args.autotune))
         job.set_option(OPT_GEMM_VARIANT, args.gemm_variant)
         bh = torch.tensor([beta], dtype=torch.float64).pin_memory()
         hh = torch.tensor([H_WORK], dtype=torch.float64).pin_memory()
-        job.init_tensor(bh.numpy(), hh.numpy())           # warm the job once
-        job.step(*full[0])
+        job.init_tensor(bh.numpy(), hh.numpy())           # one untimed job: kernels and tuned plans warm
+        for s in full:
+            job.step(*s)
         job.lnZ()
         barrier()
         t0 = time.perf_counter()
@@ -485,7 +505,8 @@ def main():
         secs = allmax(t1 - t0)
         e2e = {"value": allsum(fl) / secs / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 16,
                "d2h_bytes_per_step": 32, "step": f"whole {LATTICE_STEPS}-step job (1024^4 sites): init from host "
-               "beta, h (pinned) -> 40 steps -> ln Z/V read back", "seconds": secs, "lnZ_over_V": lnz40}
+               "beta, h (pinned) -> 40 steps -> ln Z/V read back, after one untimed job"
+               + (" (autotuner cache filled)" if args.autotune else ""), "seconds": secs, "lnZ_over_V": lnz40}
         del job
         torch.cuda.empty_cache()
 
@@ -508,21 +529,21 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {**workload_config(args, world),
-                   "precision": f"{args.precision} (fp32 storage)", "cuda_graphs": bool(args.graphs), "gemm_variant": args.gemm_variant,
+                   "precision": f"{args.precision} (fp32 storage)", "cuda_graphs": bool(args.graphs),
+                   "gemm_variant": args.gemm_variant, "autotune": bool(args.autotune),
                    "l2": f"operands larger than L2 (GEMM A and B: 2 x "
                          f"{(4 if args.precision == 'fp16x3' else 8) * D ** 10 / 1e9:.1f} GB per step, hi + lo)"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "algorithmic_bytes": (2 * (4 if args.precision == "fp16x3" else 8) + 4) * float(D) ** 10,
-                     "kernel": ("gemm_pair_kernel<CfgF16P> (CTA pairs, tcgen05.mma.cta_group::2)"
-                                if args.precision == "fp16x3" and args.gemm_variant == 0 else
-                                f"gemm_tf32x3_kernel<{'CfgF16' if args.precision == 'fp16x3' else 'CfgTF32'}>")
+                     "kernel": " + ".join(sorted({kernel_name(args.precision, pl["gemm_option"]) for pl in plans}))
                                + " (block-spin contraction, 2 M N K algorithmic flops per launch)",
                      "peak_source": peak_src, "launches": prof["gemm_launches"],
                      "avg_launch_ms": prof["gemm_ms"] / max(1, prof["gemm_launches"]),
                      "tensor_pipe_flops_frac": (3 * achieved / peak) if achieved else None,
                      "peak_burst": peak_burst, "frac_of_burst": (achieved / peak_burst) if achieved else None},
         "gpu_launches": prof["launches"],
+        "plans": plans, "autotuner": tune,
         "clocks": clk.summary(),
         "fp64": fp64, "accuracy": accuracy, "lnZ_over_V_after_timed_steps": lnz_run, "observables": obs,
         "cpu_baseline": cpu, "e2e": e2e,

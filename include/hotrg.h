@@ -77,6 +77,10 @@ typedef struct {
   int degenerate[4]; /* per transverse nu: the cut fell inside an eigenvalue cluster   */
   int slices[2];     /* slices of the new a leg taken for A (rows) and for B (rows) when
                         the workspace was smaller than the unsliced plan (1 = unsliced) */
+  int closing;       /* transverse direction closed by the last two isometry passes    */
+  int gemm_option;   /* HOTRG_OPT_GEMM_VARIANT value of the block-spin GEMM (-1: the
+                        CUDA-core GEMM of the FP64 and FP32 modes)                      */
+  int tuned;         /* 1 if closing and gemm_option came from the autotuner's cache    */
 } hotrg_step_record;
 
 /* Create a context for `batch` runs with bond dimensions up to `dcut_max`
@@ -187,9 +191,32 @@ hotrg_status hotrg_step_flops(const hotrg_ctx* ctx, int dir, int dcut, double* m
  * HOTRG_OPT_GRAPHS: 1 = capture each distinct step (plan, buffer, first step or not) once
  *   into a CUDA graph and replay it (every kernel of the step for every batch element in
  *   one graph launch); needs a non-default stream (hotrg_set_stream). Per-GEMM profiling
- *   events are not recorded in this mode. Errors: EINVAL. */
-enum { HOTRG_OPT_JACOBI_SWEEPS = 1, HOTRG_OPT_GEMM_VARIANT = 2, HOTRG_OPT_GRAPHS = 3 };
+ *   events are not recorded in this mode.
+ * HOTRG_OPT_AUTOTUNE: 1 = every step takes its closing direction and GEMM pipeline from the
+ *   autotuner's cache (hotrg_autotune), timing a step shape it has not seen before the step
+ *   runs (outside any capture; with HOTRG_OPT_GRAPHS, tune every shape with
+ *   hotrg_autotune before the first captured step). 0 (default) = the planner's choice:
+ *   the closing direction with the fewest flops and the option's pipeline. Errors: EINVAL. */
+enum { HOTRG_OPT_JACOBI_SWEEPS = 1, HOTRG_OPT_GEMM_VARIANT = 2, HOTRG_OPT_GRAPHS = 3, HOTRG_OPT_AUTOTUNE = 4 };
 hotrg_status hotrg_set_option(hotrg_ctx* ctx, int option, int value);
+
+/* Autotuner: times, on the GPU and on the run's current tensors, every plan of the step
+ * hotrg_step(ctx, dir, dcut) would run next that computes the same contraction: each
+ * closing direction (the transverse direction whose isometries are applied last; it sets
+ * the shapes of the half contractions and of the block-spin GEMM, Sec. 2) and, in the
+ * tensor-core modes, each pipeline that gives the same products (FP16X3: CTA pairs or one
+ * CTA per tile; TF32X3: 16- or 32-wide k-blocks). The fastest (ties to the planner's
+ * choice) is cached for this device and step shape (bond dimensions, direction, cut,
+ * precision, batch, tensors, workspace size) for the life of the process and used by
+ * every context with HOTRG_OPT_AUTOTUNE set. The run does not advance: the current
+ * tensors, ln Z and the step counter are unchanged. Synchronises the stream; not allowed
+ * while the stream is being captured (ESTATE). Errors: EINVAL, EWORKSPACE, ESTATE,
+ * ECUDA and the device-side statuses. */
+hotrg_status hotrg_autotune(hotrg_ctx* ctx, int dir, int dcut);
+
+/* Shapes this context has timed (hotrg_autotune or HOTRG_OPT_AUTOTUNE) and steps whose plan
+ * it took from the cache. Errors: EINVAL. */
+hotrg_status hotrg_tune_stats(const hotrg_ctx* ctx, uint64_t* timed, uint64_t* hits);
 
 /* Failure-detection self-test: on the context's stream, one thread waits, with the same
  * bounded wait the tensor-core GEMM uses on its mbarriers, on a barrier that nothing

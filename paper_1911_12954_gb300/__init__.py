@@ -4,5 +4,6 @@ The compute path is libhotrg.so (CUDA for sm_103a, C ABI in include/hotrg.h); th
 package holds its sources (csrc/), its build script and a thin ctypes binding.
 """
 
-from .hotrg import (FP32, FP64, IMPURE_NONE, IMPURE_SIGMA, IMPURE_SIGMASIGMA, OPT_GEMM_VARIANT, OPT_GRAPHS,  # noqa: F401
-                    OPT_JACOBI_SWEEPS, PRECISIONS, SYMBOLS, TF32X3, HOTRG, HotrgError, library_path)
+from .hotrg import (FP32, FP64, IMPURE_NONE, IMPURE_SIGMA, IMPURE_SIGMASIGMA, OPT_AUTOTUNE,  # noqa: F401
+                    OPT_GEMM_VARIANT, OPT_GRAPHS, OPT_JACOBI_SWEEPS, PRECISIONS, SYMBOLS, TF32X3, HOTRG,
+                    HotrgError, library_path)

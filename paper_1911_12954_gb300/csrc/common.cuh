@@ -13,6 +13,7 @@ constexpr int kMaxLeg = 16;       // largest bond dimension (dcut_max)
 constexpr int kMaxGramN = kMaxLeg * kMaxLeg;  // largest Gram matrix side (D_nu^2)
 constexpr int kMaxSteps = 64;     // steps recorded per batch element
 constexpr int kJacobiMaxSweeps = 60;
+constexpr int kJacobiSmemN = 96;  // the eigensolver keeps A and V in shared memory up to this n (no work buffer)
 
 // Device-side status words (in the caller's workspace), read back at sync points.
 enum StatusWord { kStNoConv = 0, kStNonFinite = 1, kStTimeout = 2, kStWords = 4 };
@@ -92,13 +93,33 @@ struct DevRecord {
 };
 
 // Job packs passed to kernels by value (kernel parameter space), so a step needs no
-// host-to-device copies of job descriptors and can be captured in a CUDA graph.
+// host-to-device copies of job descriptors and can be captured in a CUDA graph. A pack
+// describes the jobs of batch element 0; with batch > 1 one launch also runs them for
+// elements 1 .. batch - 1, every pointer of element b advanced by b times its stride
+// (counted in elements of the pointed-to type). batch = 1 is the plain pack.
 constexpr int kMaxGramJobs = 12;
 constexpr int kMaxEigJobs = 6;
 constexpr int kMaxSelectJobs = 3;
-struct GramPack { GramJob j[kMaxGramJobs]; };
-struct EigPack { EigJob j[kMaxEigJobs]; };
-struct SelectPack { SelectJob j[kMaxSelectJobs]; };
+struct GramPack {
+  GramJob j[kMaxGramJobs];
+  int batch = 1;
+  int64_t sT = 0;           // tensor (storage elements)
+  int64_t sPart = 0;        // split-K partials (doubles)
+};
+struct EigPack {
+  EigJob j[kMaxEigJobs];
+  int batch = 1;
+  int64_t sG = 0, sWork = 0, sLam = 0, sU = 0, sEps = 0, sDeg = 0;
+};
+struct SelectPack {
+  SelectJob j[kMaxSelectJobs];
+  int batch = 1;
+  int64_t sU = 0;           // candidate isometries (doubles)
+  int64_t sLam = 0, sEps = 0, sDeg = 0;
+  int64_t sU64 = 0;         // chosen isometry, FP64
+  int64_t sUr = 0;          // chosen isometry, storage precision (elements)
+  int64_t sRec = 0;         // step records (DevRecord)
+};
 
 // Message returned by hotrg_last_error for this host thread.
 void set_last_error(const char* msg);
@@ -114,12 +135,35 @@ cudaError_t launch_gram_reduce(const GramPack& jobs, int njobs, int nchunks, int
                                double* out, cudaStream_t st);
 cudaError_t launch_gram_merge(const double* A1, const double* A2, int Dn, int Dk, double* G,
                               cudaStream_t st);
+// The six Gram matrices (3 transverse directions x 2 sides) of each of `batch` elements in
+// one launch: half-Grams at half[((b * 12) + (i * 2 + side) * 2 + h) * RRs] (h = 0: k on
+// T1's mu' leg, 1: k on T2's mu leg), G at G[((b * 6) + i * 2 + side) * nn], Dn[i] the bond
+// dimension of direction i, Dk that of mu.
+cudaError_t launch_gram_merge_batch(const double* half, int64_t RRs, const int Dn[3], int Dk, double* G, int64_t nn,
+                                    int batch, cudaStream_t st);
 cudaError_t launch_jacobi(const EigPack& jobs, int njobs, int nmax, double cluster_tau, int* status,
                           cudaStream_t st, int max_sweeps = kJacobiMaxSweeps, double tie_rel = 1e-8);
 cudaError_t launch_wait_selftest(int* status, unsigned long long limit_ns, cudaStream_t st);
-cudaError_t launch_gemm_tf32x3_v(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int64_t Kp,
-                                 int64_t kps, int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha,
-                                 float beta, int* status, cudaStream_t st, int variant);
+// One output of a grouped block-spin GEMM: C = alpha * sum_{s < nseg} A_{a[s]} B_{b[s]}^T,
+// where A_w, B_w are the w-th operand tensors of the launch (the k loop runs over the nseg
+// segments one after the other, each the full K).
+struct GemmProblem {
+  float* C;
+  float alpha;
+  int nseg;
+  int a[2], b[2];
+};
+constexpr int kMaxGemmProblems = 3;
+struct GemmGroup {
+  GemmProblem p[kMaxGemmProblems];
+  int nprob;
+};
+// Tensor-core GEMM over W operand tensors per plane (hi, lo), each [P][rows][kps] in K
+// panels, tensor w of a plane aws (A) or bws (B) elements after tensor w - 1; every problem
+// has M rows, N columns and row stride ldc. variant selects the pipeline (gemm_tc.cu).
+cudaError_t launch_gemm_group(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int W, int64_t aws,
+                              int64_t bws, int64_t Kp, int64_t kps, int64_t P, int64_t M, int64_t N, int64_t ldc,
+                              const GemmGroup& g, int* status, cudaStream_t st, int variant);
 
 template <typename R>
 cudaError_t launch_select(const SelectPack& jobs, int njobs, double side_rel, cudaStream_t st);

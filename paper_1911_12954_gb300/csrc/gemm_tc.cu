@@ -1,9 +1,12 @@
 // gemm_tc.cu - tcgen05 / TMEM / TMA GEMM for the block-spin contraction (FP16x3 and TF32x3).
 //
-// C[m][n] = alpha * sum_k (Ahi Bhi + Ahi Blo + Alo Bhi)[m,n,k] + beta * C[m][n]
-// with A = Ahi + Alo and B = Bhi + Blo: either fp16 planes (hi, lo of 2^14 x; kind::f16,
-// the default) or tf32 values stored in FP32 words (kind::tf32), both operands K-major in
-// K panels (see tma_load). This is the O(D^15) block-spin contraction of the HOTRG step,
+// C[m][n] = alpha * sum_s sum_k (Ahi Bhi + Ahi Blo + Alo Bhi)[m,n,k] over the segments s of
+// one output, with A = Ahi + Alo and B = Bhi + Blo: either fp16 planes (hi, lo of 2^14 x;
+// kind::f16, the default) or tf32 values stored in FP32 words (kind::tf32), both operands
+// K-major in K panels (see tma_load). One launch computes every output of a group (the pure
+// tensor and the impure ones of a step, GemmGroup): an output with two segments, such as
+// S' = (A_S B_T^T + A_T B_S^T) / 2, runs its k loop over both operand pairs into one
+// accumulator, so no output is read back. This is the O(D^15) block-spin contraction of the HOTRG step,
 // where Sec. 2 of arXiv:1911.12954 places the D^(4d-1) cost of the method, carried out on
 // the 5th-generation tensor cores with FP32 accumulation; the dropped Alo Blo term is below
 // 2^-21 of each product.
@@ -177,24 +180,26 @@ __global__ void wait_selftest_kernel(int* status, unsigned long long limit_ns) {
   }
 }
 
-// Operands are stored in K panels: element (row, k) with k = p Kp + kin sits at
-// [(p rows + row) kps + kin] (kps = Kp rounded up to 4). The 3D tensor map is
-// {Kp, rows, P}; a panel keeps the rows of one k range contiguous, so a box of 128 rows
+// Operands are stored in K panels: element (row, k) with k = p Kp + kin of tensor w sits at
+// [((w P + p) rows + row) kps + kin] (kps = Kp rounded up to 4). The 4D tensor map is
+// {Kp, rows, P, W}; a panel keeps the rows of one k range contiguous, so a box of 128 rows
 // spans at most a few pages even when K is in the hundreds of thousands.
-__device__ __forceinline__ void tma_load(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y, int z) {
+__device__ __forceinline__ void tma_load(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y, int z,
+                                         int w) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
       "[%2];" ::"r"(su32(dst)),
-      "l"((uint64_t)map), "r"(su32(bar)), "r"(x), "r"(y), "r"(z)
+      "l"((uint64_t)map), "r"(su32(bar)), "r"(x), "r"(y), "r"(z), "r"(w)
       : "memory");
 }
 // The same load into this CTA's shared memory, with its bytes counted on an mbarrier of
 // either CTA of the pair (bar: shared::cluster address).
-__device__ __forceinline__ void tma_load_pair(const CUtensorMap* map, uint32_t bar, void* dst, int x, int y, int z) {
+__device__ __forceinline__ void tma_load_pair(const CUtensorMap* map, uint32_t bar, void* dst, int x, int y, int z,
+                                              int w) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(su32(dst)),
-      "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y), "r"(z)
+      "cp.async.bulk.tensor.4d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(su32(dst)),
+      "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y), "r"(z), "r"(w)
       : "memory");
 }
 
@@ -300,28 +305,19 @@ __device__ __forceinline__ void promote_chunk(uint32_t taddr, float* acc) {
   }
 }
 
-// alpha * acc + beta * C for one thread's 128 columns of row m (guarded).
+// alpha * acc for one thread's 128 columns of row m (guarded).
 __device__ __forceinline__ void store_row(float* __restrict__ C, int64_t ldc, int M, int N, int64_t m, int n0,
-                                          const float* acc, float alpha, float beta) {
+                                          const float* acc, float alpha) {
   if (m >= M) return;
   float* crow = C + m * ldc + n0;
   if (n0 + BN / 2 <= N && ((((uintptr_t)crow) & 15) == 0)) {
 #pragma unroll
-    for (int j = 0; j < BN / 2; j += 4) {
-      float4 o = make_float4(alpha * acc[j], alpha * acc[j + 1], alpha * acc[j + 2], alpha * acc[j + 3]);
-      if (beta != 0.f) {
-        const float4 old = *(const float4*)(crow + j);
-        o.x += beta * old.x;
-        o.y += beta * old.y;
-        o.z += beta * old.z;
-        o.w += beta * old.w;
-      }
-      *(float4*)(crow + j) = o;
-    }
+    for (int j = 0; j < BN / 2; j += 4)
+      *(float4*)(crow + j) = make_float4(alpha * acc[j], alpha * acc[j + 1], alpha * acc[j + 2], alpha * acc[j + 3]);
   } else {
 #pragma unroll
     for (int j = 0; j < BN / 2; ++j)
-      if (n0 + j < N) crow[j] = alpha * acc[j] + (beta != 0.f ? beta * crow[j] : 0.f);
+      if (n0 + j < N) crow[j] = alpha * acc[j];
   }
 }
 
@@ -329,7 +325,7 @@ template <class CF>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                        const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
-                       float* __restrict__ C, int64_t ldc, int M, int N, int Kp, int P, float alpha, float beta,
+                       const __grid_constant__ GemmGroup grp, int64_t ldc, int M, int N, int Kp, int P,
                        int* status) {
   constexpr int STAGES = CF::STAGES, BK = CF::BK, A_BYTES = CF::A_BYTES, B_BYTES = CF::B_BYTES,
                 STAGE_BYTES = CF::STAGE_BYTES, KPC = CF::KB_PER_CHUNK;
@@ -345,10 +341,10 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
-  const int ntiles = tiles_m * tiles_n;
+  const int ntiles1 = tiles_m * tiles_n;          // tiles of one output
+  const int ntiles = grp.nprob * ntiles1;         // outputs one after the other
   const int nkbp = (Kp + BK - 1) / BK;   // k-blocks per panel (the last one zero-filled past Kp)
-  const int nkb = P * nkbp;
-  const int nchunk = (nkb + KPC - 1) / KPC;
+  const int nkb = P * nkbp;              // k-blocks of one segment
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -384,20 +380,24 @@ __global__ void __launch_bounds__(THREADS, 1)
     int nissued = 0;   // k-blocks issued; stage q has been filled (nissued - q + STAGES - 1) / STAGES times
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const int pb = t / ntiles1;
       int tm, tn;
-      tile_coords(t, tiles_m, tiles_n, GROUP_M, tm, tn);
-      for (int kb = 0; kb < nkb; ++kb) {
+      tile_coords(t - pb * ntiles1, tiles_m, tiles_n, GROUP_M, tm, tn);
+      const int nseg = grp.p[pb].nseg;
+      for (int kb = 0; kb < nseg * nkb; ++kb) {
         if (!mbar_wait(&empty[s], ph ^ 1, status)) {
           ok = false;
           break;
         }
         uint8_t* st = smem + s * STAGE_BYTES;
-        const int pn = kb / nkbp, kx = (kb - pn * nkbp) * BK;
+        const int sg = kb >= nkb ? 1 : 0, kq = kb - sg * nkb;
+        const int wa = grp.p[pb].a[sg], wb = grp.p[pb].b[sg];
+        const int pn = kq / nkbp, kx = (kq - pn * nkbp) * BK;
         mbar_expect_tx(&full[s], STAGE_BYTES);
-        tma_load(&mAhi, &full[s], st, kx, tm * BM, pn);
-        tma_load(&mAlo, &full[s], st + A_BYTES, kx, tm * BM, pn);
-        tma_load(&mBhi, &full[s], st + 2 * A_BYTES, kx, tn * BN, pn);
-        tma_load(&mBlo, &full[s], st + 2 * A_BYTES + B_BYTES, kx, tn * BN, pn);
+        tma_load(&mAhi, &full[s], st, kx, tm * BM, pn, wa);
+        tma_load(&mAlo, &full[s], st + A_BYTES, kx, tm * BM, pn, wa);
+        tma_load(&mBhi, &full[s], st + 2 * A_BYTES, kx, tn * BN, pn, wb);
+        tma_load(&mBlo, &full[s], st + 2 * A_BYTES + B_BYTES, kx, tn * BN, pn, wb);
         ++nissued;
         if (++s == STAGES) {
           s = 0;
@@ -414,9 +414,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t ph = 0, cph = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      for (int kb = 0; kb < nkb; ++kb) {
+      const int nkbt = grp.p[t / ntiles1].nseg * nkb;
+      for (int kb = 0; kb < nkbt; ++kb) {
         const bool first = kb % KPC == 0;
-        const bool last = kb % KPC == KPC - 1 || kb == nkb - 1;
+        const bool last = kb % KPC == KPC - 1 || kb == nkbt - 1;
         if ((first && !mbar_wait(&cempty[cb], cph ^ 1, status)) || !mbar_wait(&full[s], ph, status)) {
           ok = false;
           break;
@@ -460,8 +461,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t cph = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const int pb = t / ntiles1;
       int tm, tn;
-      tile_coords(t, tiles_m, tiles_n, GROUP_M, tm, tn);
+      tile_coords(t - pb * ntiles1, tiles_m, tiles_n, GROUP_M, tm, tn);
+      const int nchunk = (grp.p[pb].nseg * nkb + KPC - 1) / KPC;
       float acc[BN / 2];
 #pragma unroll
       for (int j = 0; j < BN / 2; ++j) acc[j] = 0.f;
@@ -481,7 +484,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
       }
       if (!ok) break;
-      store_row(C, ldc, M, N, (int64_t)tm * BM + row, tn * BN + h * (BN / 2), acc, alpha, beta);
+      store_row(grp.p[pb].C, ldc, M, N, (int64_t)tm * BM + row, tn * BN + h * (BN / 2), acc, grp.p[pb].alpha);
     }
   }
   fence_before();
@@ -502,7 +505,7 @@ template <class CF>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_pair_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                      const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
-                     float* __restrict__ C, int64_t ldc, int M, int N, int Kp, int P, float alpha, float beta,
+                     const __grid_constant__ GemmGroup grp, int64_t ldc, int M, int N, int Kp, int P,
                      int* status) {
   static_assert(CF::kPair && CF::kF16, "pair kernel: fp16 pair configuration");
   constexpr int STAGES = CF::STAGES, BK = CF::BK, A_BYTES = CF::A_BYTES, B_BYTES = CF::B_BYTES,
@@ -522,10 +525,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int cid = blockIdx.x / 2, ncl = gridDim.x / 2;
   const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
   const int tiles_mg = (tiles_m + 1) / 2;               // 256-row tiles
-  const int ntiles = tiles_mg * tiles_n;
+  const int ntiles1 = tiles_mg * tiles_n;               // tiles of one output
+  const int ntiles = grp.nprob * ntiles1;
   const int nkbp = (Kp + BK - 1) / BK;
-  const int nkb = P * nkbp;
-  const int nchunk = (nkb + KPC - 1) / KPC;
+  const int nkb = P * nkbp;                             // k-blocks of one segment
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -563,23 +566,27 @@ __global__ void __launch_bounds__(THREADS, 1)
     int nissued = 0;   // k-blocks issued; stage q has been filled (nissued - q + STAGES - 1) / STAGES times
     bool ok = true;
     for (int t = cid; t < ntiles && ok; t += ncl) {
+      const int pb = t / ntiles1;
       int tg, tn;
-      tile_coords(t, tiles_mg, tiles_n, GROUP_M / 2, tg, tn);
+      tile_coords(t - pb * ntiles1, tiles_mg, tiles_n, GROUP_M / 2, tg, tn);
       const int tm = 2 * tg + (int)rank;
       const int yb = tn * BN + (int)rank * (BN / 2);
-      for (int kb = 0; kb < nkb; ++kb) {
+      const int nseg = grp.p[pb].nseg;
+      for (int kb = 0; kb < nseg * nkb; ++kb) {
         if (!mbar_wait<true>(&empty[s], ph ^ 1, status)) {
           ok = false;
           break;
         }
         uint8_t* st = smem + s * STAGE_BYTES;
-        const int pn = kb / nkbp, kx = (kb - pn * nkbp) * BK;
+        const int sg = kb >= nkb ? 1 : 0, kq = kb - sg * nkb;
+        const int wa = grp.p[pb].a[sg], wb = grp.p[pb].b[sg];
+        const int pn = kq / nkbp, kx = (kq - pn * nkbp) * BK;
         if (rank == 0) mbar_expect_tx(&full[s], 2 * STAGE_BYTES);   // this CTA's and the partner's copies
         const uint32_t fb = full0 + (uint32_t)(s * sizeof(uint64_t));
-        tma_load_pair(&mAhi, fb, st, kx, tm * BM, pn);
-        tma_load_pair(&mAlo, fb, st + A_BYTES, kx, tm * BM, pn);
-        tma_load_pair(&mBhi, fb, st + 2 * A_BYTES, kx, yb, pn);
-        tma_load_pair(&mBlo, fb, st + 2 * A_BYTES + B_BYTES, kx, yb, pn);
+        tma_load_pair(&mAhi, fb, st, kx, tm * BM, pn, wa);
+        tma_load_pair(&mAlo, fb, st + A_BYTES, kx, tm * BM, pn, wa);
+        tma_load_pair(&mBhi, fb, st + 2 * A_BYTES, kx, yb, pn, wb);
+        tma_load_pair(&mBlo, fb, st + 2 * A_BYTES + B_BYTES, kx, yb, pn, wb);
         ++nissued;
         if (++s == STAGES) {
           s = 0;
@@ -599,9 +606,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t ph = 0, cph = 0;
     bool ok = true;
     for (int t = cid; t < ntiles && ok; t += ncl) {
-      for (int kb = 0; kb < nkb; ++kb) {
+      const int nkbt = grp.p[t / ntiles1].nseg * nkb;
+      for (int kb = 0; kb < nkbt; ++kb) {
         const bool first = kb % KPC == 0;
-        const bool last = kb % KPC == KPC - 1 || kb == nkb - 1;
+        const bool last = kb % KPC == KPC - 1 || kb == nkbt - 1;
         if ((first && !mbar_wait<true>(&cempty[cb], cph ^ 1, status)) || !mbar_wait(&full[s], ph, status)) {
           ok = false;
           break;
@@ -647,9 +655,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t cph = 0;
     bool ok = true;
     for (int t = cid; t < ntiles && ok; t += ncl) {
+      const int pb = t / ntiles1;
       int tg, tn;
-      tile_coords(t, tiles_mg, tiles_n, GROUP_M / 2, tg, tn);
+      tile_coords(t - pb * ntiles1, tiles_mg, tiles_n, GROUP_M / 2, tg, tn);
       const int tm = 2 * tg + (int)rank;
+      const int nchunk = (grp.p[pb].nseg * nkb + KPC - 1) / KPC;
       float acc[BN / 2];
 #pragma unroll
       for (int j = 0; j < BN / 2; ++j) acc[j] = 0.f;
@@ -669,7 +679,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
       }
       if (!ok) break;
-      store_row(C, ldc, M, N, (int64_t)tm * BM + row, tn * BN + h * (BN / 2), acc, alpha, beta);
+      store_row(grp.p[pb].C, ldc, M, N, (int64_t)tm * BM + row, tn * BN + h * (BN / 2), acc, grp.p[pb].alpha);
     }
   }
   fence_before();
@@ -698,14 +708,16 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 template <class CF>
-bool make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t Kp, int64_t kps, int64_t P, int box_rows) {
+bool make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t Kp, int64_t kps, int64_t P, int64_t W,
+              int64_t wstride, int box_rows) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return false;
-  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)P};
-  cuuint64_t strides[2] = {(cuuint64_t)(kps * CF::ELT), (cuuint64_t)(rows * kps * CF::ELT)};
-  cuuint32_t box[3] = {(cuuint32_t)CF::BK, (cuuint32_t)box_rows, 1};
-  cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(map, CF::kF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)ptr,
+  cuuint64_t dims[4] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)P, (cuuint64_t)W};
+  cuuint64_t strides[3] = {(cuuint64_t)(kps * CF::ELT), (cuuint64_t)(rows * kps * CF::ELT),
+                           (cuuint64_t)(wstride * CF::ELT)};
+  cuuint32_t box[4] = {(cuuint32_t)CF::BK, (cuuint32_t)box_rows, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = enc(map, CF::kF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)ptr,
                    dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CF::LAYOUT == 2 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -766,30 +778,31 @@ const DeviceSetup* device_setup() {
 }
 
 template <class CF>
-cudaError_t launch_single(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int64_t Kp,
-                          int64_t kps, int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha,
-                          float beta, int* status, cudaStream_t st, const DeviceSetup& dv) {
+cudaError_t launch_single(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int64_t W, int64_t aws,
+                          int64_t bws, int64_t Kp, int64_t kps, int64_t P, int64_t M, int64_t N, int64_t ldc,
+                          const GemmGroup& g, int* status, cudaStream_t st, const DeviceSetup& dv) {
   CUtensorMap mAhi, mAlo, mBhi, mBlo;
-  if (!make_map<CF>(&mAhi, Ahi, M, Kp, kps, P, BM) || !make_map<CF>(&mAlo, Alo, M, Kp, kps, P, BM) ||
-      !make_map<CF>(&mBhi, Bhi, N, Kp, kps, P, BN) || !make_map<CF>(&mBlo, Blo, N, Kp, kps, P, BN))
+  if (!make_map<CF>(&mAhi, Ahi, M, Kp, kps, P, W, aws, BM) || !make_map<CF>(&mAlo, Alo, M, Kp, kps, P, W, aws, BM) ||
+      !make_map<CF>(&mBhi, Bhi, N, Kp, kps, P, W, bws, BN) || !make_map<CF>(&mBlo, Blo, N, Kp, kps, P, W, bws, BN))
     return cudaErrorInvalidValue;
-  const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  const int64_t tiles = g.nprob * ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
   const int grid = (int)(tiles < dv.sms ? tiles : dv.sms);
-  gemm_tf32x3_kernel<CF><<<grid, THREADS, CF::SMEM_BYTES, st>>>(mAhi, mAlo, mBhi, mBlo, C, ldc, (int)M, (int)N,
-                                                               (int)Kp, (int)P, alpha, beta, status);
+  gemm_tf32x3_kernel<CF><<<grid, THREADS, CF::SMEM_BYTES, st>>>(mAhi, mAlo, mBhi, mBlo, g, ldc, (int)M, (int)N,
+                                                               (int)Kp, (int)P, status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pair(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int64_t Kp, int64_t kps,
-                        int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha, float beta, int* status,
-                        cudaStream_t st, const DeviceSetup& dv) {
+cudaError_t launch_pair(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int64_t W, int64_t aws,
+                        int64_t bws, int64_t Kp, int64_t kps, int64_t P, int64_t M, int64_t N, int64_t ldc,
+                        const GemmGroup& g, int* status, cudaStream_t st, const DeviceSetup& dv) {
   using CF = CfgF16P;
   CUtensorMap mAhi, mAlo, mBhi, mBlo;
   // each CTA copies its own 128 rows of A and its own 128-row half of the B tile
-  if (!make_map<CF>(&mAhi, Ahi, M, Kp, kps, P, BM) || !make_map<CF>(&mAlo, Alo, M, Kp, kps, P, BM) ||
-      !make_map<CF>(&mBhi, Bhi, N, Kp, kps, P, BN / 2) || !make_map<CF>(&mBlo, Blo, N, Kp, kps, P, BN / 2))
+  if (!make_map<CF>(&mAhi, Ahi, M, Kp, kps, P, W, aws, BM) || !make_map<CF>(&mAlo, Alo, M, Kp, kps, P, W, aws, BM) ||
+      !make_map<CF>(&mBhi, Bhi, N, Kp, kps, P, W, bws, BN / 2) ||
+      !make_map<CF>(&mBlo, Blo, N, Kp, kps, P, W, bws, BN / 2))
     return cudaErrorInvalidValue;
-  const int64_t pairs = ((M + 2 * BM - 1) / (2 * BM)) * ((N + BN - 1) / BN);
+  const int64_t pairs = g.nprob * ((M + 2 * BM - 1) / (2 * BM)) * ((N + BN - 1) / BN);
   int grid = dv.pair_grid;
   if (grid / 2 > pairs) grid = (int)(2 * pairs);
   cudaLaunchConfig_t cfg = {};
@@ -804,46 +817,51 @@ cudaError_t launch_pair(const void* Ahi, const void* Alo, const void* Bhi, const
   cfg.stream = st;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, gemm_pair_kernel<CF>, mAhi, mAlo, mBhi, mBlo, C, ldc, (int)M, (int)N, (int)Kp,
-                            (int)P, alpha, beta, status);
+  return cudaLaunchKernelEx(&cfg, gemm_pair_kernel<CF>, mAhi, mAlo, mBhi, mBlo, g, ldc, (int)M, (int)N, (int)Kp,
+                            (int)P, status);
 }
 
 }  // namespace tc
 
-// C[M][N] (ldc) = alpha * A B^T + beta * C with A, B in K panels (see tma_load): panel
-// width Kp (kps = its stride), P panels, K = P Kp. P = 1, kps = ld is the plain row-major
-// K-major layout. variant 0 (default): tf32, k-blocks of 16, 64-byte swizzle, 4 stages;
-// variant 1: tf32, k-blocks of 32, 128-byte swizzle, 2 stages; variant 2: fp16 operands
-// (hi/lo planes of __half), k-blocks of 32, 64-byte swizzle, 4 stages, 128-k promotion
-// chunks (kps % 8 == 0); variant 3: as 2 with 64-k chunks; variant 4: as 2 with 256-k chunks;
-// variant 5: fp16 in CTA pairs (tcgen05.mma.cta_group::2, 256 x 256 tiles), 128-k chunks.
-cudaError_t launch_gemm_tf32x3_v(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int64_t Kp,
-                                 int64_t kps, int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha,
-                                 float beta, int* status, cudaStream_t st, int variant) {
+// Every output of the group g: C_p[M][N] (row stride ldc) = alpha_p * sum over its segments
+// s of A_{a_s} B_{b_s}^T, with the W operand tensors of each plane in K panels (see
+// tma_load): panel width Kp (kps = its stride), P panels, K = P Kp per segment; tensor w of
+// a plane starts aws (A) or bws (B) elements after tensor w - 1. variant 0:
+// tf32, k-blocks of 16, 64-byte swizzle, 4 stages; 1: tf32, k-blocks of 32, 128-byte
+// swizzle, 2 stages; 2: fp16 operands (hi/lo planes of __half), k-blocks of 32, 64-byte
+// swizzle, 4 stages, 128-k promotion chunks (kps % 8 == 0); 3: as 2 with 64-k chunks; 4: as
+// 2 with 256-k chunks; 5: fp16 in CTA pairs (tcgen05.mma.cta_group::2, 256 x 256 tiles),
+// k-blocks of 64 (kps % 64 == 0), 128-k chunks.
+cudaError_t launch_gemm_group(const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int W, int64_t aws,
+                              int64_t bws, int64_t Kp, int64_t kps, int64_t P, int64_t M, int64_t N, int64_t ldc,
+                              const GemmGroup& g, int* status, cudaStream_t st, int variant) {
   using namespace tc;
-  if (M <= 0 || N <= 0) return cudaSuccess;
-  if (Kp <= 0 || P <= 0 || M > 0x7fffffff || N > 0x7fffffff || Kp * P > 0x7fffffff) return cudaErrorInvalidValue;
+  if (M <= 0 || N <= 0 || g.nprob == 0) return cudaSuccess;
+  if (Kp <= 0 || P <= 0 || W < 1 || M > 0x7fffffff || N > 0x7fffffff || Kp * P > 0x7fffffff || ldc < N ||
+      g.nprob < 0 || g.nprob > kMaxGemmProblems || (W > 1 && (aws < P * M * kps || bws < P * N * kps)))
+    return cudaErrorInvalidValue;
+  for (int q = 0; q < g.nprob; ++q) {
+    const GemmProblem& pr = g.p[q];
+    if (!pr.C || pr.nseg < 1 || pr.nseg > 2) return cudaErrorInvalidValue;
+    for (int sg = 0; sg < pr.nseg; ++sg)
+      if (pr.a[sg] < 0 || pr.a[sg] >= W || pr.b[sg] < 0 || pr.b[sg] >= W) return cudaErrorInvalidValue;
+  }
   const bool f16 = variant >= 2 && variant <= 5;
-  if ((kps & (f16 ? 7 : 3)) || kps < Kp) return cudaErrorInvalidValue;
+  if ((kps & (variant == 5 ? 63 : (f16 ? 7 : 3))) || kps < Kp) return cudaErrorInvalidValue;
   if ((((uintptr_t)Ahi) | ((uintptr_t)Alo) | ((uintptr_t)Bhi) | ((uintptr_t)Blo)) & 15) return cudaErrorInvalidValue;
   const DeviceSetup* dv = device_setup();
   if (!dv) return cudaErrorInitializationError;
   if (variant == 5) {
     // a device (or partition) that cannot co-schedule two-CTA clusters runs the same
     // products on single CTAs
-    if (dv->pair_grid >= 2)
-      return launch_pair(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st, *dv);
-    return launch_single<CfgF16>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st, *dv);
+    if (dv->pair_grid >= 2) return launch_pair(Ahi, Alo, Bhi, Blo, W, aws, bws, Kp, kps, P, M, N, ldc, g, status, st, *dv);
+    return launch_single<CfgF16>(Ahi, Alo, Bhi, Blo, W, aws, bws, Kp, kps, P, M, N, ldc, g, status, st, *dv);
   }
-  if (variant == 4)
-    return launch_single<CfgF16L>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st, *dv);
-  if (variant == 3)
-    return launch_single<CfgF16S>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st, *dv);
-  if (variant == 2)
-    return launch_single<CfgF16>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st, *dv);
-  if (variant == 1)
-    return launch_single<CfgTF32W>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st, *dv);
-  return launch_single<CfgTF32>(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st, *dv);
+  if (variant == 4) return launch_single<CfgF16L>(Ahi, Alo, Bhi, Blo, W, aws, bws, Kp, kps, P, M, N, ldc, g, status, st, *dv);
+  if (variant == 3) return launch_single<CfgF16S>(Ahi, Alo, Bhi, Blo, W, aws, bws, Kp, kps, P, M, N, ldc, g, status, st, *dv);
+  if (variant == 2) return launch_single<CfgF16>(Ahi, Alo, Bhi, Blo, W, aws, bws, Kp, kps, P, M, N, ldc, g, status, st, *dv);
+  if (variant == 1) return launch_single<CfgTF32W>(Ahi, Alo, Bhi, Blo, W, aws, bws, Kp, kps, P, M, N, ldc, g, status, st, *dv);
+  return launch_single<CfgTF32>(Ahi, Alo, Bhi, Blo, W, aws, bws, Kp, kps, P, M, N, ldc, g, status, st, *dv);
 }
 
 // Sets the kernels' shared-memory attributes and caches the SM count and pair grid of the
@@ -854,13 +872,6 @@ void gemm_prepare() { tc::device_setup(); }
 cudaError_t launch_wait_selftest(int* status, unsigned long long limit_ns, cudaStream_t st) {
   tc::wait_selftest_kernel<<<1, 32, 0, st>>>(status, limit_ns);
   return cudaGetLastError();
-}
-
-cudaError_t launch_gemm_tf32x3(const float* Ahi, const float* Alo, const float* Bhi, const float* Blo, int64_t Kp,
-                               int64_t kps, int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha,
-                               float beta, int* status, cudaStream_t st) {
-  // plain tf32 entry: pipeline variant 0
-  return launch_gemm_tf32x3_v(Ahi, Alo, Bhi, Blo, Kp, kps, P, C, ldc, M, N, alpha, beta, status, st, 0);
 }
 
 }  // namespace hotrg

@@ -8,11 +8,15 @@
 //   G[(a1 a2),(b1 b2)] = sum_{k,k'} A1[(a1,k),(b1,k')] A2[(a2,k),(b2,k')].
 // gram_kernel computes 64x64 tiles of one half-Gram over one chunk of the summed index
 // (split-K: K = D^6 is long, R = D_l D_mu is short), products in the storage precision
-// summed per 32-term slice, the slice sums accumulated exactly: in FP64 for FP64 tensors,
-// for FP32 ones as an unevaluated pair of floats (hi + lo, Knuth's TwoSum), which carries
-// about 48 bits without the FP64 pipe (a few FP64 operations per clock per SM on this
-// chip, against 128 FP32 FMAs). gram_reduce adds the chunks of every job in a fixed order
-// (deterministic, one launch); gram_merge forms G in FP64.
+// summed per 32-term slice with FMA, then the slice sums accumulated: in FP64 for FP64
+// tensors, for FP32 ones as an unevaluated pair of floats (hi + lo, Knuth's TwoSum) that
+// adds them without a further rounding and without the FP64 pipe (a few FP64 operations
+// per clock per SM on this chip, against 128 FP32 FMAs). For FP32 tensors each slice sum
+// is therefore rounded once in FP32 (2^-24 of the slice's magnitude), and a Gram entry's
+// error is bounded by 2^-24 times the sum of its slices' magnitudes, whatever K is, where
+// one FP32 running sum over K = D^6 terms would add an error that grows with K.
+// gram_reduce adds the chunks of every job in a fixed order (deterministic, one launch);
+// gram_merge forms G in FP64.
 #include <type_traits>
 
 #include "common.cuh"
@@ -32,15 +36,17 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) gram_kernel(const __grid_constant__ GramPack jobs, int Rmax, int nchunks) {
-  const GramJob& jb = jobs.j[blockIdx.z];
+__global__ void __launch_bounds__(256) gram_kernel(const __grid_constant__ GramPack jobs, int njobs, int Rmax,
+                                                   int nchunks) {
+  const int bidx = blockIdx.z / njobs;        // batch element
+  const GramJob& jb = jobs.j[blockIdx.z - bidx * njobs];
   const int Rn = jb.D1 * jb.D2;
   const int ntile = (Rn + kGT - 1) / kGT;
   const int ti = blockIdx.y / ((Rmax + kGT - 1) / kGT);
   const int tj = blockIdx.y % ((Rmax + kGT - 1) / kGT);
   if (ti >= ntile || tj >= ntile) return;
   const bool diag = ti == tj;                 // both operand tiles are the same rows
-  const R* T = (const R*)jb.T;
+  const R* T = (const R*)jb.T + bidx * jobs.sT;
   const int64_t kchunk = (jb.K + nchunks - 1) / nchunks;
   const int64_t k0 = blockIdx.x * kchunk;
   const int64_t k1 = min(jb.K, k0 + kchunk);
@@ -116,7 +122,7 @@ __global__ void __launch_bounds__(256) gram_kernel(const __grid_constant__ GramP
   // on a diagonal tile only the blocks ty <= tx were summed; the block (ty, tx) also gives
   // (tx, ty) as its transpose (the same products in the same order: bit-identical)
   if (diag && ty > tx) return;
-  double* out = jb.partial + (int64_t)blockIdx.x * Rn * Rn;
+  double* out = jb.partial + bidx * jobs.sPart + (int64_t)blockIdx.x * Rn * Rn;
   for (int a = 0; a < 4; ++a) {
     const int i = ti * kGT + ty * 4 + a;
     if (i >= Rn) continue;
@@ -133,20 +139,23 @@ __global__ void __launch_bounds__(256) gram_kernel(const __grid_constant__ GramP
 template <typename R>
 cudaError_t launch_gram(const GramPack& jobs, int njobs, int Rmax, int nchunks, cudaStream_t st) {
   const int nt = (Rmax + kGT - 1) / kGT;
-  dim3 grid(nchunks, nt * nt, njobs);
-  gram_kernel<R><<<grid, 256, 0, st>>>(jobs, Rmax, nchunks);
+  dim3 grid(nchunks, nt * nt, njobs * jobs.batch);
+  gram_kernel<R><<<grid, 256, 0, st>>>(jobs, njobs, Rmax, nchunks);
   return cudaGetLastError();
 }
 template cudaError_t launch_gram<double>(const GramPack&, int, int, int, cudaStream_t);
 template cudaError_t launch_gram<float>(const GramPack&, int, int, int, cudaStream_t);
 
-// out_i[e] = sum_c partial_i[c][e] for every job i of the pack, in one launch. A block
-// takes 32 consecutive entries of one job; its 8 warps add interleaved chunk subsets
-// (warp w: chunks c = w mod 8, in increasing c) and the 8 warp sums are added in warp
-// order, so the result does not depend on scheduling.
-__global__ void __launch_bounds__(256) gram_reduce_kernel(const __grid_constant__ GramPack jobs, int nchunks,
-                                                          int64_t out_stride, double* __restrict__ out) {
-  const GramJob& jb = jobs.j[blockIdx.y];
+// out_i[e] = sum_c partial_i[c][e] for every job i of the pack (and batch element), in one
+// launch; job i of element b goes to out[(b njobs + i) out_stride]. A block takes 32
+// consecutive entries of one job; its 8 warps add interleaved chunk subsets (warp w: chunks
+// c = w mod 8, in increasing c) and the 8 warp sums are added in warp order, so the result
+// does not depend on scheduling.
+__global__ void __launch_bounds__(256) gram_reduce_kernel(const __grid_constant__ GramPack jobs, int njobs,
+                                                          int nchunks, int64_t out_stride, double* __restrict__ out) {
+  const int bidx = blockIdx.y / njobs;
+  const GramJob& jb = jobs.j[blockIdx.y - bidx * njobs];
+  const double* partial = jb.partial + bidx * jobs.sPart;
   const int64_t RR = (int64_t)jb.D1 * jb.D2 * jb.D1 * jb.D2;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   __shared__ double red[8][32];
@@ -154,7 +163,7 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(const __grid_constant_
     const int64_t e = e0 + lane;
     double s = 0;
     if (e < RR)
-      for (int c = w; c < nchunks; c += 8) s += jb.partial[(int64_t)c * RR + e];
+      for (int c = w; c < nchunks; c += 8) s += partial[(int64_t)c * RR + e];
     red[w][lane] = s;
     __syncthreads();
     if (w == 0 && e < RR) {
@@ -170,7 +179,8 @@ cudaError_t launch_gram_reduce(const GramPack& jobs, int njobs, int nchunks, int
                                double* out, cudaStream_t st) {
   int64_t blocks = (RRmax + 31) / 32;
   if (blocks > 1024) blocks = 1024;
-  gram_reduce_kernel<<<dim3((unsigned)blocks, (unsigned)njobs), 256, 0, st>>>(jobs, nchunks, out_stride, out);
+  gram_reduce_kernel<<<dim3((unsigned)blocks, (unsigned)(njobs * jobs.batch)), 256, 0, st>>>(jobs, njobs, nchunks,
+                                                                                             out_stride, out);
   return cudaGetLastError();
 }
 
@@ -193,6 +203,38 @@ __global__ void gram_merge_kernel(const double* __restrict__ A1, const double* _
 cudaError_t launch_gram_merge(const double* A1, const double* A2, int Dn, int Dk, double* G, cudaStream_t st) {
   const int n2 = Dn * Dn * Dn * Dn;
   gram_merge_kernel<<<(n2 + 255) / 256, 256, 0, st>>>(A1, A2, Dn, Dk, G);
+  return cudaGetLastError();
+}
+
+// One launch for the six Gram matrices of every batch element: blockIdx.y = b * 6 + i * 2 +
+// side (same arithmetic and order as gram_merge_kernel).
+__global__ void gram_merge_batch_kernel(const double* __restrict__ half, int64_t RRs, int Dn0, int Dn1, int Dn2,
+                                        int Dk, double* __restrict__ G, int64_t nn) {
+  const int q = blockIdx.y % 6, bidx = blockIdx.y / 6;
+  const int i = q / 2;
+  const int Dn = i == 0 ? Dn0 : (i == 1 ? Dn1 : Dn2);
+  const double* A1 = half + ((int64_t)bidx * 12 + q * 2) * RRs;
+  const double* A2 = A1 + RRs;
+  double* Gq = G + ((int64_t)bidx * 6 + q) * nn;
+  const int n = Dn * Dn;
+  const int Rk = Dn * Dk;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+    const int row = e / n, col = e % n;
+    const int a1 = row / Dn, a2 = row % Dn, b1 = col / Dn, b2 = col % Dn;
+    double s = 0;
+    for (int k = 0; k < Dk; ++k)
+      for (int kp = 0; kp < Dk; ++kp)
+        s = fma(A1[(int64_t)(a1 * Dk + k) * Rk + b1 * Dk + kp], A2[(int64_t)(a2 * Dk + k) * Rk + b2 * Dk + kp], s);
+    Gq[e] = s;
+  }
+}
+
+cudaError_t launch_gram_merge_batch(const double* half, int64_t RRs, const int Dn[3], int Dk, double* G, int64_t nn,
+                                    int batch, cudaStream_t st) {
+  int nmax = 0;
+  for (int i = 0; i < 3; ++i) nmax = nmax > Dn[i] * Dn[i] ? nmax : Dn[i] * Dn[i];
+  const int blocks = (nmax * nmax + 255) / 256;
+  gram_merge_batch_kernel<<<dim3(blocks, 6 * batch), 256, 0, st>>>(half, RRs, Dn[0], Dn[1], Dn[2], Dk, G, nn);
   return cudaGetLastError();
 }
 

@@ -20,17 +20,12 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
 #include "common.cuh"
 #include "hotrg.h"
-
-namespace hotrg {
-cudaError_t launch_gemm_tf32x3(const float* Ahi, const float* Alo, const float* Bhi, const float* Blo, int64_t Kp,
-                               int64_t kps, int64_t P, float* C, int64_t ldc, int64_t M, int64_t N, float alpha,
-                               float beta, int* status, cudaStream_t st);
-}
 
 using namespace hotrg;
 
@@ -65,6 +60,9 @@ struct StepPlan {
   // Gram
   int R[4];               // rows of the half-Gram per direction = D_nu D_mu
   int Rmax, nmax, nchunks;
+  int batch;              // batch elements whose isometry stages run together
+  int gemm_opt;           // tensor-core GEMM pipeline option of this step (-1: the context's)
+  bool tuned;             // closing direction and pipeline taken from the autotuner's cache
   double main_flops, total_flops;
 };
 
@@ -102,6 +100,12 @@ struct hotrg_ctx {
   int jacobi_sweeps = kJacobiMaxSweeps;
   int gemm_variant = 0;
   bool use_graphs = false;
+  bool autotune = false;
+  int c_hist[kMaxSteps];       // closing direction of each step
+  int opt_hist[kMaxSteps];     // GEMM pipeline option of each step (-1: CUDA cores)
+  int tuned_hist[kMaxSteps];   // plan from the autotuner's cache
+  uint64_t tune_timed = 0;     // step shapes timed by this context
+  uint64_t tune_hits = 0;      // steps whose plan came from the cache
   struct GraphEntry {
     cudaGraphExec_t exec;
     uint64_t launches;
@@ -138,9 +142,6 @@ hotrg_status cuda_fail(hotrg_ctx* ctx, cudaError_t e, const char* where) {
     if (e__ != cudaSuccess) return cuda_fail(ctx, e__, where); \
   } while (0)
 
-template <typename R>
-hotrg_status gemm_launch(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R* Blo, const StepPlan& p, R* C,
-                         int64_t M, int64_t N, double alpha, double beta, cudaStream_t st);
 
 // A launcher call that issues `n` kernels.
 #define LK(n, call, where)                                \
@@ -201,9 +202,13 @@ double plan_main_flops(const int D[4], const int chi[4], int mu, int a, int b, i
   return 2.0 * rows * rows * K;
 }
 
-StepPlan make_plan(const int D[4], int mu, int dcut, int prec) {
+// force_c >= 0 (a transverse direction) fixes the closing direction; otherwise the one
+// with the fewest flops is taken.
+StepPlan make_plan(const int D[4], int mu, int dcut, int prec, int batch = 1, int force_c = -1) {
   StepPlan p{};
   p.mu = mu;
+  p.batch = batch;
+  p.gemm_opt = -1;
   for (int n = 0; n < 4; ++n) {
     p.D[n] = D[n];
     p.chi[n] = (n == mu) ? D[n] : std::min(D[n] * D[n], dcut);
@@ -221,7 +226,7 @@ StepPlan make_plan(const int D[4], int mu, int dcut, int prec) {
     for (int j = 0; j < 3; ++j)
       if (j != i) ab[q++] = tr[j];
     const double f = plan_main_flops(D, p.chi, mu, ab[0], ab[1], c);
-    if (best < 0 || f <= best) {
+    if (force_c >= 0 ? c == force_c : (best < 0 || f <= best)) {
       best = f;
       bc = c;
     }
@@ -273,8 +278,8 @@ StepPlan make_plan(const int D[4], int mu, int dcut, int prec) {
   int64_t nc = (Kg + 511) / 512;
   if (nc > 256) nc = 256;
   if (nc < 1) nc = 1;
-  // keep the split-K partials under 256 MB
-  const int64_t per = (int64_t)kMaxGramJobs * p.Rmax * p.Rmax * 8;
+  // keep the split-K partials of all batch elements under 256 MB
+  const int64_t per = (int64_t)batch * kMaxGramJobs * p.Rmax * p.Rmax * 8;
   while (nc > 1 && nc * per > (256LL << 20)) nc /= 2;
   p.nchunks = (int)nc;
   p.main_flops = best;
@@ -308,15 +313,17 @@ Scratch scratch_layout(const StepPlan& p, int xs, int xs2, int prec, int impure,
     return o;
   };
   const int nt = ntensors(impure);
-  s.gpart = take((size_t)kMaxGramJobs * p.nchunks * p.Rmax * p.Rmax * 8);
+  // isometry stage: one copy per batch element (all elements run it together)
+  const size_t nb = (size_t)p.batch;
+  s.gpart = take(nb * kMaxGramJobs * p.nchunks * p.Rmax * p.Rmax * 8);
   s.npart = take((size_t)kNormPartials * 8);
-  s.gA = take((size_t)kMaxGramJobs * p.Rmax * p.Rmax * 8);
-  s.G = take((size_t)6 * p.nmax * p.nmax * 8);
-  s.jwork = take((size_t)6 * 2 * p.nmax * p.nmax * 8);
-  s.lam = take((size_t)6 * p.nmax * 8);
-  s.eps = take(6 * 8);
-  s.degen = take(6 * 4);
-  s.Uside = take((size_t)6 * p.nmax * kMaxLeg * 8);
+  s.gA = take(nb * kMaxGramJobs * p.Rmax * p.Rmax * 8);
+  s.G = take(nb * 6 * p.nmax * p.nmax * 8);
+  s.jwork = take(p.nmax > kJacobiSmemN ? nb * 6 * 2 * p.nmax * p.nmax * 8 : 0);
+  s.lam = take(nb * 6 * p.nmax * 8);
+  s.eps = take(nb * 6 * 8);
+  s.degen = take(nb * 6 * 4);
+  s.Uside = take(nb * 6 * p.nmax * kMaxLeg * 8);
   const int64_t rowsA = (int64_t)xs * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[p.mu];
   const int64_t rowsB = (int64_t)xs2 * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[p.mu];
   const bool split = tc_mode(prec);
@@ -617,31 +624,44 @@ hotrg_status close_C(hotrg_ctx* ctx, const StepPlan& p, const R* C, const R* Uc,
   return HOTRG_OK;
 }
 
-template <typename R>
-hotrg_status gemm(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R* Blo, const StepPlan& p, R* C,
-                  int64_t M, int64_t N, double alpha, double beta, cudaStream_t st) {
-  const int64_t K = p.K;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (ctx->profiling && !ctx->use_graphs) {
+// Records a profiling event pair around one GEMM launch (eager steps only).
+struct GemmTimer {
+  hotrg_ctx* ctx;
+  cudaStream_t st;
+  cudaEvent_t e1 = nullptr;
+  hotrg_status start() {
+    if (!ctx->profiling || ctx->use_graphs) return HOTRG_OK;
     while (ctx->ev.size() < ctx->ev_used + 2) {
       cudaEvent_t e;
       CK(cudaEventCreate(&e), "event create");
       ctx->ev.push_back(e);
     }
-    e0 = ctx->ev[ctx->ev_used];
+    cudaEvent_t e0 = ctx->ev[ctx->ev_used];
     e1 = ctx->ev[ctx->ev_used + 1];
     ctx->ev_used += 2;
     CK(cudaEventRecord(e0, st), "event record");
+    return HOTRG_OK;
   }
-  hotrg_status r = gemm_launch<R>(ctx, A, Alo, B, Blo, p, C, M, N, alpha, beta, st);
-  if (r != HOTRG_OK) return r;
-  ctx->launches += 1;
-  if (ctx->profiling && !ctx->use_graphs) {
+  hotrg_status stop(double flops) {
+    ctx->launches += 1;
+    if (!e1) return HOTRG_OK;
     CK(cudaEventRecord(e1, st), "event record");
     ctx->gemm_launches += 1;
-    ctx->gemm_flops += 2.0 * (double)M * (double)N * (double)K;
+    ctx->gemm_flops += flops;
+    return HOTRG_OK;
   }
-  return HOTRG_OK;
+};
+
+// CUDA-core GEMM (FP64 and FP32 modes): C = alpha A B^T + beta C, one product per launch.
+template <typename R>
+hotrg_status gemm_simt(hotrg_ctx* ctx, const R* A, const R* B, const StepPlan& p, R* C, int64_t M, int64_t N,
+                       double alpha, double beta, cudaStream_t st) {
+  if (p.P != 1) return HOTRG_EUNSUPPORTED;
+  GemmTimer tm{ctx, st};
+  hotrg_status r = tm.start();
+  if (r != HOTRG_OK) return r;
+  CK(launch_gemm_simt<R>(A, p.kps, B, p.kps, C, N, M, N, p.K, alpha, beta, st), "gemm simt");
+  return tm.stop(2.0 * (double)M * (double)N * (double)p.K);
 }
 
 // FP16X3 pipelines by option value: 0 = CTA pairs (tcgen05.mma.cta_group::2, 256 x 256 tiles),
@@ -649,34 +669,160 @@ hotrg_status gemm(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R*
 // 128-k chunks.
 constexpr int kF16Variant[4] = {5, 3, 4, 2};
 
+// Tensor-core modes: every output of the group in one launch. The W operand tensors of a
+// plane start Asz / Bsz operand elements apart.
+hotrg_status gemm_tc(hotrg_ctx* ctx, const void* A, const void* Alo, const void* B, const void* Blo, int W,
+                     int64_t Asz, int64_t Bsz, const StepPlan& p, const GemmGroup& g, int64_t M, int64_t N,
+                     cudaStream_t st) {
+  GemmTimer tm{ctx, st};
+  hotrg_status r = tm.start();
+  if (r != HOTRG_OK) return r;
+  const int opt = p.gemm_opt >= 0 ? p.gemm_opt : ctx->gemm_variant;
+  const int variant = ctx->prec == HOTRG_FP16X3 ? kF16Variant[opt] : opt;
+  CK(launch_gemm_group(A, Alo, B, Blo, W, Asz, Bsz, p.Kp, p.kps, p.P, M, N, N, g, (int*)(ctx->ws + ctx->L.status),
+                       st, variant),
+     ctx->prec == HOTRG_FP16X3 ? "gemm f16x3" : "gemm tf32x3");
+  double segs = 0;
+  for (int q = 0; q < g.nprob; ++q) segs += g.p[q].nseg;
+  return tm.stop(2.0 * (double)M * (double)N * (double)p.K * segs);
+}
+
+// Step 1 and 2 for every batch element in one set of launches: Gram halves (12 split-K
+// jobs per element), chunk reduction, merge into the six Gram matrices, Jacobi (six
+// matrices per element) and the side choice with Gram-Schmidt (three directions per
+// element). The isometries land in each element's persistent slot (L.U64, L.Ur).
 template <typename R>
-hotrg_status gemm_launch(hotrg_ctx* ctx, const R* A, const R* Alo, const R* B, const R* Blo, const StepPlan& p, R* C,
-                         int64_t M, int64_t N, double alpha, double beta, cudaStream_t st) {
-  if (ctx->prec == HOTRG_TF32X3) {
-    CK(launch_gemm_tf32x3_v(A, Alo, B, Blo, p.Kp, p.kps, p.P, (float*)C, N, M, N, (float)alpha, (float)beta,
-                            (int*)(ctx->ws + ctx->L.status), st, ctx->gemm_variant),
-       "gemm tf32x3");
-  } else if (ctx->prec == HOTRG_FP16X3) {
-    // operands carry the factor 2^14 each
-    const float unscale = 1.0f / (kF16Scale * kF16Scale);
-    CK(launch_gemm_tf32x3_v(A, Alo, B, Blo, p.Kp, p.kps, p.P, (float*)C, N, M, N, (float)alpha * unscale,
-                            (float)beta, (int*)(ctx->ws + ctx->L.status), st, kF16Variant[ctx->gemm_variant]),
-       "gemm f16x3");
-  } else {
-    if (p.P != 1) return HOTRG_EUNSUPPORTED;
-    CK(launch_gemm_simt<R>(A, p.kps, B, p.kps, C, N, M, N, p.K, alpha, beta, st), "gemm simt");
+hotrg_status isometry_stage(hotrg_ctx* ctx, const StepPlan& p, const Scratch& sc, char* sb, cudaStream_t st) {
+  const int mu = p.mu;
+  const int nb = p.batch;
+  int* status = (int*)(ctx->ws + ctx->L.status);
+  const int* dstep = (const int*)(ctx->ws + ctx->L.step);
+  int64_t ts[8];
+  canon_strides(p.D, ts);
+  int dirs[3], nd = 0;
+  for (int n = 0; n < 4; ++n)
+    if (n != mu) dirs[nd++] = n;
+  // ---------------------------------------------------------------- 1. Gram
+  GramPack gp{};
+  int nj = 0;
+  double* gpart = (double*)(sb + sc.gpart);
+  double* gA = (double*)(sb + sc.gA);
+  const int64_t RR = (int64_t)p.Rmax * p.Rmax;
+  for (int i = 0; i < 3; ++i) {
+    const int n = dirs[i];
+    for (int side = 0; side < 2; ++side) {
+      for (int half = 0; half < 2; ++half) {   // half 0: k on mu' (T1), 1: k on mu (T2)
+        GramJob& j = gp.j[nj];
+        j.T = tensor_ptr<R>(ctx, 0, ctx->cur, 0);
+        const int leg = 2 * n + side;
+        const int kleg = half == 0 ? 2 * mu + 1 : 2 * mu;
+        j.D1 = p.D[n];
+        j.D2 = p.D[mu];
+        j.s1 = ts[leg];
+        j.s2 = ts[kleg];
+        j.nrest = 0;
+        j.K = 1;
+        for (int l = 0; l < 8; ++l) {
+          if (l == leg || l == kleg) continue;
+          j.rdims[j.nrest] = p.D[l / 2];
+          j.rst[j.nrest] = ts[l];
+          j.K *= p.D[l / 2];
+          ++j.nrest;
+        }
+        j.partial = gpart + (int64_t)nj * p.nchunks * RR;
+        ++nj;
+      }
+    }
   }
+  gp.batch = nb;
+  gp.sT = ctx->L.cap;                                   // tensor slots of consecutive elements
+  gp.sPart = (int64_t)kMaxGramJobs * p.nchunks * RR;
+  LK(1, launch_gram<R>(gp, nj, p.Rmax, p.nchunks, st), "gram");
+  LK(1, launch_gram_reduce(gp, nj, p.nchunks, RR, RR, gA, st), "gram reduce");
+  double* G = (double*)(sb + sc.G);
+  const int64_t nn = (int64_t)p.nmax * p.nmax;
+  const int Dn[3] = {p.D[dirs[0]], p.D[dirs[1]], p.D[dirs[2]]};
+  LK(1, launch_gram_merge_batch(gA, RR, Dn, p.D[mu], G, nn, nb, st), "gram merge");
+  // ---------------------------------------------------------------- 2. eigen + side
+  EigPack ep{};
+  double* lam = (double*)(sb + sc.lam);
+  double* eps = (double*)(sb + sc.eps);
+  int* degen = (int*)(sb + sc.degen);
+  double* Uside = (double*)(sb + sc.Uside);
+  double* jwork = (double*)(sb + sc.jwork);
+  const bool big = p.nmax > kJacobiSmemN;
+  int nmax = 0;
+  for (int i = 0; i < 3; ++i) {
+    for (int side = 0; side < 2; ++side) {
+      const int e = i * 2 + side;
+      EigJob& j = ep.j[e];
+      j.n = p.D[dirs[i]] * p.D[dirs[i]];
+      j.chi = p.chi[dirs[i]];
+      j.G = G + (int64_t)e * nn;
+      j.work = big ? jwork + (int64_t)e * 2 * nn : nullptr;
+      j.lam = lam + (int64_t)e * p.nmax;
+      j.eps = eps + e;
+      j.degenerate = degen + e;
+      j.U = Uside + (int64_t)e * p.nmax * kMaxLeg;
+      nmax = std::max(nmax, j.n);
+    }
+  }
+  ep.batch = nb;
+  ep.sG = 6 * nn;
+  ep.sWork = big ? 6 * 2 * nn : 0;
+  ep.sLam = 6 * (int64_t)p.nmax;
+  ep.sU = 6 * (int64_t)p.nmax * kMaxLeg;
+  ep.sEps = 6;
+  ep.sDeg = 6;
+  const bool fp64 = ctx->prec == HOTRG_FP64;
+  LK(1, launch_jacobi(ep, 6, nmax, fp64 ? 1e-10 : 1e-6, status, st, ctx->jacobi_sweeps, fp64 ? 1e-8 : 1e-4),
+     "jacobi");
+  SelectPack sp{};
+  double* U64 = (double*)(ctx->ws + ctx->L.U64);
+  R* Ur = (R*)(ctx->ws + ctx->L.Ur);
+  DevRecord* rec = (DevRecord*)(ctx->ws + ctx->L.rec);
+  for (int i = 0; i < 3; ++i) {
+    const int n = dirs[i];
+    SelectJob& j = sp.j[i];
+    j.U[0] = ep.j[i * 2].U;
+    j.U[1] = ep.j[i * 2 + 1].U;
+    j.lam0 = ep.j[i * 2].lam;
+    j.eps[0] = ep.j[i * 2].eps;
+    j.eps[1] = ep.j[i * 2 + 1].eps;
+    j.degen[0] = ep.j[i * 2].degenerate;
+    j.degen[1] = ep.j[i * 2 + 1].degenerate;
+    j.U64 = U64 + (int64_t)n * kMaxGramN * kMaxLeg;
+    j.Ur = Ur + (int64_t)n * kMaxGramN * kMaxLeg;
+    j.n = ep.j[i * 2].n;
+    j.chi = ep.j[i * 2].chi;
+    j.rec_eps = nullptr;
+    j.rec_primed = nullptr;
+    j.rec_degen = nullptr;
+    j.rec_b = rec;
+    j.step = dstep;
+    j.nu = n;
+  }
+  sp.batch = nb;
+  sp.sU = ep.sU;
+  sp.sLam = ep.sLam;
+  sp.sEps = ep.sEps;
+  sp.sDeg = ep.sDeg;
+  sp.sU64 = 4 * (int64_t)kMaxGramN * kMaxLeg;
+  sp.sUr = 4 * (int64_t)kMaxGramN * kMaxLeg;
+  sp.sRec = kMaxSteps;
+  LK(1, launch_select<R>(sp, 3, fp64 ? 1e-9 : 1e-6, st), "select");
   return HOTRG_OK;
 }
 
+// Step 3 for batch element bidx: the half contractions, the grouped block-spin GEMM and the
+// closing isometries, slice block by slice block, into the element's next tensors (not
+// yet normalised). Reads the element's isometries from its persistent slot.
 template <typename R>
-hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
-  cudaStream_t st = ctx->stream;
+hotrg_status contract_element(hotrg_ctx* ctx, const StepPlan& p, int bidx, cudaStream_t st) {
   const Scratch sc = scratch_layout(p, p.xs, p.xs2, ctx->prec, ctx->impure_active, ctx->rsize);
   char* sb = ctx->ws + ctx->L.persistent_end;
   const int mu = p.mu;
   const int kstep = ctx->k;  // steps done before this one
-  int* status = (int*)(ctx->ws + ctx->L.status);
   const int nt = ntensors(ctx->impure_active);
   const bool split = tc_mode(ctx->prec);
   const size_t osz = operand_size(ctx->prec);
@@ -684,110 +830,8 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
   const int64_t rowsB = (int64_t)p.xs2 * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[mu];
   const int ca = p.chi[p.a];
   const bool b_sliced = p.xs2 < ca;
-
-  for (int bidx = 0; bidx < ctx->batch; ++bidx) {
-    const R* T = tensor_ptr<R>(ctx, 0, ctx->cur, bidx);
-    DevRecord* rec_b = (DevRecord*)(ctx->ws + ctx->L.rec) + (int64_t)bidx * kMaxSteps;
-    const int* dstep = (const int*)(ctx->ws + ctx->L.step);
-    // ---------------------------------------------------------------- 1. Gram
-    int64_t ts[8];
-    canon_strides(p.D, ts);
-    GramPack gp{};
-    int nj = 0;
-    int dirs[3], nd = 0;
-    for (int n = 0; n < 4; ++n)
-      if (n != mu) dirs[nd++] = n;
-    double* gpart = (double*)(sb + sc.gpart);
-    double* gA = (double*)(sb + sc.gA);
-    for (int i = 0; i < 3; ++i) {
-      const int n = dirs[i];
-      for (int side = 0; side < 2; ++side) {
-        for (int half = 0; half < 2; ++half) {   // half 0: k on mu' (T1), 1: k on mu (T2)
-          GramJob& j = gp.j[nj];
-          j.T = T;
-          const int leg = 2 * n + side;
-          const int kleg = half == 0 ? 2 * mu + 1 : 2 * mu;
-          j.D1 = p.D[n];
-          j.D2 = p.D[mu];
-          j.s1 = ts[leg];
-          j.s2 = ts[kleg];
-          j.nrest = 0;
-          j.K = 1;
-          for (int l = 0; l < 8; ++l) {
-            if (l == leg || l == kleg) continue;
-            j.rdims[j.nrest] = p.D[l / 2];
-            j.rst[j.nrest] = ts[l];
-            j.K *= p.D[l / 2];
-            ++j.nrest;
-          }
-          j.partial = gpart + (int64_t)nj * p.nchunks * p.Rmax * p.Rmax;
-          ++nj;
-        }
-      }
-    }
-    LK(1, launch_gram<R>(gp, nj, p.Rmax, p.nchunks, st), "gram");
-    LK(1, launch_gram_reduce(gp, nj, p.nchunks, (int64_t)p.Rmax * p.Rmax, (int64_t)p.Rmax * p.Rmax, gA, st),
-       "gram reduce");
-    double* G = (double*)(sb + sc.G);
-    for (int i = 0; i < 3; ++i) {
-      for (int side = 0; side < 2; ++side) {
-        const int j1 = (i * 2 + side) * 2;
-        LK(1, launch_gram_merge(gA + (int64_t)j1 * p.Rmax * p.Rmax, gA + (int64_t)(j1 + 1) * p.Rmax * p.Rmax,
-                             p.D[dirs[i]], p.D[mu], G + (int64_t)(i * 2 + side) * p.nmax * p.nmax, st),
-           "gram merge");
-      }
-    }
-    // ---------------------------------------------------------------- 2. eigen + side
-    EigPack ep{};
-    double* lam = (double*)(sb + sc.lam);
-    double* eps = (double*)(sb + sc.eps);
-    int* degen = (int*)(sb + sc.degen);
-    double* Uside = (double*)(sb + sc.Uside);
-    double* jwork = (double*)(sb + sc.jwork);
-    int nmax = 0;
-    for (int i = 0; i < 3; ++i) {
-      for (int side = 0; side < 2; ++side) {
-        const int e = i * 2 + side;
-        EigJob& j = ep.j[e];
-        j.n = p.D[dirs[i]] * p.D[dirs[i]];
-        j.chi = p.chi[dirs[i]];
-        j.G = G + (int64_t)e * p.nmax * p.nmax;
-        j.work = jwork + (int64_t)e * 2 * p.nmax * p.nmax;
-        j.lam = lam + (int64_t)e * p.nmax;
-        j.eps = eps + e;
-        j.degenerate = degen + e;
-        j.U = Uside + (int64_t)e * p.nmax * kMaxLeg;
-        nmax = std::max(nmax, j.n);
-      }
-    }
-    const bool fp64 = ctx->prec == HOTRG_FP64;
-    LK(1, launch_jacobi(ep, 6, nmax, fp64 ? 1e-10 : 1e-6, status, st, ctx->jacobi_sweeps, fp64 ? 1e-8 : 1e-4),
-       "jacobi");
-    SelectPack sp{};
-    double* U64 = (double*)(ctx->ws + ctx->L.U64) + (int64_t)bidx * 4 * kMaxGramN * kMaxLeg;
+  {
     R* Ur = (R*)(ctx->ws + ctx->L.Ur) + (int64_t)bidx * 4 * kMaxGramN * kMaxLeg;
-    for (int i = 0; i < 3; ++i) {
-      const int n = dirs[i];
-      SelectJob& j = sp.j[i];
-      j.U[0] = ep.j[i * 2].U;
-      j.U[1] = ep.j[i * 2 + 1].U;
-      j.lam0 = ep.j[i * 2].lam;
-      j.eps[0] = ep.j[i * 2].eps;
-      j.eps[1] = ep.j[i * 2 + 1].eps;
-      j.degen[0] = ep.j[i * 2].degenerate;
-      j.degen[1] = ep.j[i * 2 + 1].degenerate;
-      j.U64 = U64 + (int64_t)n * kMaxGramN * kMaxLeg;
-      j.Ur = Ur + (int64_t)n * kMaxGramN * kMaxLeg;
-      j.n = ep.j[i * 2].n;
-      j.chi = ep.j[i * 2].chi;
-      j.rec_eps = nullptr;
-      j.rec_primed = nullptr;
-      j.rec_degen = nullptr;
-      j.rec_b = rec_b;
-      j.step = dstep;
-      j.nu = n;
-    }
-    LK(1, launch_select<R>(sp, 3, fp64 ? 1e-9 : 1e-6, st), "select");
     const R* Ua = Ur + (int64_t)p.a * kMaxGramN * kMaxLeg;
     const R* Ub = Ur + (int64_t)p.b * kMaxGramN * kMaxLeg;
     const R* Uc = Ur + (int64_t)p.c * kMaxGramN * kMaxLeg;
@@ -838,29 +882,43 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
           hotrg_status s = buildB(x20, xs2);
           if (s != HOTRG_OK) return s;
         }
-        auto Ap = [&](int w) { return opnd(Abuf, w * Asz); };
-        auto Alp = [&](int w) { return opnd(Alob, w * Asz); };
-        auto Bp = [&](int w) { return opnd(Bbuf, w * Bsz); };
-        auto Blp = [&](int w) { return opnd(Blob, w * Bsz); };
         hotrg_status s;
-        // C_T = A(T) B(T)^T
-        s = gemm<R>(ctx, Ap(0), Alp(0), Bp(0), Blp(0), p, Cbuf, rA, rB, 1.0, 0.0, st);
-        if (s != HOTRG_OK) return s;
-        if (nt >= 2) {  // C_S = (A(S) B(T)^T + A(T) B(S)^T) / 2
-          s = gemm<R>(ctx, Ap(1), Alp(1), Bp(0), Blp(0), p, Cbuf + Csz, rA, rB, 0.5, 0.0, st);
+        if (split) {
+          // every output of the block in one launch: C_T = A_T B_T^T, C_S = (A_S B_T^T + A_T B_S^T) / 2,
+          // and M_1 = A_S B_S^T (the nearest-neighbour pair inside the first block) or
+          // C_M = (A_M B_T^T + A_T B_M^T) / 2; fp16 operands carry the factor 2^14 each
+          const double un = ctx->prec == HOTRG_FP16X3 ? 1.0 / ((double)kF16Scale * kF16Scale) : 1.0;
+          GemmGroup g{};
+          g.nprob = nt;
+          g.p[0] = GemmProblem{(float*)Cbuf, (float)un, 1, {0, 0}, {0, 0}};
+          if (nt >= 2) g.p[1] = GemmProblem{(float*)(Cbuf + Csz), (float)(0.5 * un), 2, {1, 0}, {0, 1}};
+          if (nt >= 3)
+            g.p[2] = kstep == 0 ? GemmProblem{(float*)(Cbuf + 2 * Csz), (float)un, 1, {1, 0}, {1, 0}}
+                                : GemmProblem{(float*)(Cbuf + 2 * Csz), (float)(0.5 * un), 2, {2, 0}, {0, 2}};
+          s = gemm_tc(ctx, Abuf, Alob, Bbuf, Blob, nt, Asz, Bsz, p, g, rA, rB, st);
           if (s != HOTRG_OK) return s;
-          s = gemm<R>(ctx, Ap(0), Alp(0), Bp(1), Blp(1), p, Cbuf + Csz, rA, rB, 0.5, 1.0, st);
+        } else {
+          auto Ap = [&](int w) { return opnd(Abuf, w * Asz); };
+          auto Bp = [&](int w) { return opnd(Bbuf, w * Bsz); };
+          // C_T = A(T) B(T)^T
+          s = gemm_simt<R>(ctx, Ap(0), Bp(0), p, Cbuf, rA, rB, 1.0, 0.0, st);
           if (s != HOTRG_OK) return s;
-        }
-        if (nt >= 3) {
-          if (kstep == 0) {  // M_1 = A(S) B(S)^T: the nearest-neighbour pair inside the first block
-            s = gemm<R>(ctx, Ap(1), Alp(1), Bp(1), Blp(1), p, Cbuf + 2 * Csz, rA, rB, 1.0, 0.0, st);
+          if (nt >= 2) {  // C_S = (A(S) B(T)^T + A(T) B(S)^T) / 2
+            s = gemm_simt<R>(ctx, Ap(1), Bp(0), p, Cbuf + Csz, rA, rB, 0.5, 0.0, st);
             if (s != HOTRG_OK) return s;
-          } else {           // M' = (A(M) B(T)^T + A(T) B(M)^T) / 2
-            s = gemm<R>(ctx, Ap(2), Alp(2), Bp(0), Blp(0), p, Cbuf + 2 * Csz, rA, rB, 0.5, 0.0, st);
+            s = gemm_simt<R>(ctx, Ap(0), Bp(1), p, Cbuf + Csz, rA, rB, 0.5, 1.0, st);
             if (s != HOTRG_OK) return s;
-            s = gemm<R>(ctx, Ap(0), Alp(0), Bp(2), Blp(2), p, Cbuf + 2 * Csz, rA, rB, 0.5, 1.0, st);
-            if (s != HOTRG_OK) return s;
+          }
+          if (nt >= 3) {
+            if (kstep == 0) {  // M_1 = A(S) B(S)^T: the nearest-neighbour pair inside the first block
+              s = gemm_simt<R>(ctx, Ap(1), Bp(1), p, Cbuf + 2 * Csz, rA, rB, 1.0, 0.0, st);
+              if (s != HOTRG_OK) return s;
+            } else {           // M' = (A(M) B(T)^T + A(T) B(M)^T) / 2
+              s = gemm_simt<R>(ctx, Ap(2), Bp(0), p, Cbuf + 2 * Csz, rA, rB, 0.5, 0.0, st);
+              if (s != HOTRG_OK) return s;
+              s = gemm_simt<R>(ctx, Ap(0), Bp(2), p, Cbuf + 2 * Csz, rA, rB, 0.5, 1.0, st);
+              if (s != HOTRG_OK) return s;
+            }
           }
         }
         for (int w = 0; w < nt; ++w) {
@@ -869,7 +927,27 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
         }
       }
     }
+  }
+  return HOTRG_OK;
+}
+
+template <typename R>
+hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
+  cudaStream_t st = ctx->stream;
+  const Scratch sc = scratch_layout(p, p.xs, p.xs2, ctx->prec, ctx->impure_active, ctx->rsize);
+  char* sb = ctx->ws + ctx->L.persistent_end;
+  int* status = (int*)(ctx->ws + ctx->L.status);
+  const int nt = ntensors(ctx->impure_active);
+  const int* dstep = (const int*)(ctx->ws + ctx->L.step);
+  hotrg_status s = isometry_stage<R>(ctx, p, sc, sb, st);
+  if (s != HOTRG_OK) return s;
+  for (int bidx = 0; bidx < ctx->batch; ++bidx) {
+    s = contract_element<R>(ctx, p, bidx, st);
+    if (s != HOTRG_OK) return s;
     // ---------------------------------------------------------------- 4. normalise
+    DevRecord* rec_b = (DevRecord*)(ctx->ws + ctx->L.rec) + (int64_t)bidx * kMaxSteps;
+    R* dst[3];
+    for (int w = 0; w < nt; ++w) dst[w] = tensor_ptr<R>(ctx, w, 1 - ctx->cur, bidx);
     double* lnz = (double*)(ctx->ws + ctx->L.lnz) + bidx;
     double* cval = (double*)(ctx->ws + ctx->L.cval) + bidx;
     LK(2, launch_norm<R>(dst[0], p.Enew, (double*)(sb + sc.npart), dstep, cval, lnz, rec_b, status, st), "norm");
@@ -895,6 +973,125 @@ hotrg_status sync_and_status(hotrg_ctx* ctx) {
   else if (st[kStNonFinite]) ctx->sticky = HOTRG_ENONFINITE;
   else if (st[kStNoConv]) ctx->sticky = HOTRG_ENOCONV;
   return ctx->sticky ? (hotrg_status)ctx->sticky : HOTRG_OK;
+}
+
+// Slice sizes (X for A and C rows, X' for B rows and C columns): the pair that fits the
+// workspace with the fewest GEMM blocks, then the largest X' slice. False if none fits.
+bool choose_slices(const hotrg_ctx* ctx, StepPlan& p) {
+  const size_t avail = ctx->ws_bytes - ctx->L.persistent_end;
+  const int ca = p.chi[p.a];
+  int best_xs = 0, best_xs2 = 0;
+  int64_t best_blocks = -1;
+  for (int xs = ca; xs >= 1; --xs) {
+    for (int xs2 = ca; xs2 >= 1; --xs2) {
+      if (scratch_layout(p, xs, xs2, ctx->prec, ctx->impure_active, ctx->rsize).total > avail) continue;
+      const int64_t blocks = (int64_t)((ca + xs - 1) / xs) * ((ca + xs2 - 1) / xs2);
+      if (best_blocks < 0 || blocks < best_blocks || (blocks == best_blocks && xs2 > best_xs2)) {
+        best_blocks = blocks;
+        best_xs = xs;
+        best_xs2 = xs2;
+      }
+      break;  // smaller xs2 only adds blocks for this xs
+    }
+  }
+  if (best_blocks < 0) return false;
+  p.xs = best_xs;
+  p.xs2 = best_xs2;
+  return true;
+}
+
+// ---------------------------------------------------------------------------- autotuner
+// The plan choices that leave the method's arithmetic unchanged up to rounding are timed on
+// the GPU and the fastest is kept, per device and step shape: the closing direction c (which
+// transverse direction the last two isometry passes close; it fixes the shapes of the half
+// contractions and of the GEMM) and the tensor-core pipeline (FP16X3: CTA pairs or single
+// CTAs, which give bit-identical products; TF32X3: 16- or 32-wide k-blocks). The promotion
+// chunk changes the truncation bias of the tensor-core accumulator, so it is not a candidate.
+struct TuneChoice {
+  int c;
+  int opt;
+  float ms;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneChoice> g_tune;   // keyed by device and step shape
+
+std::string tune_key(const hotrg_ctx* ctx, int dir, int dcut) {
+  int dev = -1;
+  cudaGetDevice(&dev);
+  char key[160];
+  snprintf(key, sizeof(key), "dev%d prec%d b%d t%d D%d,%d,%d,%d mu%d cut%d ws%zu", dev, ctx->prec, ctx->batch,
+           ntensors(ctx->impure_active), ctx->dims[0], ctx->dims[1], ctx->dims[2], ctx->dims[3], dir, dcut,
+           ctx->ws_bytes);
+  return key;
+}
+
+bool tune_lookup(const std::string& key, TuneChoice* out) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(key);
+  if (it == g_tune.end()) return false;
+  *out = it->second;
+  return true;
+}
+
+// Times the contraction of batch element 0 (every tensor product and slice block of it) for
+// each candidate plan of the step hotrg_step(ctx, dir, dcut) would run next, on the real
+// operands: the isometry stage runs once, each candidate then writes the (not normalised)
+// next tensor, which the real step overwrites. Neither the ln Z accumulator, the step
+// counter nor the current tensors change. Not callable inside a stream capture.
+template <typename R>
+hotrg_status tune_step(hotrg_ctx* ctx, int dir, int dcut, TuneChoice* best_out) {
+  cudaStream_t st = ctx->stream;
+  StepPlan p0 = make_plan(ctx->dims, dir, dcut, ctx->prec, ctx->batch);
+  if (!choose_slices(ctx, p0)) return HOTRG_EWORKSPACE;
+  const Scratch sc0 = scratch_layout(p0, p0.xs, p0.xs2, ctx->prec, ctx->impure_active, ctx->rsize);
+  hotrg_status s = isometry_stage<R>(ctx, p0, sc0, ctx->ws + ctx->L.persistent_end, st);
+  if (s != HOTRG_OK) return s;
+  std::vector<int> opts;
+  if (ctx->prec == HOTRG_FP16X3) opts = {0, 3};        // CTA pairs, single CTAs (128-k chunks both)
+  else if (ctx->prec == HOTRG_TF32X3) opts = {0, 1};
+  else opts = {-1};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), "tune event");
+  CK(cudaEventCreate(&e1), "tune event");
+  TuneChoice best{p0.c, opts[0], -1.f};
+  const bool prof = ctx->profiling;
+  ctx->profiling = false;
+  s = HOTRG_OK;
+  for (int c = 0; c < 4 && s == HOTRG_OK; ++c) {
+    if (c == dir) continue;
+    StepPlan pc = make_plan(ctx->dims, dir, dcut, ctx->prec, ctx->batch, c);
+    if (!choose_slices(ctx, pc)) continue;
+    for (int opt : opts) {
+      pc.gemm_opt = opt;
+      const uint64_t l0 = ctx->launches;
+      cudaError_t e = cudaEventRecord(e0, st);
+      if (e == cudaSuccess) {
+        s = contract_element<R>(ctx, pc, 0, st);
+        if (s != HOTRG_OK) break;
+        e = cudaEventRecord(e1, st);
+      }
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      ctx->launches = l0;
+      if (e != cudaSuccess) {
+        s = cuda_fail(ctx, e, "tune timing");
+        break;
+      }
+      // a candidate replaces the one in hand only when faster by more than 1 %, so ties go
+      // to the planner's closing direction and the default pipeline
+      const bool is_default = c == p0.c && opt == opts[0];
+      if (best.ms < 0 || ms < 0.99f * best.ms || (is_default && ms <= 1.01f * best.ms)) best = TuneChoice{c, opt, ms};
+    }
+  }
+  ctx->profiling = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != HOTRG_OK) return s;
+  hotrg_status st2 = sync_and_status(ctx);
+  if (st2 != HOTRG_OK) return st2;
+  *best_out = best;
+  return HOTRG_OK;
 }
 
 size_t persistent_bytes(const hotrg_ctx* ctx, int64_t cap) {
@@ -955,13 +1152,13 @@ hotrg_status hotrg_workspace_size(hotrg_ctx* ctx, int nsteps, const int* dirs, c
   int64_t cap = tensor_elems(D);
   if (nsteps == 0) {
     int Dm[4] = {ctx->dcut_max, ctx->dcut_max, ctx->dcut_max, ctx->dcut_max};
-    StepPlan p = make_plan(Dm, 0, ctx->dcut_max, ctx->prec);
+    StepPlan p = make_plan(Dm, 0, ctx->dcut_max, ctx->prec, ctx->batch);
     scratch = scratch_layout(p, p.xs, p.xs2, ctx->prec, ctx->impure, ctx->rsize).total;
     cap = std::max(cap, tensor_elems(Dm));
   } else {
     for (int i = 0; i < nsteps; ++i) {
       if (dirs[i] < 0 || dirs[i] > 3 || dcuts[i] < 1 || dcuts[i] > ctx->dcut_max) return HOTRG_EINVAL;
-      StepPlan p = make_plan(D, dirs[i], dcuts[i], ctx->prec);
+      StepPlan p = make_plan(D, dirs[i], dcuts[i], ctx->prec, ctx->batch);
       scratch = std::max(scratch, scratch_layout(p, p.xs, p.xs2, ctx->prec, ctx->impure, ctx->rsize).total);
       for (int n = 0; n < 4; ++n) {
         D[n] = p.newD[n];
@@ -1090,31 +1287,30 @@ hotrg_status hotrg_step(hotrg_ctx* ctx, int dir, int dcut) {
   if (dir < 0 || dir > 3 || dcut < 1 || dcut > ctx->dcut_max) return HOTRG_EINVAL;
   if (!ctx->initialised || ctx->sticky) return HOTRG_ESTATE;
   if (ctx->k >= kMaxSteps) return HOTRG_ESTATE;
-  StepPlan p = make_plan(ctx->dims, dir, dcut, ctx->prec);
+  StepPlan p = make_plan(ctx->dims, dir, dcut, ctx->prec, ctx->batch);
   for (int n = 0; n < 4; ++n)
     if (p.newD[n] > kMaxLeg) return HOTRG_EINVAL;
   if (p.Enew > ctx->L.cap) return HOTRG_EWORKSPACE;
-  // slice sizes (X for A and C rows, X' for B rows and C columns): the pair that fits with
-  // the fewest GEMM blocks, then the largest X' slice
-  const size_t avail = ctx->ws_bytes - ctx->L.persistent_end;
-  const int ca = p.chi[p.a];
-  int best_xs = 0, best_xs2 = 0;
-  int64_t best_blocks = -1;
-  for (int xs = ca; xs >= 1; --xs) {
-    for (int xs2 = ca; xs2 >= 1; --xs2) {
-      if (scratch_layout(p, xs, xs2, ctx->prec, ctx->impure_active, ctx->rsize).total > avail) continue;
-      const int64_t blocks = (int64_t)((ca + xs - 1) / xs) * ((ca + xs2 - 1) / xs2);
-      if (best_blocks < 0 || blocks < best_blocks || (blocks == best_blocks && xs2 > best_xs2)) {
-        best_blocks = blocks;
-        best_xs = xs;
-        best_xs2 = xs2;
-      }
-      break;  // smaller xs2 only adds blocks for this xs
+  // the autotuner's plan for this shape (timed now if the context tunes and it is new)
+  if (ctx->autotune) {
+    const std::string key = tune_key(ctx, dir, dcut);
+    TuneChoice tc{};
+    bool hit = tune_lookup(key, &tc);
+    if (hit) {
+      ctx->tune_hits += 1;
+    } else {
+      hotrg_status ts = ctx->prec == HOTRG_FP64 ? tune_step<double>(ctx, dir, dcut, &tc)
+                                                : tune_step<float>(ctx, dir, dcut, &tc);
+      if (ts != HOTRG_OK) return ts;
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune[key] = tc;
+      ctx->tune_timed += 1;
     }
+    p = make_plan(ctx->dims, dir, dcut, ctx->prec, ctx->batch, tc.c);
+    p.gemm_opt = tc.opt;
+    p.tuned = hit;
   }
-  if (best_blocks < 0) return HOTRG_EWORKSPACE;
-  p.xs = best_xs;
-  p.xs2 = best_xs2;
+  if (!choose_slices(ctx, p)) return HOTRG_EWORKSPACE;
   hotrg_status s = HOTRG_OK;
   if (!ctx->use_graphs) {
     s = ctx->prec == HOTRG_FP64 ? do_step<double>(ctx, p) : do_step<float>(ctx, p);
@@ -1124,8 +1320,9 @@ hotrg_status hotrg_step(hotrg_ctx* ctx, int dir, int dcut) {
     // which buffer holds the tensors, whether it is the first step (M_1 = C(S,S)) and the
     // impure tensors in use. ln c / 2^k and the record slot come from the device counter.
     char key[256];
-    snprintf(key, sizeof(key), "%d %d %d %d %d %d %d %d %d %d %d %d", dir, dcut, ctx->dims[0], ctx->dims[1],
-             ctx->dims[2], ctx->dims[3], ctx->cur, ctx->k == 0, ctx->impure_active, p.xs, p.xs2, ctx->batch);
+    snprintf(key, sizeof(key), "%d %d %d %d %d %d %d %d %d %d %d %d %d %d", dir, dcut, ctx->dims[0], ctx->dims[1],
+             ctx->dims[2], ctx->dims[3], ctx->cur, ctx->k == 0, ctx->impure_active, p.xs, p.xs2, ctx->batch, p.c,
+             p.gemm_opt);
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
       const uint64_t l0 = ctx->launches;
@@ -1149,6 +1346,9 @@ hotrg_status hotrg_step(hotrg_ctx* ctx, int dir, int dcut) {
     ctx->launches += it->second.launches;
   }
   ctx->mu_hist[ctx->k] = dir;
+  ctx->c_hist[ctx->k] = p.c;
+  ctx->opt_hist[ctx->k] = tc_mode(ctx->prec) ? (p.gemm_opt >= 0 ? p.gemm_opt : ctx->gemm_variant) : -1;
+  ctx->tuned_hist[ctx->k] = p.tuned ? 1 : 0;
   ctx->slices_hist[ctx->k][0] = (p.chi[p.a] + p.xs - 1) / p.xs;
   ctx->slices_hist[ctx->k][1] = (p.chi[p.a] + p.xs2 - 1) / p.xs2;
   for (int n = 0; n < 4; ++n) {
@@ -1272,6 +1472,9 @@ hotrg_status hotrg_step_info(hotrg_ctx* ctx, int b, int step, hotrg_step_record*
   rec->ln_c = d.ln_c;
   rec->slices[0] = ctx->slices_hist[step - 1][0];
   rec->slices[1] = ctx->slices_hist[step - 1][1];
+  rec->closing = ctx->c_hist[step - 1];
+  rec->gemm_option = ctx->opt_hist[step - 1];
+  rec->tuned = ctx->tuned_hist[step - 1];
   return HOTRG_OK;
 }
 
@@ -1335,9 +1538,41 @@ hotrg_status hotrg_set_option(hotrg_ctx* ctx, int option, int value) {
       if (value && ctx->stream == nullptr) return HOTRG_EINVAL;
       ctx->use_graphs = value != 0;
       return HOTRG_OK;
+    case HOTRG_OPT_AUTOTUNE:
+      if (value < 0 || value > 1) return HOTRG_EINVAL;
+      ctx->autotune = value != 0;
+      return HOTRG_OK;
     default:
       return HOTRG_EINVAL;
   }
+}
+
+hotrg_status hotrg_autotune(hotrg_ctx* ctx, int dir, int dcut) {
+  hotrg_status r = check_ready(ctx);
+  if (r != HOTRG_OK) return r;
+  if (dir < 0 || dir > 3 || dcut < 1 || dcut > ctx->dcut_max) return HOTRG_EINVAL;
+  if (!ctx->initialised || ctx->sticky) return HOTRG_ESTATE;
+  StepPlan p = make_plan(ctx->dims, dir, dcut, ctx->prec, ctx->batch);
+  for (int n = 0; n < 4; ++n)
+    if (p.newD[n] > kMaxLeg) return HOTRG_EINVAL;
+  if (p.Enew > ctx->L.cap) return HOTRG_EWORKSPACE;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(ctx->stream, &cs), "capture query");
+  if (cs != cudaStreamCaptureStatusNone) return HOTRG_ESTATE;
+  TuneChoice tc{};
+  r = ctx->prec == HOTRG_FP64 ? tune_step<double>(ctx, dir, dcut, &tc) : tune_step<float>(ctx, dir, dcut, &tc);
+  if (r != HOTRG_OK) return r;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[tune_key(ctx, dir, dcut)] = tc;
+  ctx->tune_timed += 1;
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_tune_stats(const hotrg_ctx* ctx, uint64_t* timed, uint64_t* hits) {
+  if (!ctx) return HOTRG_EINVAL;
+  if (timed) *timed = ctx->tune_timed;
+  if (hits) *hits = ctx->tune_hits;
+  return HOTRG_OK;
 }
 
 hotrg_status hotrg_selftest_wait(hotrg_ctx* ctx, int limit_ms) {

@@ -32,7 +32,7 @@
 namespace hotrg {
 
 constexpr int kJT = 256;            // threads per Jacobi CTA
-constexpr int kSmemJacobiN = 96;    // A and V in shared memory up to this n
+constexpr int kSmemJacobiN = kJacobiSmemN;    // A and V in shared memory up to this n
 
 __device__ __forceinline__ void rr_pair(int r, int i, int m, int& p, int& q) {
   if (i == 0) {
@@ -72,7 +72,7 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
-__global__ void __launch_bounds__(kJT) jacobi_kernel(const __grid_constant__ EigPack jobs, int use_smem,
+__global__ void __launch_bounds__(kJT) jacobi_kernel(const __grid_constant__ EigPack jobs, int njobs, int use_smem,
                                                      double cluster_tau, double tie_rel, int max_sweeps,
                                                      int* status) {
   extern __shared__ double dyn[];
@@ -92,7 +92,15 @@ __global__ void __launch_bounds__(kJT) jacobi_kernel(const __grid_constant__ Eig
   __shared__ int ncomp, rmax, changed;
   __shared__ double pivval;
 
-  const EigJob& jb = jobs.j[blockIdx.x];
+  // job blockIdx.x % njobs of batch element blockIdx.x / njobs
+  const int64_t bidx = blockIdx.x / njobs;
+  EigJob jb = jobs.j[blockIdx.x - bidx * njobs];
+  jb.G += bidx * jobs.sG;
+  if (jb.work) jb.work += bidx * jobs.sWork;
+  jb.lam += bidx * jobs.sLam;
+  jb.U += bidx * jobs.sU;
+  jb.eps += bidx * jobs.sEps;
+  jb.degenerate += bidx * jobs.sDeg;
   const int n = jb.n, chi = jb.chi;
   const int tid = threadIdx.x;
   double* A = use_smem ? dyn : jb.work;   // use_smem: every job of the launch has n <= kSmemJacobiN
@@ -337,30 +345,53 @@ __global__ void __launch_bounds__(kJT) jacobi_kernel(const __grid_constant__ Eig
   }
 }
 
-void jacobi_prepare() {
-  cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       2 * kSmemJacobiN * kSmemJacobiN * (int)sizeof(double));
+// The shared-memory attribute is set once per device: by jacobi_prepare (called when a
+// workspace is attached, ahead of any stream capture) or at the first launch on a device.
+constexpr int kJacobiMaxDevices = 64;
+bool g_jacobi_attr[kJacobiMaxDevices] = {};
+
+cudaError_t jacobi_attr_for_current_device() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kJacobiMaxDevices) return cudaErrorInvalidDevice;
+  if (g_jacobi_attr[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           2 * kSmemJacobiN * kSmemJacobiN * (int)sizeof(double));
+  if (e == cudaSuccess) g_jacobi_attr[dev] = true;
+  return e;
 }
+
+void jacobi_prepare() { jacobi_attr_for_current_device(); }
 
 cudaError_t launch_jacobi(const EigPack& jobs, int njobs, int nmax, double cluster_tau, int* status,
                           cudaStream_t st, int max_sweeps, double tie_rel) {
   const int smem_n = nmax <= kSmemJacobiN ? nmax : 0;
   const size_t smem = (size_t)2 * smem_n * smem_n * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         2 * kSmemJacobiN * kSmemJacobiN * (int)sizeof(double));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  jacobi_kernel<<<njobs, kJT, smem, st>>>(jobs, smem_n > 0 ? 1 : 0, cluster_tau, tie_rel, max_sweeps, status);
+  const cudaError_t e = jacobi_attr_for_current_device();
+  if (e != cudaSuccess) return e;
+  jacobi_kernel<<<njobs * jobs.batch, kJT, smem, st>>>(jobs, njobs, smem_n > 0 ? 1 : 0, cluster_tau, tie_rel,
+                                                      max_sweeps, status);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------- side choice
 template <typename R>
-__global__ void __launch_bounds__(256) select_kernel(const __grid_constant__ SelectPack jobs, double side_rel) {
-  const SelectJob& jb = jobs.j[blockIdx.x];
+__global__ void __launch_bounds__(256) select_kernel(const __grid_constant__ SelectPack jobs, int njobs,
+                                                     double side_rel) {
+  // job blockIdx.x % njobs of batch element blockIdx.x / njobs
+  const int64_t bidx = blockIdx.x / njobs;
+  SelectJob jb = jobs.j[blockIdx.x - bidx * njobs];
+  jb.U[0] += bidx * jobs.sU;
+  jb.U[1] += bidx * jobs.sU;
+  jb.lam0 += bidx * jobs.sLam;
+  jb.eps[0] += bidx * jobs.sEps;
+  jb.eps[1] += bidx * jobs.sEps;
+  jb.degen[0] += bidx * jobs.sDeg;
+  jb.degen[1] += bidx * jobs.sDeg;
+  jb.U64 += bidx * jobs.sU64;
+  jb.Ur = (R*)jb.Ur + bidx * jobs.sUr;
+  if (jb.rec_b) jb.rec_b += bidx * jobs.sRec;
   __shared__ double red[8];
   __shared__ int side;
   const int n = jb.n, chi = jb.chi, tid = threadIdx.x;
@@ -407,7 +438,7 @@ __global__ void __launch_bounds__(256) select_kernel(const __grid_constant__ Sel
 
 template <typename R>
 cudaError_t launch_select(const SelectPack& jobs, int njobs, double side_rel, cudaStream_t st) {
-  select_kernel<R><<<njobs, 256, 0, st>>>(jobs, side_rel);
+  select_kernel<R><<<njobs * jobs.batch, 256, 0, st>>>(jobs, njobs, side_rel);
   return cudaGetLastError();
 }
 template cudaError_t launch_select<double>(const SelectPack&, int, double, cudaStream_t);

@@ -18,7 +18,7 @@ from . import build as _build
 FP64, FP32, TF32X3, FP16X3 = 0, 1, 2, 3
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32x3": TF32X3, "fp16x3": FP16X3}
 IMPURE_NONE, IMPURE_SIGMA, IMPURE_SIGMASIGMA = 0, 1, 2
-OPT_JACOBI_SWEEPS, OPT_GEMM_VARIANT, OPT_GRAPHS = 1, 2, 3
+OPT_JACOBI_SWEEPS, OPT_GEMM_VARIANT, OPT_GRAPHS, OPT_AUTOTUNE = 1, 2, 3, 4
 
 STATUS = {0: "ok", -1: "EINVAL", -2: "EWORKSPACE", -3: "ECUDA", -4: "ENOCONV", -5: "ENONFINITE",
           -6: "ETIMEOUT", -7: "ESTATE", -8: "EUNSUPPORTED"}
@@ -36,7 +36,8 @@ class HotrgError(RuntimeError):
 class StepRecord(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_int), ("dims", ctypes.c_int * 4), ("primed", ctypes.c_int * 4),
                 ("eps", (ctypes.c_double * 2) * 4), ("ln_c", ctypes.c_double),
-                ("degenerate", ctypes.c_int * 4), ("slices", ctypes.c_int * 2)]
+                ("degenerate", ctypes.c_int * 4), ("slices", ctypes.c_int * 2), ("closing", ctypes.c_int),
+                ("gemm_option", ctypes.c_int), ("tuned", ctypes.c_int)]
 
 
 class Profile(ctypes.Structure):
@@ -49,7 +50,7 @@ SYMBOLS = ["hotrg_create", "hotrg_destroy", "hotrg_workspace_size", "hotrg_set_w
            "hotrg_init_tensor", "hotrg_set_tensor", "hotrg_step", "hotrg_lnZ", "hotrg_impure_magnetization",
            "hotrg_impure_energy", "hotrg_x_indicator", "hotrg_step_info", "hotrg_state", "hotrg_copy_tensor",
            "hotrg_copy_isometry", "hotrg_step_flops", "hotrg_set_option", "hotrg_selftest_wait", "hotrg_profile_enable",
-           "hotrg_profile_read", "hotrg_isometry_noalloc",
+           "hotrg_profile_read", "hotrg_isometry_noalloc", "hotrg_autotune", "hotrg_tune_stats",
            "hotrg_status_string", "hotrg_last_error"]
 
 
@@ -90,6 +91,8 @@ def _lib():
         "hotrg_profile_read": (c_int, [c_void_p, P(Profile)]),
         "hotrg_isometry_noalloc": (c_int, [c_void_p, P(c_int), c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                            c_void_p]),
+        "hotrg_autotune": (c_int, [c_void_p, c_int, c_int]),
+        "hotrg_tune_stats": (c_int, [c_void_p, P(ctypes.c_uint64), P(ctypes.c_uint64)]),
         "hotrg_status_string": (ctypes.c_char_p, [c_int]),
         "hotrg_last_error": (ctypes.c_char_p, []),
     }
@@ -127,10 +130,12 @@ class HOTRG:
         dcut_max), dims0 : starting bond dimensions for set_tensor runs.
     workspace_bytes : override of the workspace size (smaller makes steps slice).
     graphs : capture each distinct step into a CUDA graph and replay it (own stream).
+    autotune : take each step's closing direction and GEMM pipeline from the autotuner
+        (timing new step shapes first; see autotune()).
     """
 
     def __init__(self, batch=1, dcut_max=4, precision="fp64", impure=0, schedule=None, dims0=None,
-                 workspace_bytes=None, device=None, stream=None, graphs=False):
+                 workspace_bytes=None, device=None, stream=None, graphs=False, autotune=False):
         import torch
 
         if not torch.cuda.is_available():
@@ -162,6 +167,8 @@ class HOTRG:
         _check(self.lib.hotrg_set_stream(self.ctx, ctypes.c_void_p(self.stream.cuda_stream)), "set_stream")
         if graphs:
             _check(self.lib.hotrg_set_option(self.ctx, OPT_GRAPHS, 1), "set_option(graphs)")
+        if autotune:
+            _check(self.lib.hotrg_set_option(self.ctx, OPT_AUTOTUNE, 1), "set_option(autotune)")
 
     def workspace_size(self, schedule=None, dims0=None) -> int:
         n = 0 if schedule is None else len(schedule)
@@ -229,7 +236,8 @@ class HOTRG:
         _check(self.lib.hotrg_step_info(self.ctx, b, step, ctypes.byref(r)), "step_info")
         return dict(mu=r.mu, dims=tuple(r.dims), primed=tuple(r.primed),
                     eps=tuple(tuple(r.eps[n]) for n in range(4)), ln_c=r.ln_c,
-                    degenerate=tuple(r.degenerate), slices=tuple(r.slices))
+                    degenerate=tuple(r.degenerate), slices=tuple(r.slices), closing=r.closing,
+                    gemm_option=r.gemm_option, tuned=bool(r.tuned))
 
     def tensor(self, which: int = 0, b: int = 0) -> np.ndarray:
         _, dims = self.state()
@@ -242,6 +250,16 @@ class HOTRG:
         out = np.zeros(16 * 16 * 16)
         _check(self.lib.hotrg_copy_isometry(self.ctx, b, nu, _dptr(out), out.size), "copy_isometry")
         return out[: dold * dold * chi].reshape(dold, dold, chi)
+
+    def autotune(self, direction: int, dcut: int):
+        """Time the candidate plans of the next step along `direction` and cache the fastest
+        (the run does not advance)."""
+        _check(self.lib.hotrg_autotune(self.ctx, direction, dcut), "autotune")
+
+    def tune_stats(self) -> dict:
+        t, h = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(self.lib.hotrg_tune_stats(self.ctx, ctypes.byref(t), ctypes.byref(h)), "tune_stats")
+        return dict(timed=t.value, hits=h.value)
 
     def set_option(self, option: int, value: int):
         _check(self.lib.hotrg_set_option(self.ctx, option, value), "set_option")

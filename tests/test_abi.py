@@ -61,6 +61,12 @@ def test_host_argument_checks(lib):
     m, t = ctypes.c_double(), ctypes.c_double()
     assert lib.hotrg_step_flops(ctx, 0, 4, ctypes.byref(m), ctypes.byref(t)) == 0
     assert m.value == pytest.approx(2.0 * (4 * 4 * 4 * 2) ** 2 * (4 * 4 * 2))   # from 2x2x2x2
+    assert lib.hotrg_autotune(ctx, 0, 4) == -2                            # no workspace yet
+    assert lib.hotrg_set_option(ctx, 4, 2) == -1                          # autotune is 0 or 1
+    assert lib.hotrg_set_option(ctx, 4, 1) == 0
+    t, h = ctypes.c_uint64(), ctypes.c_uint64()
+    assert lib.hotrg_tune_stats(ctx, ctypes.byref(t), ctypes.byref(h)) == 0 and (t.value, h.value) == (0, 0)
+    assert lib.hotrg_tune_stats(None, None, None) == -1
     assert lib.hotrg_destroy(ctx) == 0
 
 
