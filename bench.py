@@ -53,6 +53,9 @@ def parse_args():
     p.add_argument("--fp64", type=int, default=1, help="time one FP64 GPU step for the mixed-vs-FP64 ratio")
     p.add_argument("--e2e", type=int, default=1, help="time the whole 40-step job through the public API")
     p.add_argument("--cpu", type=int, default=1, help="time the FP64 oracle on a bounded sample (rank 0, N=1)")
+    p.add_argument("--ref-steps", type=int, default=-1,
+                   help="steps of the FP64-grade tensor-core reference run (HOTRG_FP64OZ) the mixed run is "
+                        "compared with, step by step (-1: 8 at D_cut <= 8, 6 up to 11, 5 at 12, 4 at 13; 0: none)")
     p.add_argument("--batch", type=int, default=1, help="temperatures per GPU (evenly spaced in [6.60, 6.72])")
     p.add_argument("--impure", type=int, default=0, help="propagate the sigma and sigma-sigma impure tensors")
     p.add_argument("--graphs", type=int, default=0, help="replay each distinct step as a captured CUDA graph")
@@ -434,7 +437,10 @@ def main():
 
     # ---------------------------------------------------------------- accuracy vs FP64
     accuracy = {}
-    nver = 8 if D <= 8 else 3
+    nref = args.ref_steps if args.ref_steps >= 0 else (8 if D <= 8 else (6 if D <= 11 else (5 if D == 12 else 4)))
+    if impure:
+        nref = 0                  # the FP64-grade mode propagates the pure tensor only
+    nver = max(8 if D <= 8 else 3, nref)
     # the first temperature of this rank's workload, with its field and impure tensors
     ver = HOTRG(batch=1, dcut_max=D, precision=args.precision, impure=impure, schedule=sched[:nver])
     ver.set_option(OPT_GEMM_VARIANT, args.gemm_variant)
@@ -479,6 +485,37 @@ def main():
         accuracy["abs_dlnZ_mixed_vs_fp64_gpu_step4"] = abs(mixed_lnz[3] - lnz64)
     del r64
     torch.cuda.empty_cache()
+
+    # ---------------------------------------------------------------- FP64-grade reference
+    # HOTRG_FP64OZ: FP64 tensors, the block-spin product from exact integer slices on the fp16
+    # tensor cores (error below 2^-40 of the operands): the steady-state reference at large
+    # D_cut, where the DFMA product takes minutes to hours per step; its last step is timed.
+    fp64oz = None
+    if nref > 0:
+        oz = HOTRG(batch=1, dcut_max=D, precision="fp64oz", schedule=sched[:nref])
+        oz.init_tensor(beta, hfield)
+        doz = []
+        ms_oz, fl_last = None, 0.0
+        for i in range(nref):
+            if i == nref - 1:
+                fl_last = oz.step_flops(*sched[i])[1]      # flops of the step about to run
+                barrier()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(oz.stream)
+            oz.step(*sched[i])
+            if i == nref - 1:
+                e1.record(oz.stream)
+                barrier()
+                ms_oz = allmax(e0.elapsed_time(e1))
+            doz.append(abs(mixed_lnz[i] - float(oz.lnZ()[0])))
+        accuracy[f"abs_dlnZ_mixed_vs_fp64oz_steps1to{nref}"] = doz
+        accuracy["max_abs_dlnZ_mixed_vs_fp64oz"] = max(doz)
+        fp64oz = {"value": allsum(fl_last) / (ms_oz * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms_oz,
+                  "timed_step": nref, "steps_compared": nref,
+                  "what": "FP64 tensors; block-spin product as 15 exact integer-slice products on the fp16 "
+                          "tensor cores (FP64-grade); the step timed is the last one compared"}
+        del oz
+        torch.cuda.empty_cache()
 
     # ---------------------------------------------------------------- end to end, public API
     e2e = None
@@ -528,11 +565,11 @@ def main():
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-        "config": {**workload_config(args, world),
-                   "precision": f"{args.precision} (fp32 storage)", "cuda_graphs": bool(args.graphs),
-                   "gemm_variant": args.gemm_variant, "autotune": bool(args.autotune),
-                   "l2": f"operands larger than L2 (GEMM A and B: 2 x "
-                         f"{(4 if args.precision == 'fp16x3' else 8) * D ** 10 / 1e9:.1f} GB per step, hi + lo)"},
+        "config": workload_config(args, world),
+        "run_config": {"precision": f"{args.precision} (fp32 storage)", "cuda_graphs": bool(args.graphs),
+                       "gemm_variant": args.gemm_variant, "autotune": bool(args.autotune),
+                       "l2": f"operands larger than L2 (GEMM A and B: 2 x "
+                             f"{(4 if args.precision == 'fp16x3' else 8) * D ** 10 / 1e9:.1f} GB per step, hi + lo)"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "algorithmic_bytes": (2 * (4 if args.precision == "fp16x3" else 8) + 4) * float(D) ** 10,
@@ -545,7 +582,7 @@ def main():
         "gpu_launches": prof["launches"],
         "plans": plans, "autotuner": tune,
         "clocks": clk.summary(),
-        "fp64": fp64, "accuracy": accuracy, "lnZ_over_V_after_timed_steps": lnz_run, "observables": obs,
+        "fp64": fp64, "fp64oz": fp64oz, "accuracy": accuracy, "lnZ_over_V_after_timed_steps": lnz_run, "observables": obs,
         "cpu_baseline": cpu, "e2e": e2e,
     }
     if rank == 0:

@@ -57,9 +57,23 @@ typedef enum {
  * HOTRG_FP16X3: the same three products on fp16 hi + lo planes of 2^14 x (kind::f16:
  *               twice the tensor rate and half the operand bytes of TF32X3; the scale
  *               keeps normalised tensors inside fp16's normal range).
- * In every mode the Gram matrices are accumulated in FP64, and the eigensolver, the
- * isometries, the norm and ln Z / V are FP64. */
-typedef enum { HOTRG_FP64 = 0, HOTRG_FP32 = 1, HOTRG_TF32X3 = 2, HOTRG_FP16X3 = 3 } hotrg_precision;
+ * HOTRG_FP64OZ: FP64-grade block-spin product on the fp16 tensor cores (Ozaki-type
+ *               splitting): tensors stored in FP64, each GEMM operand split into 5 planes of
+ *               exact 8-bit integer slices, the 15 leading slice products summed exactly
+ *               per 256-k chunk (FP32 in TMEM) and across chunks as float pairs; error
+ *               below 2^-40 of the operands' magnitudes. Pure tensor only (impure_mask
+ *               must be 0): the reference for the mixed modes at large D_cut, where the
+ *               DFMA product of HOTRG_FP64 takes about 25 min per step (D_cut = 10).
+ * In every mode the Gram matrices are accumulated in FP64 (float pairs of FP32 slice
+ * sums for FP32-stored tensors), and the eigensolver, the isometries, the norm and
+ * ln Z / V are FP64. */
+typedef enum {
+  HOTRG_FP64 = 0,
+  HOTRG_FP32 = 1,
+  HOTRG_TF32X3 = 2,
+  HOTRG_FP16X3 = 3,
+  HOTRG_FP64OZ = 4
+} hotrg_precision;
 
 /* Impure tensors propagated with the pure one (same isometries, same c):
  * SIGMA: S (one sigma inserted) -> magnetisation <sigma> = Tr S / Tr T.

@@ -36,7 +36,12 @@ struct TTMArgs {
   double alpha, beta;
 };
 
-enum TTMMode { kTTMStore = 0, kTTMSplitTF32 = 1, kTTMAccumulate = 2, kTTMSplitF16 = 3 };
+enum TTMMode { kTTMStore = 0, kTTMSplitTF32 = 1, kTTMAccumulate = 2, kTTMSplitF16 = 3, kTTMSplitOz = 4 };
+// FP64-grade tensor-core mode (Ozaki-type splitting): an FP64 operand x with |x| <= 1 is
+// stored as kOzSlices fp16 planes of integers v_i, x = sum_i v_i 2^(-8 (i + 1)) up to
+// 2^-41; |v_0| <= 256, |v_i| <= 128 for i >= 1. Plane p of an operand starts p times the
+// plane size after plane 0 (the split pass takes the plane size as out_lo - out).
+constexpr int kOzSlices = 5;
 // Scale applied to operands stored as fp16 hi/lo pairs: |x| <= 1 (normalised tensors
 // contracted with isometries) becomes <= 2^14, inside fp16's normal range with room for
 // the products; the GEMM undoes it with alpha * 2^-28.
@@ -144,6 +149,11 @@ cudaError_t launch_gram_merge_batch(const double* half, int64_t RRs, const int D
 cudaError_t launch_jacobi(const EigPack& jobs, int njobs, int nmax, double cluster_tau, int* status,
                           cudaStream_t st, int max_sweeps = kJacobiMaxSweeps, double tie_rel = 1e-8);
 cudaError_t launch_wait_selftest(int* status, unsigned long long limit_ns, cudaStream_t st);
+// FP64-grade product on the fp16 tensor cores: C[M][N] (double, row stride ldc) =
+// alpha A B^T with A, B given as kOzSlices integer planes each (K panels as in
+// launch_gemm_group; plane p of A at A + p aps elements, of B at B + p bps).
+cudaError_t launch_gemm_oz(const void* A, const void* B, int64_t aps, int64_t bps, int64_t Kp, int64_t kps, int64_t P,
+                           int64_t M, int64_t N, double* C, int64_t ldc, double alpha, int* status, cudaStream_t st);
 // One output of a grouped block-spin GEMM: C = alpha * sum_{s < nseg} A_{a[s]} B_{b[s]}^T,
 // where A_w, B_w are the w-th operand tensors of the launch (the k loop runs over the nseg
 // segments one after the other, each the full K).

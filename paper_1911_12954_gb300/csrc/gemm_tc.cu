@@ -694,6 +694,242 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------------------- FP64-grade GEMM
+// gemm_oz_kernel: C = alpha A B^T in FP64 accuracy on the fp16 tensor cores (an Ozaki-type
+// splitting; Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59 (2012), here with fixed-point
+// slices). Each operand is given as kOzSlices = 5 planes of integers, x = sum_i v_i 2^-8(i+1)
+// (|v_0| <= 256, |v_i| <= 128), so x_A x_B = sum_{i,j} v_i w_j 2^-8(i+j+2). The products with
+// i + j <= 4 (15 of the 25; the rest lie below 2^-40 of the leading one) are formed, one TMEM
+// accumulator per group g = i + j (5 x 96 columns). Within a chunk of 256 k the sums of groups
+// 0 and 1 are integers below 2^24, exact in FP32 whatever order and truncation the tensor
+// cores use; groups 2..4 lie below 2^-16 of the leading group, where one FP32 rounding per
+// chunk is below 2^-40 of the result. After each chunk the epilogue adds group 0 and 2^-8
+// group 1 into a float pair hi + lo (TwoSum) and 2^-16, 2^-24, 2^-32 times groups 2, 3, 4 into
+// lo alone (lo stays below 2^-15 of hi, so its FP32 rounding is below 2^-39 of the result),
+// and writes alpha 2^-16 (hi + lo) in FP64 at the end: no FP64 arithmetic in the k loop (a few
+// FP64 operations per clock per SM on this chip).
+//   Tile 128 x 96 per CTA, one CTA per SM; k-blocks of 32 fp16 (64-byte swizzle), 3 stages
+//   of 10 planes (70 KB); warp 0 TMA, warp 1 MMA (15 products x 2 k-steps per k-block),
+//   warps 2..13 promotion (warp w: TMEM lane quarter w % 4, 32 of the 96 columns).
+constexpr int OZ_BN = 96;
+constexpr int OZ_EPI_WARPS = 12;
+constexpr int OZ_THREADS = 64 + 32 * OZ_EPI_WARPS;
+constexpr int OZ_COLS = OZ_BN / (OZ_EPI_WARPS / 4);   // 32 columns per epilogue thread
+constexpr int OZ_TMEM_COLS = 512;                       // 5 x 96 used
+struct CfgOz {
+  static constexpr bool kF16 = true;
+  static constexpr bool kPair = false;
+  static constexpr int ELT = 2;
+  static constexpr int BK = 32;
+  static constexpr int KSTEPS = 2;
+  static constexpr int STAGES = 3;
+  static constexpr int A_PLANE = BM * 64;                 // bytes of one plane's k-block
+  static constexpr int B_PLANE = OZ_BN * 64;
+  static constexpr int STAGE_BYTES = kOzSlices * (A_PLANE + B_PLANE);
+  static constexpr int KB_PER_CHUNK = 256 / BK;
+  static constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+  static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
+  static constexpr uint64_t LAYOUT = 4;                   // 64-byte swizzle
+  static constexpr uint32_t SBO = 8 * 64;
+  // D = F32, A = B = F16, both K-major, N = 96, M = 128
+  static constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(OZ_BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+};
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// hi + lo += x (Knuth's TwoSum; the error of the sum goes into lo)
+__device__ __forceinline__ void two_sum_into(float& hi, float& lo, float x) {
+  const float t = hi + x;
+  const float bp = t - hi;
+  lo += (hi - (t - bp)) + (x - bp);
+  hi = t;
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    gemm_oz_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
+                   double* __restrict__ C, int64_t ldc, int M, int N, int Kp, int P, double alpha, int* status) {
+  using CF = CfgOz;
+  constexpr int STAGES = CF::STAGES, BK = CF::BK, STAGE_BYTES = CF::STAGE_BYTES, KPC = CF::KB_PER_CHUNK;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* full = bars;                 // [STAGES]
+  uint64_t* empty = bars + STAGES;       // [STAGES]
+  uint64_t* cfull = bars + 2 * STAGES;   // chunk accumulators written
+  uint64_t* cempty = cfull + 1;          // chunk accumulators drained
+  uint64_t* drain = cempty + 1;
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + OZ_BN - 1) / OZ_BN;
+  const int ntiles = tiles_m * tiles_n;
+  const int nkbp = (Kp + BK - 1) / BK;
+  const int nkb = P * nkbp;
+  const int nchunk = (nkb + KPC - 1) / KPC;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(cfull, 1);
+    mbar_init(cempty, 32 * OZ_EPI_WARPS);
+    mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(OZ_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ TMA producer
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mB) : "memory");
+    int s = 0, nissued = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int tm, tn;
+      tile_coords(t, tiles_m, tiles_n, GROUP_M, tm, tn);
+      for (int kb = 0; kb < nkb; ++kb) {
+        if (!mbar_wait(&empty[s], ph ^ 1, status)) {
+          ok = false;
+          break;
+        }
+        uint8_t* st = smem + s * STAGE_BYTES;
+        const int pn = kb / nkbp, kx = (kb - pn * nkbp) * BK;
+        mbar_expect_tx(&full[s], STAGE_BYTES);
+#pragma unroll
+        for (int q = 0; q < kOzSlices; ++q) {
+          tma_load(&mA, &full[s], st + q * CF::A_PLANE, kx, tm * BM, pn, q);
+          tma_load(&mB, &full[s], st + kOzSlices * CF::A_PLANE + q * CF::B_PLANE, kx, tn * OZ_BN, pn, q);
+        }
+        ++nissued;
+        if (++s == STAGES) {
+          s = 0;
+          ph ^= 1;
+        }
+      }
+    }
+    for (int q = 0; q < STAGES && q < nissued; ++q)
+      mbar_wait(&full[q], (uint32_t)(((nissued - q + STAGES - 1) / STAGES - 1) & 1), status);
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    int s = 0;
+    uint32_t ph = 0, cph = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int kb = 0; kb < nkb; ++kb) {
+        const bool first = kb % KPC == 0;
+        const bool last = kb % KPC == KPC - 1 || kb == nkb - 1;
+        if ((first && !mbar_wait(cempty, cph ^ 1, status)) || !mbar_wait(&full[s], ph, status)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t base = su32(smem + s * STAGE_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < CF::KSTEPS; ++kk) {
+          const uint64_t off = (uint64_t)(kk * 32) >> 4;
+#pragma unroll
+          for (int g = 0; g < kOzSlices; ++g) {
+            const uint32_t d = tmem + (uint32_t)(g * OZ_BN);
+#pragma unroll
+            for (int i = 0; i <= g; ++i) {
+              const uint64_t a = smem_desc<CF>(base + i * CF::A_PLANE) + off;
+              const uint64_t b = smem_desc<CF>(base + kOzSlices * CF::A_PLANE + (g - i) * CF::B_PLANE) + off;
+              mma<CF>(d, a, b, (first && kk == 0 && i == 0) ? 0u : 1u);
+            }
+          }
+        }
+        mma_commit(&empty[s]);
+        if (last) {
+          mma_commit(cfull);
+          cph ^= 1;
+        }
+        if (++s == STAGES) {
+          s = 0;
+          ph ^= 1;
+        }
+      }
+    }
+    mma_commit(drain);
+    mbar_wait(drain, 0, status);
+  } else if (warp >= 2) {
+    // ------------------------------------------------------------ promotion + epilogue
+    const int q = warp & 3;                       // TMEM lane quarter
+    const int cpart = (warp - 2) >> 2;            // which 32 of the 96 columns
+    const int row = q * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    uint32_t cph = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int tm, tn;
+      tile_coords(t, tiles_m, tiles_n, GROUP_M, tm, tn);
+      float hi[OZ_COLS], lo[OZ_COLS];
+#pragma unroll
+      for (int j = 0; j < OZ_COLS; ++j) hi[j] = lo[j] = 0.f;
+      for (int kc = 0; kc < nchunk; ++kc) {
+        if (!__all_sync(0xffffffffu, mbar_wait(cfull, cph, status))) {
+          ok = false;
+          break;
+        }
+        fence_after();
+#pragma unroll
+        for (int g = 0; g < kOzSlices; ++g) {
+          // 2^-8g: exact scalings of exact (groups 0, 1) or nearly exact (2..4) chunk sums
+          const float sc = g == 0 ? 1.f : (g == 1 ? 0x1p-8f : (g == 2 ? 0x1p-16f : (g == 3 ? 0x1p-24f : 0x1p-32f)));
+#pragma unroll
+          for (int c8 = 0; c8 < OZ_COLS; c8 += 8) {
+            float v[8];
+            tmem_ld8(tmem + lane_base + (uint32_t)(g * OZ_BN + cpart * OZ_COLS + c8), v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              if (g < 2) two_sum_into(hi[c8 + j], lo[c8 + j], v[j] * sc);
+              else lo[c8 + j] = fmaf(v[j], sc, lo[c8 + j]);
+            }
+          }
+        }
+        fence_before();
+        mbar_arrive(cempty);
+        cph ^= 1;
+      }
+      if (!ok) break;
+      const int64_t m = (int64_t)tm * BM + row;
+      const int n0 = tn * OZ_BN + cpart * OZ_COLS;
+      if (m < M) {
+        double* crow = C + m * ldc + n0;
+        const double a16 = alpha * 1.52587890625e-05;   // alpha 2^-16
+#pragma unroll
+        for (int j = 0; j < OZ_COLS; ++j)
+          if (n0 + j < N) crow[j] = a16 * ((double)hi[j] + (double)lo[j]);
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS) : "memory");
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -751,6 +987,8 @@ const DeviceSetup* device_setup() {
                                   (int)CfgF16S::SMEM_BYTES) == cudaSuccess;
   ok = ok && cudaFuncSetAttribute(gemm_tf32x3_kernel<CfgF16L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)CfgF16L::SMEM_BYTES) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(gemm_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)CfgOz::SMEM_BYTES) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     return nullptr;
@@ -862,6 +1100,29 @@ cudaError_t launch_gemm_group(const void* Ahi, const void* Alo, const void* Bhi,
   if (variant == 2) return launch_single<CfgF16>(Ahi, Alo, Bhi, Blo, W, aws, bws, Kp, kps, P, M, N, ldc, g, status, st, *dv);
   if (variant == 1) return launch_single<CfgTF32W>(Ahi, Alo, Bhi, Blo, W, aws, bws, Kp, kps, P, M, N, ldc, g, status, st, *dv);
   return launch_single<CfgTF32>(Ahi, Alo, Bhi, Blo, W, aws, bws, Kp, kps, P, M, N, ldc, g, status, st, *dv);
+}
+
+// FP64-grade GEMM (gemm_oz_kernel): C = alpha A B^T, A and B as kOzSlices integer planes in
+// K panels, plane p of A at A + p aps elements (B: bps); kps % 8 == 0.
+cudaError_t launch_gemm_oz(const void* A, const void* B, int64_t aps, int64_t bps, int64_t Kp, int64_t kps, int64_t P,
+                           int64_t M, int64_t N, double* C, int64_t ldc, double alpha, int* status, cudaStream_t st) {
+  using namespace tc;
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (!A || !B || !C || Kp <= 0 || P <= 0 || M > 0x7fffffff || N > 0x7fffffff || Kp * P > 0x7fffffff || ldc < N ||
+      (kps & 7) || kps < Kp || aps < P * M * kps || bps < P * N * kps)
+    return cudaErrorInvalidValue;
+  if ((((uintptr_t)A) | ((uintptr_t)B)) & 15) return cudaErrorInvalidValue;
+  const DeviceSetup* dv = device_setup();
+  if (!dv) return cudaErrorInitializationError;
+  CUtensorMap mA, mB;
+  if (!make_map<CfgOz>(&mA, A, M, Kp, kps, P, kOzSlices, aps, BM) ||
+      !make_map<CfgOz>(&mB, B, N, Kp, kps, P, kOzSlices, bps, OZ_BN))
+    return cudaErrorInvalidValue;
+  const int64_t tiles = ((M + BM - 1) / BM) * ((N + OZ_BN - 1) / OZ_BN);
+  const int grid = (int)(tiles < dv->sms ? tiles : dv->sms);
+  gemm_oz_kernel<<<grid, OZ_THREADS, CfgOz::SMEM_BYTES, st>>>(mA, mB, C, ldc, (int)M, (int)N, (int)Kp, (int)P, alpha,
+                                                              status);
+  return cudaGetLastError();
 }
 
 // Sets the kernels' shared-memory attributes and caches the SM count and pair grid of the

@@ -194,7 +194,19 @@ int64_t tensor_elems(const int D[4]) {
 
 // Tensor-core modes split each operand into hi + lo planes; operand element size in bytes.
 inline bool tc_mode(int prec) { return prec == HOTRG_TF32X3 || prec == HOTRG_FP16X3; }
-inline size_t operand_size(int prec) { return prec == HOTRG_FP64 ? 8 : (prec == HOTRG_FP16X3 ? 2 : 4); }
+// tensors stored in FP64 (FP64 and FP64-grade tensor-core modes)
+inline bool f64_store(int prec) { return prec == HOTRG_FP64 || prec == HOTRG_FP64OZ; }
+// GEMM operands in K panels with 128-byte rows (every tensor-core mode)
+inline bool panel_mode(int prec) { return tc_mode(prec) || prec == HOTRG_FP64OZ; }
+// operand planes: hi + lo (FP16X3, TF32X3), the integer slices (FP64OZ), or one
+inline int operand_planes(int prec) { return tc_mode(prec) ? 2 : (prec == HOTRG_FP64OZ ? kOzSlices : 1); }
+// TTM pass that writes the GEMM operand planes
+inline int split_mode(int prec) {
+  return prec == HOTRG_FP16X3 ? kTTMSplitF16 : (prec == HOTRG_FP64OZ ? kTTMSplitOz : kTTMSplitTF32);
+}
+inline size_t operand_size(int prec) {
+  return prec == HOTRG_FP64 ? 8 : ((prec == HOTRG_FP16X3 || prec == HOTRG_FP64OZ) ? 2 : 4);
+}
 
 double plan_main_flops(const int D[4], const int chi[4], int mu, int a, int b, int c) {
   const double rows = (double)chi[a] * chi[b] * D[c] * D[c] * D[mu];
@@ -251,7 +263,7 @@ StepPlan make_plan(const int D[4], int mu, int dcut, int prec, int batch = 1, in
     p.ksuf = 0;
     for (int q = 1; q <= 5; ++q) {
       const int64_t next = prod * kd[5 - q];
-      if (tc_mode(prec) && next > 4096 && q > 1) break;
+      if (panel_mode(prec) && next > 4096 && q > 1) break;
       prod = next;
       p.ksuf = q;
     }
@@ -259,7 +271,7 @@ StepPlan make_plan(const int D[4], int mu, int dcut, int prec, int batch = 1, in
     // tensor-core operands: panel rows start on 128-byte boundaries, so the 64-byte rows the
     // GEMM's copies fetch never straddle an L2 line (unaligned strides cost D = 10 and 13 a
     // third of their throughput); CUDA-core operands: 16-byte rows
-    const int64_t al = tc_mode(prec) ? 128 / (int64_t)operand_size(prec) : 4;
+    const int64_t al = panel_mode(prec) ? 128 / (int64_t)operand_size(prec) : 4;
     p.kps = (p.Kp + al - 1) / al * al;
     p.P = p.K / p.Kp;
   }
@@ -327,7 +339,7 @@ Scratch scratch_layout(const StepPlan& p, int xs, int xs2, int prec, int impure,
   const int64_t rowsA = (int64_t)xs * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[p.mu];
   const int64_t rowsB = (int64_t)xs2 * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[p.mu];
   const bool split = tc_mode(prec);
-  const size_t os = operand_size(prec);
+  const size_t os = operand_size(prec) * (prec == HOTRG_FP64OZ ? kOzSlices : 1);   // the slices of one operand
   s.O1A = take((size_t)xs * p.E * rs);
   s.A = take((size_t)nt * p.P * rowsA * p.kps * os);
   s.Alo = split ? take((size_t)nt * p.P * rowsA * p.kps * os) : 0;
@@ -494,7 +506,7 @@ hotrg_status build_A(hotrg_ctx* ctx, const StepPlan& p, const R* P, const R* Ua,
         {Dm, os[8], 0, o[9]},   // k
     };
     TTMArgs t = make_ttm(d, Db, os[1], (int64_t)Db * cb, 1, 0, 0, 1.0, 0.0);
-    const int mode = !Alo ? kTTMStore : (ctx->prec == HOTRG_FP16X3 ? kTTMSplitF16 : kTTMSplitTF32);
+    const int mode = !Alo ? kTTMStore : split_mode(ctx->prec);
     ttm_limits((int64_t)xs * p.E, (int64_t)Db * Db * cb, p.P * ((int64_t)xs * cb * Dc * Dc * Dm) * p.kps);
     LK(1, launch_ttm_r<R>(O1, Ub, A, Alo, t, mode, st), "ttm A2");
   }
@@ -544,7 +556,7 @@ hotrg_status build_B(hotrg_ctx* ctx, const StepPlan& p, const R* Q, const R* Ua,
         {Dm, os[8], 0, o[9]},                   // k
     };
     TTMArgs t = make_ttm(d, Db, os[1], cb, 1, 0, 0, 1.0, 0.0);
-    const int mode = !Blo ? kTTMStore : (ctx->prec == HOTRG_FP16X3 ? kTTMSplitF16 : kTTMSplitTF32);
+    const int mode = !Blo ? kTTMStore : split_mode(ctx->prec);
     ttm_limits((int64_t)xs * p.E, (int64_t)Db * Db * cb, p.P * ((int64_t)xs * cb * Dc * Dc * Dm) * p.kps);
     LK(1, launch_ttm_r<R>(O1, Ub, B, Blo, t, mode, st), "ttm B2");
   }
@@ -774,7 +786,7 @@ hotrg_status isometry_stage(hotrg_ctx* ctx, const StepPlan& p, const Scratch& sc
   ep.sU = 6 * (int64_t)p.nmax * kMaxLeg;
   ep.sEps = 6;
   ep.sDeg = 6;
-  const bool fp64 = ctx->prec == HOTRG_FP64;
+  const bool fp64 = f64_store(ctx->prec);
   LK(1, launch_jacobi(ep, 6, nmax, fp64 ? 1e-10 : 1e-6, status, st, ctx->jacobi_sweeps, fp64 ? 1e-8 : 1e-4),
      "jacobi");
   SelectPack sp{};
@@ -814,11 +826,22 @@ hotrg_status isometry_stage(hotrg_ctx* ctx, const StepPlan& p, const Scratch& sc
   return HOTRG_OK;
 }
 
+// What one contract_element call runs: the whole contraction (default), or a timing probe of
+// the first slice block only: its tensor passes without the GEMM, or its GEMM alone on the
+// first gemm_rows rows (operands left in place by a tensor-pass probe of the same plan).
+struct Probe {
+  bool first_block = false;
+  bool ttm = true;
+  bool gemm = true;
+  int64_t gemm_rows = 0;
+};
+
 // Step 3 for batch element bidx: the half contractions, the grouped block-spin GEMM and the
 // closing isometries, slice block by slice block, into the element's next tensors (not
 // yet normalised). Reads the element's isometries from its persistent slot.
 template <typename R>
-hotrg_status contract_element(hotrg_ctx* ctx, const StepPlan& p, int bidx, cudaStream_t st) {
+hotrg_status contract_element(hotrg_ctx* ctx, const StepPlan& p, int bidx, cudaStream_t st,
+                              const Probe& pr = Probe()) {
   const Scratch sc = scratch_layout(p, p.xs, p.xs2, ctx->prec, ctx->impure_active, ctx->rsize);
   char* sb = ctx->ws + ctx->L.persistent_end;
   const int mu = p.mu;
@@ -838,15 +861,17 @@ hotrg_status contract_element(hotrg_ctx* ctx, const StepPlan& p, int bidx, cudaS
     // ---------------------------------------------------------------- 3. contraction
     R* O1A = (R*)(sb + sc.O1A);
     R* O1B = (R*)(sb + sc.O1B);
-    // operand planes, addressed in bytes (fp16 operands are half the storage type's size)
+    // operand planes, addressed in bytes (fp16 operands are half the storage type's size);
+    // FP64OZ: the kOzSlices planes of one operand follow each other (plane 1 in place of lo)
+    const bool oz = ctx->prec == HOTRG_FP64OZ;
+    const int64_t Asz = p.P * rowsA * p.kps, Bsz = p.P * rowsB * p.kps, Csz = rowsA * rowsB;
     char* Abuf = sb + sc.A;
-    char* Alob = split ? sb + sc.Alo : nullptr;
+    char* Alob = split ? sb + sc.Alo : (oz ? Abuf + Asz * (int64_t)osz : nullptr);
     char* Bbuf = sb + sc.B;
-    char* Blob = split ? sb + sc.Blo : nullptr;
+    char* Blob = split ? sb + sc.Blo : (oz ? Bbuf + Bsz * (int64_t)osz : nullptr);
     auto opnd = [&](char* base, int64_t elems) { return base ? (R*)(base + elems * (int64_t)osz) : (R*)nullptr; };
     R* Cbuf = (R*)(sb + sc.C);
     R* O3 = (R*)(sb + sc.O3);
-    const int64_t Asz = p.P * rowsA * p.kps, Bsz = p.P * rowsB * p.kps, Csz = rowsA * rowsB;
     const R* src[3];
     R* dst[3];
     for (int w = 0; w < nt; ++w) {
@@ -863,27 +888,32 @@ hotrg_status contract_element(hotrg_ctx* ctx, const StepPlan& p, int bidx, cudaS
       }
       return HOTRG_OK;
     };
-    if (!b_sliced) {
+    if (!b_sliced && pr.ttm) {
       hotrg_status s = buildB(0, ca);
       if (s != HOTRG_OK) return s;
     }
-    for (int x0 = 0; x0 < ca; x0 += p.xs) {
+    const int xend = pr.first_block ? std::min(p.xs, ca) : ca;
+    const int x2end = pr.first_block ? std::min(p.xs2, ca) : ca;
+    for (int x0 = 0; x0 < xend; x0 += p.xs) {
       const int xs = std::min(p.xs, ca - x0);
-      const int64_t rA = (int64_t)xs * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[mu];
-      for (int w = 0; w < nt; ++w) {
+      const int64_t rA_full = (int64_t)xs * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[mu];
+      const int64_t rA = pr.gemm_rows > 0 ? std::min(rA_full, pr.gemm_rows) : rA_full;
+      for (int w = 0; w < nt && pr.ttm; ++w) {
         hotrg_status s = build_A<R>(ctx, p, src[w], Ua, Ub, x0, xs, O1A, opnd(Abuf, w * Asz),
                                     opnd(Alob, w * Asz), st);
         if (s != HOTRG_OK) return s;
       }
-      for (int x20 = 0; x20 < ca; x20 += p.xs2) {
+      for (int x20 = 0; x20 < x2end; x20 += p.xs2) {
         const int xs2 = std::min(p.xs2, ca - x20);
         const int64_t rB = (int64_t)xs2 * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[mu];
-        if (b_sliced) {
+        if (b_sliced && pr.ttm) {
           hotrg_status s = buildB(x20, xs2);
           if (s != HOTRG_OK) return s;
         }
         hotrg_status s;
-        if (split) {
+        if (!pr.gemm) {
+          // tensor-pass probe: no product
+        } else if (split) {
           // every output of the block in one launch: C_T = A_T B_T^T, C_S = (A_S B_T^T + A_T B_S^T) / 2,
           // and M_1 = A_S B_S^T (the nearest-neighbour pair inside the first block) or
           // C_M = (A_M B_T^T + A_T B_M^T) / 2; fp16 operands carry the factor 2^14 each
@@ -897,6 +927,13 @@ hotrg_status contract_element(hotrg_ctx* ctx, const StepPlan& p, int bidx, cudaS
                                 : GemmProblem{(float*)(Cbuf + 2 * Csz), (float)(0.5 * un), 2, {2, 0}, {0, 2}};
           s = gemm_tc(ctx, Abuf, Alob, Bbuf, Blob, nt, Asz, Bsz, p, g, rA, rB, st);
           if (s != HOTRG_OK) return s;
+        } else if (oz) {   // pure tensor only: C_T = A_T B_T^T in FP64 accuracy
+          GemmTimer tm{ctx, st};
+          if ((s = tm.start()) != HOTRG_OK) return s;
+          CK(launch_gemm_oz(Abuf, Bbuf, Asz, Bsz, p.Kp, p.kps, p.P, rA, rB, (double*)Cbuf, rB, 1.0,
+                            (int*)(ctx->ws + ctx->L.status), st),
+             "gemm oz");
+          if ((s = tm.stop(2.0 * (double)rA * (double)rB * (double)p.K)) != HOTRG_OK) return s;
         } else {
           auto Ap = [&](int w) { return opnd(Abuf, w * Asz); };
           auto Bp = [&](int w) { return opnd(Bbuf, w * Bsz); };
@@ -921,7 +958,7 @@ hotrg_status contract_element(hotrg_ctx* ctx, const StepPlan& p, int bidx, cudaS
             }
           }
         }
-        for (int w = 0; w < nt; ++w) {
+        for (int w = 0; w < nt && pr.ttm; ++w) {
           s = close_C<R>(ctx, p, Cbuf + w * Csz, Uc, x0, xs, x20, xs2, O3, dst[w], st);
           if (s != HOTRG_OK) return s;
         }
@@ -1033,11 +1070,14 @@ bool tune_lookup(const std::string& key, TuneChoice* out) {
   return true;
 }
 
-// Times the contraction of batch element 0 (every tensor product and slice block of it) for
-// each candidate plan of the step hotrg_step(ctx, dir, dcut) would run next, on the real
-// operands: the isometry stage runs once, each candidate then writes the (not normalised)
-// next tensor, which the real step overwrites. Neither the ln Z accumulator, the step
-// counter nor the current tensors change. Not callable inside a stream capture.
+// Ranks the candidate plans of the step hotrg_step(ctx, dir, dcut) would run next, with timing
+// probes on the real operands of batch element 0 (the isometry stage runs once): for each
+// closing direction the tensor passes of its first slice block (times its number of blocks),
+// and the GEMM pipelines on the first 2048 rows of the planner's first block; a plan's
+// estimate is its tensor-pass time plus its GEMM flops at the measured rate of the fastest
+// pipeline. Probes write scratch and the (not normalised) next tensor, which the real step
+// overwrites; the ln Z accumulator, the step counter and the current tensors do not change.
+// A probe costs about one slice block, not a whole step. Not callable inside a capture.
 template <typename R>
 hotrg_status tune_step(hotrg_ctx* ctx, int dir, int dcut, TuneChoice* best_out) {
   cudaStream_t st = ctx->stream;
@@ -1053,43 +1093,87 @@ hotrg_status tune_step(hotrg_ctx* ctx, int dir, int dcut, TuneChoice* best_out) 
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0), "tune event");
   CK(cudaEventCreate(&e1), "tune event");
-  TuneChoice best{p0.c, opts[0], -1.f};
   const bool prof = ctx->profiling;
   ctx->profiling = false;
-  s = HOTRG_OK;
+  const uint64_t l0 = ctx->launches;
+  auto timed = [&](const StepPlan& pl, const Probe& pr, float* ms) -> hotrg_status {
+    cudaError_t e = cudaEventRecord(e0, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tune timing");
+    hotrg_status r = contract_element<R>(ctx, pl, 0, st, pr);
+    if (r != HOTRG_OK) return r;
+    e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    return e == cudaSuccess ? HOTRG_OK : cuda_fail(ctx, e, "tune timing");
+  };
+  const int nprod = ntensors(ctx->impure_active) == 1 ? 1 : (ctx->k == 0 ? 4 : 5);   // products per block
+  double est_ttm[4] = {-1, -1, -1, -1}, flops[4] = {0, 0, 0, 0};
   for (int c = 0; c < 4 && s == HOTRG_OK; ++c) {
-    if (c == dir) continue;
+    if (c == dir || c == p0.c) continue;   // the planner's direction last: its operands stay for the GEMM probe
     StepPlan pc = make_plan(ctx->dims, dir, dcut, ctx->prec, ctx->batch, c);
     if (!choose_slices(ctx, pc)) continue;
-    for (int opt : opts) {
-      pc.gemm_opt = opt;
-      const uint64_t l0 = ctx->launches;
-      cudaError_t e = cudaEventRecord(e0, st);
-      if (e == cudaSuccess) {
-        s = contract_element<R>(ctx, pc, 0, st);
-        if (s != HOTRG_OK) break;
-        e = cudaEventRecord(e1, st);
-      }
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float ms = 0;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      ctx->launches = l0;
-      if (e != cudaSuccess) {
-        s = cuda_fail(ctx, e, "tune timing");
-        break;
-      }
-      // a candidate replaces the one in hand only when faster by more than 1 %, so ties go
-      // to the planner's closing direction and the default pipeline
-      const bool is_default = c == p0.c && opt == opts[0];
-      if (best.ms < 0 || ms < 0.99f * best.ms || (is_default && ms <= 1.01f * best.ms)) best = TuneChoice{c, opt, ms};
+    Probe pr;
+    pr.first_block = true;
+    pr.gemm = false;
+    float ms = 0;
+    s = timed(pc, pr, &ms);
+    const int ca = pc.chi[pc.a];
+    est_ttm[c] = (double)ms * ((ca + pc.xs - 1) / pc.xs) * ((ca + pc.xs2 - 1) / pc.xs2);
+    flops[c] = nprod * pc.main_flops;
+  }
+  float best_g = -1.f;
+  int best_opt = opts[0];
+  if (s == HOTRG_OK) {
+    Probe pr;
+    pr.first_block = true;
+    pr.gemm = false;
+    float ms = 0;
+    s = timed(p0, pr, &ms);
+    const int ca = p0.chi[p0.a];
+    est_ttm[p0.c] = (double)ms * ((ca + p0.xs - 1) / p0.xs) * ((ca + p0.xs2 - 1) / p0.xs2);
+    flops[p0.c] = nprod * p0.main_flops;
+  }
+  const int64_t rows0 = (int64_t)std::min(p0.xs, p0.chi[p0.a]) * p0.chi[p0.b] * p0.D[p0.c] * p0.D[p0.c] * p0.D[dir];
+  const int64_t cols0 = (int64_t)std::min(p0.xs2, p0.chi[p0.a]) * p0.chi[p0.b] * p0.D[p0.c] * p0.D[p0.c] * p0.D[dir];
+  const int64_t probe_rows = std::min<int64_t>(rows0, 2048);
+  for (int opt : opts) {
+    if (s != HOTRG_OK) break;
+    StepPlan pg = p0;
+    pg.gemm_opt = opt;
+    Probe pr;
+    pr.first_block = true;
+    pr.ttm = false;
+    pr.gemm_rows = probe_rows;
+    float ms = 0;
+    s = timed(pg, pr, &ms);
+    // ties (within 1 %) go to the default pipeline
+    if (best_g < 0 || ms < 0.99f * best_g) {
+      best_g = ms;
+      best_opt = opt;
     }
   }
+  ctx->launches = l0;
   ctx->profiling = prof;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s != HOTRG_OK) return s;
   hotrg_status st2 = sync_and_status(ctx);
   if (st2 != HOTRG_OK) return st2;
+  // GEMM rate of the best pipeline on the probe (flops of every product of the block)
+  const double probe_flops = 2.0 * (double)probe_rows * (double)cols0 * (double)p0.K * nprod;
+  const double rate = best_g > 0 ? probe_flops / best_g : 0.0;   // flops per ms
+  TuneChoice best{p0.c, best_opt, -1.f};
+  double best_est = -1;
+  for (int c = 0; c < 4; ++c) {
+    if (est_ttm[c] < 0) continue;
+    const double est = est_ttm[c] + (rate > 0 ? flops[c] / rate : 0.0);
+    const bool is_default = c == p0.c;
+    if (best_est < 0 || est < 0.99 * best_est || (is_default && est <= 1.01 * best_est)) {
+      best_est = est;
+      best.c = c;
+    }
+  }
+  best.ms = (float)best_est;
   *best_out = best;
   return HOTRG_OK;
 }
@@ -1121,7 +1205,14 @@ const char* hotrg_last_error(void) { return g_last_error.c_str(); }
 
 hotrg_status hotrg_create(hotrg_ctx** out, int batch, int dcut_max, int prec, int impure_mask) {
   if (!out || batch < 1 || batch > 4096 || dcut_max < 2 || dcut_max > kMaxLeg) return HOTRG_EINVAL;
-  if (prec != HOTRG_FP64 && prec != HOTRG_FP32 && prec != HOTRG_TF32X3 && prec != HOTRG_FP16X3) return HOTRG_EINVAL;
+  if (prec != HOTRG_FP64 && prec != HOTRG_FP32 && prec != HOTRG_TF32X3 && prec != HOTRG_FP16X3 &&
+      prec != HOTRG_FP64OZ)
+    return HOTRG_EINVAL;
+  if (prec == HOTRG_FP64OZ && impure_mask != 0) {
+    // the integer slices assume |x| <= 1, which the normalised pure tensor's operands meet
+    set_last_error("HOTRG_FP64OZ propagates the pure tensor only (impure tensors: HOTRG_FP64)");
+    return HOTRG_EINVAL;
+  }
   if (impure_mask < 0 || impure_mask > 3 || impure_mask == HOTRG_IMPURE_SIGMASIGMA) return HOTRG_EINVAL;
   hotrg_ctx* c = new hotrg_ctx();
   c->batch = batch;
@@ -1129,7 +1220,7 @@ hotrg_status hotrg_create(hotrg_ctx** out, int batch, int dcut_max, int prec, in
   c->prec = prec;
   c->impure = impure_mask;
   c->impure_active = impure_mask;
-  c->rsize = prec == HOTRG_FP64 ? 8 : 4;
+  c->rsize = f64_store(prec) ? 8 : 4;
   *out = c;
   return HOTRG_OK;
 }
@@ -1217,7 +1308,7 @@ hotrg_status hotrg_init_tensor(hotrg_ctx* ctx, const double* beta, const double*
   const double* db = (const double*)(ctx->ws + ctx->L.beta);
   const double* dh = (const double*)(ctx->ws + ctx->L.hfield);
   double* lnz = (double*)(ctx->ws + ctx->L.lnz);
-  if (ctx->prec == HOTRG_FP64)
+  if (f64_store(ctx->prec))
     LK(1, launch_init<double>(db, dh, tensor_ptr<double>(ctx, 0, 0, 0),
                            ctx->impure ? tensor_ptr<double>(ctx, 1, 0, 0) : nullptr, ctx->L.cap, lnz, ctx->batch, st),
        "init");
@@ -1260,7 +1351,7 @@ hotrg_status hotrg_set_tensor(hotrg_ctx* ctx, int b, const int dims[4], const do
     CK(cudaMemset(ctx->ws + ctx->L.rec, 0, (size_t)ctx->batch * kMaxSteps * sizeof(DevRecord)), "rec");
     ctx->cur = 0;
   }
-  if (ctx->prec == HOTRG_FP64) {
+  if (f64_store(ctx->prec)) {
     std::vector<double> tmp(E);
     for (int64_t i = 0; i < E; ++i) tmp[i] = T_host[i] / c;
     CK(cudaMemcpy(tensor_ptr<double>(ctx, 0, ctx->cur, b), tmp.data(), E * 8, cudaMemcpyHostToDevice), "upload");
@@ -1299,7 +1390,7 @@ hotrg_status hotrg_step(hotrg_ctx* ctx, int dir, int dcut) {
     if (hit) {
       ctx->tune_hits += 1;
     } else {
-      hotrg_status ts = ctx->prec == HOTRG_FP64 ? tune_step<double>(ctx, dir, dcut, &tc)
+      hotrg_status ts = f64_store(ctx->prec) ? tune_step<double>(ctx, dir, dcut, &tc)
                                                 : tune_step<float>(ctx, dir, dcut, &tc);
       if (ts != HOTRG_OK) return ts;
       std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1313,7 +1404,7 @@ hotrg_status hotrg_step(hotrg_ctx* ctx, int dir, int dcut) {
   if (!choose_slices(ctx, p)) return HOTRG_EWORKSPACE;
   hotrg_status s = HOTRG_OK;
   if (!ctx->use_graphs) {
-    s = ctx->prec == HOTRG_FP64 ? do_step<double>(ctx, p) : do_step<float>(ctx, p);
+    s = f64_store(ctx->prec) ? do_step<double>(ctx, p) : do_step<float>(ctx, p);
     if (s != HOTRG_OK) return s;
   } else {
     // Everything the step's launches depend on: the plan (dims, direction, cut, slices),
@@ -1327,7 +1418,7 @@ hotrg_status hotrg_step(hotrg_ctx* ctx, int dir, int dcut) {
     if (it == ctx->graphs.end()) {
       const uint64_t l0 = ctx->launches;
       CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-      s = ctx->prec == HOTRG_FP64 ? do_step<double>(ctx, p) : do_step<float>(ctx, p);
+      s = f64_store(ctx->prec) ? do_step<double>(ctx, p) : do_step<float>(ctx, p);
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
       if (s != HOTRG_OK) {
@@ -1365,7 +1456,7 @@ hotrg_status hotrg_step(hotrg_ctx* ctx, int dir, int dcut) {
 
 static hotrg_status traces(hotrg_ctx* ctx, int which, std::vector<double>& out) {
   const double* dtr = (const double*)(ctx->ws + ctx->L.trace);
-  if (ctx->prec == HOTRG_FP64)
+  if (f64_store(ctx->prec))
     LK(1, launch_trace<double>(tensor_ptr<double>(ctx, which, ctx->cur, 0), ctx->L.cap, ctx->dims, ctx->batch,
                             (double*)dtr + which * ctx->batch, ctx->stream),
        "trace");
@@ -1407,7 +1498,7 @@ hotrg_status hotrg_x_indicator(hotrg_ctx* ctx, int nu, double* X) {
   if (!X || nu < 0 || nu > 3) return HOTRG_EINVAL;
   if (!ctx->initialised) return HOTRG_ESTATE;
   double* dx = (double*)(ctx->ws + ctx->L.trace) + 3 * ctx->batch;
-  if (ctx->prec == HOTRG_FP64)
+  if (f64_store(ctx->prec))
     LK(1, launch_xind<double>(tensor_ptr<double>(ctx, 0, ctx->cur, 0), ctx->L.cap, ctx->dims, ctx->batch, nu, dx,
                            ctx->stream),
        "x indicator");
@@ -1495,7 +1586,7 @@ hotrg_status hotrg_copy_tensor(hotrg_ctx* ctx, int which, int b, double* host, s
   const int64_t E = tensor_elems(ctx->dims);
   if ((int64_t)n < E) return HOTRG_EINVAL;
   CK(cudaStreamSynchronize(ctx->stream), "sync");
-  if (ctx->prec == HOTRG_FP64) {
+  if (f64_store(ctx->prec)) {
     CK(cudaMemcpy(host, tensor_ptr<double>(ctx, which, ctx->cur, b), E * 8, cudaMemcpyDeviceToHost), "copy");
   } else {
     std::vector<float> tmp(E);
@@ -1560,7 +1651,7 @@ hotrg_status hotrg_autotune(hotrg_ctx* ctx, int dir, int dcut) {
   CK(cudaStreamIsCapturing(ctx->stream, &cs), "capture query");
   if (cs != cudaStreamCaptureStatusNone) return HOTRG_ESTATE;
   TuneChoice tc{};
-  r = ctx->prec == HOTRG_FP64 ? tune_step<double>(ctx, dir, dcut, &tc) : tune_step<float>(ctx, dir, dcut, &tc);
+  r = f64_store(ctx->prec) ? tune_step<double>(ctx, dir, dcut, &tc) : tune_step<float>(ctx, dir, dcut, &tc);
   if (r != HOTRG_OK) return r;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[tune_key(ctx, dir, dcut)] = tc;

@@ -26,6 +26,19 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
+// Exact 8-bit slices of x (|x| <= 1, FP64): r <- 256 r, v = rint(r), r <- r - v, five times;
+// every step is exact in FP64 and every v an integer fp16 holds exactly (|v| <= 256).
+__device__ __forceinline__ void oz_store(__half* out, int64_t plane, int64_t o, double x) {
+  double r = x;
+#pragma unroll
+  for (int i = 0; i < kOzSlices; ++i) {
+    r *= 256.0;
+    const double v = rint(r);
+    out[o + i * plane] = __float2half_rn((float)v);
+    r -= v;
+  }
+}
+
 template <typename TI, typename TU, typename TO, int MODE>
 __global__ void __launch_bounds__(256) ttm_kernel(const TI* __restrict__ in, const TU* __restrict__ U,
                                                   TO* __restrict__ out, TO* __restrict__ out_lo,
@@ -75,6 +88,8 @@ __global__ void __launch_bounds__(256) ttm_kernel(const TI* __restrict__ in, con
         const __half hi = __float2half_rn(v);
         ((__half*)out)[o1] = hi;
         ((__half*)out_lo)[o1] = __float2half_rn(v - __half2float(hi));
+      } else if (MODE == kTTMSplitOz) {
+        oz_store((__half*)out, (__half*)out_lo - (__half*)out, o1, (double)acc);
       } else if (MODE == kTTMAccumulate) {
         out[o1] = (TO)(acc + (Acc)a.beta * (Acc)out[o1]);
       } else {
@@ -136,6 +151,8 @@ __device__ __forceinline__ void fiber_store(R* out, R* out_lo, int64_t o, R acc)
     const __half hi = __float2half_rn(v);
     ((__half*)out)[o] = hi;
     ((__half*)out_lo)[o] = __float2half_rn(v - __half2float(hi));
+  } else if (MODE == kTTMSplitOz) {
+    oz_store((__half*)out, (__half*)out_lo - (__half*)out, o, (double)acc);
   } else {
     out[o] = acc;
   }
@@ -516,6 +533,7 @@ cudaError_t launch_fiber(const R* in, const R* U, R* out, R* out_lo, const Fiber
   }
   if (mode == kTTMSplitTF32) ttm_short_kernel<R, kTTMSplitTF32><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
   else if (mode == kTTMSplitF16) ttm_short_kernel<R, kTTMSplitF16><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
+  else if (mode == kTTMSplitOz) ttm_short_kernel<R, kTTMSplitOz><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
   else ttm_short_kernel<R, kTTMStore><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
   return cudaGetLastError();
 }
@@ -542,6 +560,9 @@ cudaError_t launch_ttm(const TI* in, const TU* U, TO* out, TO* out_lo, const TTM
       break;
     case kTTMSplitF16:
       ttm_kernel<TI, TU, TO, kTTMSplitF16><<<(unsigned)blocks, threads, 0, st>>>(in, U, out, out_lo, a);
+      break;
+    case kTTMSplitOz:
+      ttm_kernel<TI, TU, TO, kTTMSplitOz><<<(unsigned)blocks, threads, 0, st>>>(in, U, out, out_lo, a);
       break;
     default:
       ttm_kernel<TI, TU, TO, kTTMAccumulate><<<(unsigned)blocks, threads, 0, st>>>(in, U, out, out_lo, a);

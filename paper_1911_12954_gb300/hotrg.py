@@ -15,8 +15,8 @@ import numpy as np
 
 from . import build as _build
 
-FP64, FP32, TF32X3, FP16X3 = 0, 1, 2, 3
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32x3": TF32X3, "fp16x3": FP16X3}
+FP64, FP32, TF32X3, FP16X3, FP64OZ = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32x3": TF32X3, "fp16x3": FP16X3, "fp64oz": FP64OZ}
 IMPURE_NONE, IMPURE_SIGMA, IMPURE_SIGMASIGMA = 0, 1, 2
 OPT_JACOBI_SWEEPS, OPT_GEMM_VARIANT, OPT_GRAPHS, OPT_AUTOTUNE = 1, 2, 3, 4
 
@@ -124,7 +124,8 @@ class HOTRG:
     ----------
     batch : number of independent runs (temperatures).
     dcut_max : largest bond dimension (2..16).
-    precision : "fp64", "fp32", "tf32x3" or "fp16x3" (the fastest mixed mode).
+    precision : "fp64", "fp32", "tf32x3", "fp16x3" (the fastest mixed mode) or "fp64oz" (FP64-grade
+        product on the tensor cores; pure tensor only).
     impure : 0, IMPURE_SIGMA or IMPURE_SIGMA | IMPURE_SIGMASIGMA.
     schedule : list of (dir, dcut) used to size the workspace (None: steady state at
         dcut_max), dims0 : starting bond dimensions for set_tensor runs.

@@ -359,6 +359,44 @@ def test_fp16x3_step_legs8_elementwise_vs_oracle():
     assert err <= 3e-5 * np.abs(ref).max(), err
 
 
+# ------------------------------------------------------------------ FP64-grade tensor-core mode
+@pytest.mark.parametrize("dims,mu,dcut", [((3, 4, 2, 3), 1, 5), ((8, 8, 7, 8), 0, 4)])
+def test_fp64oz_step_elementwise_vs_oracle(dims, mu, dcut):
+    """HOTRG_FP64OZ (integer-slice products on the fp16 tensor cores, FP64 tensors): one step
+    element by element against the oracle (coarse_grain with the oracle's isometries) to
+    1e-12 of max, the bar of the DFMA path. The second case runs the product at scale: 6272
+    rows and columns (66 x 66 tiles of 128 x 96), K = 32768 in 8 panels of 4096."""
+    T = (random_tensor(77, dims) if max(dims) < 8 else decaying_tensor(31, dims))
+    T = T / np.linalg.norm(T)
+    g = _gpu(batch=1, dcut_max=8, precision="fp64oz", schedule=[(mu, dcut)], dims0=dims)
+    g.set_tensor(T)
+    g.step(mu, dcut)
+    got = g.tensor()
+    trans = [n for n in range(4) if n != mu]
+    isos = {n: H.isometry(T, T, mu, n, dcut) for n in trans}
+    assert not any(i.degenerate_cut for i in isos.values())
+    ref = H.coarse_grain(T, T, {n: i.U for n, i in isos.items()}, mu)
+    ref = ref / np.linalg.norm(ref)
+    err = np.abs(got - ref).max()
+    assert err <= 1e-12 * np.abs(ref).max(), err
+
+
+def test_fp64oz_dcut8_first_8_steps_vs_golden():
+    """HOTRG_FP64OZ on the D_cut = 8 workload (T = 6.65, h = 0, towards 1024^4): ln Z/V and
+    ln c within 1e-10 relative of the oracle after each of the first 8 steps, the bar of the
+    FP64 path, in about a second per steady-state step instead of a minute."""
+    gd = _golden("ising4d_T6.65_h0_dcut8_8steps")
+    cfg = gd["config"]
+    sched = [(s["mu"], cfg["dcut"]) for s in gd["steps"][:8]]
+    g = _gpu(batch=1, dcut_max=8, precision="fp64oz", schedule=sched)
+    g.init_tensor(gd["beta"], cfg["h"])
+    for i, (mu, dc) in enumerate(sched):
+        g.step(mu, dc)
+        ref = gd["steps"][i]
+        assert g.lnZ()[0] == pytest.approx(ref["lnZ"], rel=1e-10), (i + 1, g.lnZ()[0], ref["lnZ"])
+        assert g.step_info(i + 1)["ln_c"] == pytest.approx(ref["ln_c"], rel=1e-10)
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("tf32x3", 3e-5), ("fp16x3", 3e-5)])
 def test_long_closing_contraction(prec, tol):
     """Uniform bond dimension 9: the closing passes contract D_c^2 = 81 > 64 values per
