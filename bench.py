@@ -71,6 +71,10 @@ def parse_args():
     p.add_argument("--autotune", type=int, default=1,
                    help="take each step's closing direction and GEMM pipeline from the autotuner (the "
                         "steady-state shapes are tuned after the warm-up steps, outside the timed region)")
+    p.add_argument("--maxnorm", type=int, default=1, choices=[0, 1, 2],
+                   help="FP16X3 operand scaling: 1 bound from the first pass, 2 exact max pass, 0 fixed 2^14")
+    p.add_argument("--group", type=int, default=0,
+                   help="most temperatures contracted together (HOTRG_OPT_GROUP; 0: the planner's choice)")
     p.add_argument("--gemm-variant", type=int, default=0,
                    help="tensor-core GEMM pipeline option (HOTRG_OPT_GEMM_VARIANT) for every mixed run")
     p.add_argument("--precision", choices=["tf32x3", "fp16x3"], default="fp16x3",
@@ -401,7 +405,7 @@ def main():
 
     # ---------------------------------------------------------------- mixed precision, timed
     run = HOTRG(batch=args.batch, dcut_max=D, precision=args.precision, impure=impure, schedule=sched,
-                graphs=bool(args.graphs), autotune=bool(args.autotune))
+                graphs=bool(args.graphs), autotune=bool(args.autotune), group=args.group, maxnorm=args.maxnorm)
     run.set_option(OPT_GEMM_VARIANT, args.gemm_variant)
     run.init_tensor(betas, hfield)
     for i in range(args.warmup):
@@ -423,7 +427,7 @@ def main():
         barrier()
     prof = run.profile_read()
     run.profile(False)
-    plans = [{"step": k, **{f: run.step_info(k)[f] for f in ("mu", "closing", "gemm_option", "tuned")}}
+    plans = [{"step": k, **{f: run.step_info(k)[f] for f in ("mu", "closing", "gemm_option", "tuned", "group")}}
              for k in range(args.warmup + 1, nsteps + 1)]
     tune = run.tune_stats()
     value, ms_max = sync.throughput(flops, start.elapsed_time(stop))
@@ -438,25 +442,44 @@ def main():
     # ---------------------------------------------------------------- accuracy vs FP64
     accuracy = {}
     nref = args.ref_steps if args.ref_steps >= 0 else (8 if D <= 8 else (6 if D <= 11 else (5 if D == 12 else 4)))
-    if impure:
-        nref = 0                  # the FP64-grade mode propagates the pure tensor only
     nver = max(8 if D <= 8 else 3, nref)
-    # the first temperature of this rank's workload, with its field and impure tensors
-    ver = HOTRG(batch=1, dcut_max=D, precision=args.precision, impure=impure, schedule=sched[:nver])
-    ver.set_option(OPT_GEMM_VARIANT, args.gemm_variant)
-    ver.init_tensor(beta, hfield)
-    mixed_lnz = []
-    for i in range(nver):
-        ver.step(*sched[i])
-        mixed_lnz.append(float(ver.lnZ()[0]))
-    del ver
-    torch.cuda.empty_cache()
+    def verify(maxnorm):
+        """The first temperature of this rank's workload, with its field and impure tensors:
+        ln Z/V (and E, m) after each of the first nver steps, and the fp16 split statistics of
+        the last step's operands."""
+        ver = HOTRG(batch=1, dcut_max=D, precision=args.precision, impure=impure, schedule=sched[:nver],
+                    maxnorm=maxnorm)
+        ver.set_option(OPT_GEMM_VARIANT, args.gemm_variant)
+        ver.init_tensor(beta, hfield)
+        lnz, ob = [], []
+        for i in range(nver):
+            ver.step(*sched[i])
+            lnz.append(float(ver.lnZ()[0]))
+            if impure:
+                e, _ = ver.energy()
+                ob.append((float(e[0]), float(ver.magnetization()[0])))
+        st = ver.split_stats() if args.precision == "fp16x3" else None
+        del ver
+        torch.cuda.empty_cache()
+        return lnz, ob, st
+
+    mixed_lnz, mixed_obs, split_default = verify(args.maxnorm)
+    # the other operand scalings of the fp16 planes, on the same steps (split statistics and
+    # ln Z/V; compared with the FP64 references below)
+    split_runs = {}
+    if args.precision == "fp16x3" and rank == 0 and D <= 8:     # two more verification runs: cheap at D <= 8
+        for mode in (1, 2, 0):
+            lz, _, st = (mixed_lnz, None, split_default) if mode == args.maxnorm else verify(mode)
+            split_runs[mode] = (lz, st)
     if rank == 0 and D == 8 and args.batch == 1 and not impure and os.path.exists(GOLDEN_D8):
         with open(GOLDEN_D8) as f:
             gd = json.load(f)
         diffs = [abs(mixed_lnz[i] - s["lnZ"]) for i, s in enumerate(gd["steps"][:8])]
         accuracy["max_abs_dlnZ_vs_fp64_oracle_steps1to8"] = max(diffs)
         accuracy["dlnZ_per_step"] = diffs
+        split_ref = [s["lnZ"] for s in gd["steps"][:8]]
+    else:
+        split_ref = None
 
     # ---------------------------------------------------------------- FP64 GPU path
     # steps 1..3 (the DFMA product; skipped where the FP64-grade reference below covers them,
@@ -466,12 +489,19 @@ def main():
     n64 = 3 if (D <= 8 or nref == 0) else 0
     r64 = HOTRG(batch=1, dcut_max=D, precision="fp64", impure=impure, schedule=sched[:max(1, n64 + ntimed64)])
     r64.init_tensor(beta, hfield)
-    d64 = []
+    d64, dE, dm = [], [], []
     for i in range(n64):
         r64.step(*sched[i])
         d64.append(abs(mixed_lnz[i] - float(r64.lnZ()[0])))
+        if impure:
+            e, _ = r64.energy()
+            dE.append(abs(mixed_obs[i][0] - float(e[0])))
+            dm.append(abs(mixed_obs[i][1] - float(r64.magnetization()[0])))
     if n64:
         accuracy["abs_dlnZ_mixed_vs_fp64_gpu_steps1to3"] = d64
+    if dE:
+        accuracy["abs_dE_per_site_mixed_vs_fp64_gpu_steps1to3"] = dE
+        accuracy["abs_dmagnetization_mixed_vs_fp64_gpu_steps1to3"] = dm
     if ntimed64:
         barrier()
         f64 = r64.step_flops(*sched[3])[1]
@@ -494,14 +524,15 @@ def main():
     # tensor cores (error below 2^-40 of the operands): the steady-state reference at large
     # D_cut, where the DFMA product takes minutes to hours per step; its last step is timed.
     fp64oz = None
+    oz_vals = []
     if nref > 0:
-        oz = HOTRG(batch=1, dcut_max=D, precision="fp64oz", schedule=sched[:nref])
+        oz = HOTRG(batch=1, dcut_max=D, precision="fp64oz", impure=impure, schedule=sched[:nref])
         oz.init_tensor(beta, hfield)
-        doz = []
+        doz, oz_vals, dEoz, dmoz = [], [], [], []
         ms_oz, fl_last = None, 0.0
         for i in range(nref):
             if i == nref - 1:
-                fl_last = oz.step_flops(*sched[i])[1]      # flops of the step about to run
+                fl_last = step_flops(oz, *sched[i], i) / args.batch   # the step about to run, one temperature
                 barrier()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(oz.stream)
@@ -510,21 +541,53 @@ def main():
                 e1.record(oz.stream)
                 barrier()
                 ms_oz = allmax(e0.elapsed_time(e1))
-            doz.append(abs(mixed_lnz[i] - float(oz.lnZ()[0])))
+            oz_vals.append(float(oz.lnZ()[0]))
+            doz.append(abs(mixed_lnz[i] - oz_vals[-1]))
+            if impure:
+                e, _ = oz.energy()
+                dEoz.append(abs(mixed_obs[i][0] - float(e[0])))
+                dmoz.append(abs(mixed_obs[i][1] - float(oz.magnetization()[0])))
         accuracy[f"abs_dlnZ_mixed_vs_fp64oz_steps1to{nref}"] = doz
         accuracy["max_abs_dlnZ_mixed_vs_fp64oz"] = max(doz)
+        if impure:
+            accuracy[f"abs_dE_per_site_mixed_vs_fp64oz_steps1to{nref}"] = dEoz
+            accuracy[f"abs_dmagnetization_mixed_vs_fp64oz_steps1to{nref}"] = dmoz
         fp64oz = {"value": allsum(fl_last) / (ms_oz * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms_oz,
                   "timed_step": nref, "steps_compared": nref,
                   "what": "FP64 tensors; block-spin product as 15 exact integer-slice products on the fp16 "
-                          "tensor cores (FP64-grade); the step timed is the last one compared"}
+                          "tensor cores (FP64-grade); the step timed is the last one compared"
+                          + ("; T, S and M propagated (5 products per step)" if impure else "")}
         del oz
         torch.cuda.empty_cache()
+
+    # ---------------------------------------------------------------- fp16 split, per scaling
+    # fractions of the last verification step's operand entries whose hi or lo plane value is
+    # zero or in fp16's subnormal range, the largest |hi| (log2; the planes hold < 2^15), and
+    # each scaling's ln Z/V error against the FP64 reference of those steps
+    split = None
+    if split_runs:
+        ref, ref_name = (split_ref, "fp64_oracle") if split_ref else (oz_vals, "fp64oz")
+        names = {1: "bound: 2^e from sqrt(D_b) x the first pass's largest |output|",
+                 2: "exact: 2^e from the operand's largest |entry| (max pass)", 0: "fixed 2^14"}
+        split = {"default": args.maxnorm, "step": nver, "modes": {}}
+        for mode, (lz, st) in split_runs.items():
+            n = max(1, st["entries"])
+            d = {"scale": names[mode], "entries": st["entries"], "hi_zero_frac": st["hi_zero"] / n,
+                 "hi_subnormal_frac": st["hi_subnormal"] / n, "lo_zero_frac": st["lo_zero"] / n,
+                 "lo_subnormal_frac": st["lo_subnormal"] / n,
+                 "hi_max_log2_A_B": [math.log2(x) if x > 0 else None for x in st["hi_max"]],
+                 "max_abs_dlnZ_vs_default": max(abs(a - b) for a, b in zip(lz, split_runs[args.maxnorm][0]))}
+            m = min(len(ref or []), len(lz))
+            if m:
+                d[f"max_abs_dlnZ_vs_{ref_name}_steps1to{m}"] = max(abs(lz[i] - ref[i]) for i in range(m))
+            split["modes"][str(mode)] = d
 
     # ---------------------------------------------------------------- end to end, public API
     e2e = None
     if args.e2e and args.batch == 1 and not impure:
         full = [(i % 4, D) for i in range(LATTICE_STEPS)]
-        job = HOTRG(batch=1, dcut_max=D, precision=args.precision, schedule=full, autotune=bool(args.autotune))
+        job = HOTRG(batch=1, dcut_max=D, precision=args.precision, schedule=full, autotune=bool(args.autotune),
+                    maxnorm=args.maxnorm)
         job.set_option(OPT_GEMM_VARIANT, args.gemm_variant)
         bh = torch.tensor([beta], dtype=torch.float64).pin_memory()
         hh = torch.tensor([H_WORK], dtype=torch.float64).pin_memory()
@@ -571,6 +634,7 @@ def main():
         "config": workload_config(args, world),
         "run_config": {"precision": f"{args.precision} (fp32 storage)", "cuda_graphs": bool(args.graphs),
                        "gemm_variant": args.gemm_variant, "autotune": bool(args.autotune),
+                       "maxnorm": args.maxnorm,
                        "l2": f"operands larger than L2 (GEMM A and B: 2 x "
                              f"{(4 if args.precision == 'fp16x3' else 8) * D ** 10 / 1e9:.1f} GB per step, hi + lo)"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -585,7 +649,7 @@ def main():
         "gpu_launches": prof["launches"],
         "plans": plans, "autotuner": tune,
         "clocks": clk.summary(),
-        "fp64": fp64, "fp64oz": fp64oz, "accuracy": accuracy, "lnZ_over_V_after_timed_steps": lnz_run, "observables": obs,
+        "fp64": fp64, "fp64oz": fp64oz, "accuracy": accuracy, "fp16_split": split, "lnZ_over_V_after_timed_steps": lnz_run, "observables": obs,
         "cpu_baseline": cpu, "e2e": e2e,
     }
     if rank == 0:

@@ -54,16 +54,19 @@ typedef enum {
  * HOTRG_TF32X3: tcgen05 tensor cores, each FP32 operand split into tf32 hi + lo,
  *               products hi*hi + hi*lo + lo*hi accumulated in FP32 (TMEM, promoted
  *               to FP32 registers every 32 k).
- * HOTRG_FP16X3: the same three products on fp16 hi + lo planes of 2^14 x (kind::f16:
- *               twice the tensor rate and half the operand bytes of TF32X3; the scale
- *               keeps normalised tensors inside fp16's normal range).
+ * HOTRG_FP16X3: the same three products on fp16 hi + lo planes of 2^e x, e a power of two
+ *               per operand from its magnitude (max-norm scaling, HOTRG_OPT_MAXNORM),
+ *               removed in the GEMM epilogue (kind::f16: twice the tensor rate and half
+ *               the operand bytes of TF32X3).
  * HOTRG_FP64OZ: FP64-grade block-spin product on the fp16 tensor cores (Ozaki-type
- *               splitting): tensors stored in FP64, each GEMM operand split into 5 planes of
- *               exact 8-bit integer slices, the 15 leading slice products summed exactly
- *               per 256-k chunk (FP32 in TMEM) and across chunks as float pairs; error
- *               below 2^-40 of the operands' magnitudes. Pure tensor only (impure_mask
- *               must be 0): the reference for the mixed modes at large D_cut, where the
- *               DFMA product of HOTRG_FP64 takes about 25 min per step (D_cut = 10).
+ *               splitting): tensors stored in FP64, each GEMM operand scaled by a power of
+ *               two below 1 in magnitude (from its exact largest entry) and split into 5
+ *               planes of exact 8-bit integer slices, the 15 leading slice products summed
+ *               exactly per 256-k chunk (FP32 in TMEM) and across chunks as float pairs;
+ *               error below 2^-40 of the operands' largest magnitudes per product term.
+ *               Pure and impure tensors: the reference for the mixed modes at large D_cut,
+ *               where the DFMA product of HOTRG_FP64 takes about 25 min per step (D_cut =
+ *               10).
  * In every mode the Gram matrices are accumulated in FP64 (float pairs of FP32 slice
  * sums for FP32-stored tensors), and the eigensolver, the isometries, the norm and
  * ln Z / V are FP64. */
@@ -95,6 +98,8 @@ typedef struct {
   int gemm_option;   /* HOTRG_OPT_GEMM_VARIANT value of the block-spin GEMM (-1: the
                         CUDA-core GEMM of the FP64 and FP32 modes)                      */
   int tuned;         /* 1 if closing and gemm_option came from the autotuner's cache    */
+  int group;         /* batch elements contracted together (each launch of the
+                        contraction covered this many temperatures)                     */
 } hotrg_step_record;
 
 /* Create a context for `batch` runs with bond dimensions up to `dcut_max`
@@ -210,8 +215,34 @@ hotrg_status hotrg_step_flops(const hotrg_ctx* ctx, int dir, int dcut, double* m
  *   autotuner's cache (hotrg_autotune), timing a step shape it has not seen before the step
  *   runs (outside any capture; with HOTRG_OPT_GRAPHS, tune every shape with
  *   hotrg_autotune before the first captured step). 0 (default) = the planner's choice:
- *   the closing direction with the fewest flops and the option's pipeline. Errors: EINVAL. */
-enum { HOTRG_OPT_JACOBI_SWEEPS = 1, HOTRG_OPT_GEMM_VARIANT = 2, HOTRG_OPT_GRAPHS = 3, HOTRG_OPT_AUTOTUNE = 4 };
+ *   the closing direction with the fewest flops and the option's pipeline.
+ * HOTRG_OPT_GROUP: most batch elements contracted together, 0..96 (0, the default: as many
+ *   as the planner finds best). The isometry stage and the normalisation always run once
+ *   for the whole batch; the contraction runs group by group, every launch covering the
+ *   group (tensor passes over all its elements, one grouped GEMM for all its outputs). The
+ *   planner compares one element at a time (slices with the fewest GEMM blocks) with groups
+ *   that fit the workspace with B unsliced, and takes the fewest launches; results do not
+ *   depend on the grouping (every element's arithmetic is the same, its operand scales
+ *   included).
+ * HOTRG_OPT_MAXNORM: FP16X3 operand scaling. Each operand side of each batch element is
+ *   multiplied by a power of two 2^e with B 2^e in [2^14, 2^15), B a bound of its largest
+ *   magnitude m, so that no entry overflows the fp16 planes; the GEMM epilogue multiplies by
+ *   2^-(eA + eB) (exact). 1 (default) = B recorded by the first half-contraction pass, no
+ *   extra pass: sqrt(D_b) times that pass's largest |output|, a bound of every operand entry
+ *   by Cauchy-Schwarz (the second pass applies part of an isometry column); the largest
+ *   entry then sits at most log2(B / m) + 1 bits below 2^15. 2 = B = m, from a max pass
+ *   that computes the second pass's outputs once more (largest entry in [2^14, 2^15)).
+ *   0 = the fixed 2^14 of every operand. Other precisions ignore it (FP64OZ always scales
+ *   by the exact largest magnitude, from a max pass).
+ * Errors: EINVAL. */
+enum {
+  HOTRG_OPT_JACOBI_SWEEPS = 1,
+  HOTRG_OPT_GEMM_VARIANT = 2,
+  HOTRG_OPT_GRAPHS = 3,
+  HOTRG_OPT_AUTOTUNE = 4,
+  HOTRG_OPT_GROUP = 5,
+  HOTRG_OPT_MAXNORM = 6
+};
 hotrg_status hotrg_set_option(hotrg_ctx* ctx, int option, int value);
 
 /* Autotuner: times, on the GPU and on the run's current tensors, every plan of the step
@@ -254,6 +285,24 @@ hotrg_status hotrg_profile_enable(hotrg_ctx* ctx, int enable);
 
 /* Counters since the last hotrg_profile_enable. Synchronises the stream. */
 hotrg_status hotrg_profile_read(hotrg_ctx* ctx, hotrg_profile* out);
+
+/* Rounding statistics of the FP16X3 split (max-norm scaling, HOTRG_OPT_MAXNORM), over the
+ * operands of the last block-spin GEMM of the last step (the A and B planes still in the
+ * workspace: every tensor of the last group of batch elements, the last slice block of
+ * each side). An operand entry x is stored as hi = fp16(2^e x), lo = fp16(2^e x - hi). */
+typedef struct {
+  uint64_t entries;       /* operand entries counted (A and B)                                */
+  uint64_t hi_zero;       /* entries whose hi is zero                                         */
+  uint64_t hi_subnormal;  /* entries whose hi is nonzero and below 2^-14 (fp16 subnormal)     */
+  uint64_t lo_zero;       /* entries whose lo is zero (hi holds 2^e x exactly)                */
+  uint64_t lo_subnormal;  /* entries whose lo is nonzero and below 2^-14: bits lost           */
+  double hi_max[2];       /* largest |hi| of the A and of the B operands (below 2^15)        */
+} hotrg_split_counts;
+
+/* Counts over the last step's operands (reads the workspace; synchronises the stream).
+ * Errors: EUNSUPPORTED unless the precision is FP16X3; ESTATE before the first step after
+ * hotrg_init_tensor / hotrg_set_tensor. */
+hotrg_status hotrg_split_stats(hotrg_ctx* ctx, hotrg_split_counts* out);
 
 /* HOSVD isometry of one transverse direction, for callers that cannot allocate device
  * memory. The paper has no counterpart: this is an allocation-free form of the isometry

@@ -5,5 +5,5 @@ package holds its sources (csrc/), its build script and a thin ctypes binding.
 """
 
 from .hotrg import (FP32, FP64, IMPURE_NONE, IMPURE_SIGMA, IMPURE_SIGMASIGMA, OPT_AUTOTUNE,  # noqa: F401
-                    OPT_GEMM_VARIANT, OPT_GRAPHS, OPT_JACOBI_SWEEPS, PRECISIONS, SYMBOLS, TF32X3, HOTRG,
-                    HotrgError, library_path)
+                    OPT_GEMM_VARIANT, OPT_GRAPHS, OPT_GROUP, OPT_JACOBI_SWEEPS, OPT_MAXNORM, PRECISIONS, SYMBOLS,
+                    TF32X3, HOTRG, HotrgError, library_path)

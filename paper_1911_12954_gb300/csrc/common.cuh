@@ -34,9 +34,40 @@ struct TTMArgs {
   int64_t in_sj1, in_sj2, u_sj1, u_sj2;
   int64_t outer, inner;
   double alpha, beta;
+  // nb batch elements in one launch: element e reads in + e in_bs and U + e u_bs and writes
+  // out + e out_bs (output strides count fp16 values in the fp16 split modes)
+  int nb;
+  int64_t in_bs, u_bs, out_bs;
+  // split modes: an upper bound of the operand's magnitudes (bits of a non-negative float)
+  // that sets its power-of-two scale (nullptr: the fixed scale); kTTMMaxAbs and kTTMStoreMax:
+  // where the pass accumulates amax_mul times its largest |output| (atomicMax, rounded up).
+  // One word per batch element: element e uses amax[e].
+  unsigned* amax;
+  float amax_mul;
 };
 
-enum TTMMode { kTTMStore = 0, kTTMSplitTF32 = 1, kTTMAccumulate = 2, kTTMSplitF16 = 3, kTTMSplitOz = 4 };
+enum TTMMode {
+  kTTMStore = 0,
+  kTTMSplitTF32 = 1,
+  kTTMAccumulate = 2,
+  kTTMSplitF16 = 3,
+  kTTMSplitOz = 4,
+  kTTMMaxAbs = 5,    // computes the outputs, keeps only their largest magnitude (a.amax)
+  kTTMStoreMax = 6   // kTTMStore, and accumulates the largest |output| as kTTMMaxAbs does
+};
+// Per-operand power-of-two scale of the split modes (max-norm scaling): with m the largest
+// magnitude of the operand and m < 2^ex (frexp), the operand is multiplied by 2^(top - ex),
+// so its largest entry lies in [2^(top-1), 2^top): top = 15 for the fp16 hi/lo planes (fp16's
+// largest finite value is 65504), 0 for the integer slices (which need |x| < 1). m = 0 gives
+// the exponent top. The product of two such operands carries 2^(eA + eB), which the GEMM
+// removes. Computed identically by the split passes and the GEMM epilogues.
+__host__ __device__ inline int split_exponent(unsigned mbits, int top) {
+  if (mbits == 0u) return top;
+  const int ex = (int)((mbits >> 23) & 0xffu) - 126;   // m = f 2^ex, f in [0.5, 1)
+  return top - ex;
+}
+constexpr int kF16Top = 15;
+constexpr int kOzTop = 0;
 // FP64-grade tensor-core mode (Ozaki-type splitting): an FP64 operand x with |x| <= 1 is
 // stored as kOzSlices fp16 planes of integers v_i, x = sum_i v_i 2^(-8 (i + 1)) up to
 // 2^-41; |v_0| <= 256, |v_i| <= 128 for i >= 1. Plane p of an operand starts p times the
@@ -151,9 +182,12 @@ cudaError_t launch_jacobi(const EigPack& jobs, int njobs, int nmax, double clust
 cudaError_t launch_wait_selftest(int* status, unsigned long long limit_ns, cudaStream_t st);
 // FP64-grade product on the fp16 tensor cores: C[M][N] (double, row stride ldc) =
 // alpha A B^T with A, B given as kOzSlices integer planes each (K panels as in
-// launch_gemm_group; plane p of A at A + p aps elements, of B at B + p bps).
+// launch_gemm_group; plane p of A at A + p aps elements, of B at B + p bps), each operand
+// sliced after scaling by 2^split_exponent(*amax, kOzTop) (amax_a, amax_b; nullptr: no scale);
+// accumulate: C += alpha A B^T.
 cudaError_t launch_gemm_oz(const void* A, const void* B, int64_t aps, int64_t bps, int64_t Kp, int64_t kps, int64_t P,
-                           int64_t M, int64_t N, double* C, int64_t ldc, double alpha, int* status, cudaStream_t st);
+                           int64_t M, int64_t N, double* C, int64_t ldc, double alpha, const unsigned* amax_a,
+                           const unsigned* amax_b, bool accumulate, int* status, cudaStream_t st);
 // One output of a grouped block-spin GEMM: C = alpha * sum_{s < nseg} A_{a[s]} B_{b[s]}^T,
 // where A_w, B_w are the w-th operand tensors of the launch (the k loop runs over the nseg
 // segments one after the other, each the full K).
@@ -163,10 +197,16 @@ struct GemmProblem {
   int nseg;
   int a[2], b[2];
 };
-constexpr int kMaxGemmProblems = 3;
+constexpr int kMaxGemmProblems = 96;   // 32 temperatures x 3 tensors per launch
 struct GemmGroup {
   GemmProblem p[kMaxGemmProblems];
   int nprob;
+  // fp16 operands scaled by their max-norm exponents (split_exponent(amax[e], kF16Top), one
+  // word per batch element e, problem pb of element pb / per_elem): the epilogue multiplies by
+  // 2^-(eA + eB); nullptr: the operands carry no such scale
+  const unsigned* amax_a;
+  const unsigned* amax_b;
+  int per_elem;
 };
 // Tensor-core GEMM over W operand tensors per plane (hi, lo), each [P][rows][kps] in K
 // panels, tensor w of a plane aws (A) or bws (B) elements after tensor w - 1; every problem
@@ -181,13 +221,19 @@ template <typename R>
 cudaError_t launch_init(const double* beta, const double* h, R* T, R* S, int64_t slot, double* lnz_acc,
                         int batch, cudaStream_t st);
 template <typename R>
-cudaError_t launch_norm(const R* x, int64_t n, double* partial, const int* step, double* c_out, double* lnz_acc,
+cudaError_t launch_norm(const R* x, int64_t n, int nb, int64_t xstride, double* partial, const int* step,
+                        double* c_out, double* lnz_acc,
                         DevRecord* rec_b, int* status, cudaStream_t st);
 cudaError_t launch_step_end(int* step, cudaStream_t st);
+// Counts over one fp16 plane in K panels (nrows rows of kps values, the first Kp of each
+// read): out[0] += zero entries, out[1] += entries in fp16's subnormal range (nonzero, below
+// 2^-14), out[2] = max(out[2], bits of the largest magnitude).
+cudaError_t launch_plane_stats(const void* plane, int64_t nrows, int64_t Kp, int64_t kps, unsigned long long* out,
+                               cudaStream_t st);
 void jacobi_prepare();
 void gemm_prepare();
 template <typename R>
-cudaError_t launch_scale(R* x, int64_t n, const double* c, cudaStream_t st);
+cudaError_t launch_scale(R* x, int64_t n, int nb, int64_t xstride, const double* c, cudaStream_t st);
 template <typename R>
 cudaError_t launch_trace(const R* T, int64_t slot, const int* dims, int batch, double* out, cudaStream_t st);
 template <typename R>

@@ -305,6 +305,14 @@ __device__ __forceinline__ void promote_chunk(uint32_t taddr, float* acc) {
   }
 }
 
+// Output factor of problem pb: its alpha, times 2^-(eA + eB) for operands scaled by their
+// max-norm exponents.
+__device__ __forceinline__ float out_alpha(const GemmGroup& g, int pb) {
+  if (!g.amax_a) return g.p[pb].alpha;
+  const int e = pb / g.per_elem;
+  return ldexpf(g.p[pb].alpha, -(split_exponent(g.amax_a[e], kF16Top) + split_exponent(g.amax_b[e], kF16Top)));
+}
+
 // alpha * acc for one thread's 128 columns of row m (guarded).
 __device__ __forceinline__ void store_row(float* __restrict__ C, int64_t ldc, int M, int N, int64_t m, int n0,
                                           const float* acc, float alpha) {
@@ -484,7 +492,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
       }
       if (!ok) break;
-      store_row(grp.p[pb].C, ldc, M, N, (int64_t)tm * BM + row, tn * BN + h * (BN / 2), acc, grp.p[pb].alpha);
+      store_row(grp.p[pb].C, ldc, M, N, (int64_t)tm * BM + row, tn * BN + h * (BN / 2), acc, out_alpha(grp, pb));
     }
   }
   fence_before();
@@ -679,7 +687,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
       }
       if (!ok) break;
-      store_row(grp.p[pb].C, ldc, M, N, (int64_t)tm * BM + row, tn * BN + h * (BN / 2), acc, grp.p[pb].alpha);
+      store_row(grp.p[pb].C, ldc, M, N, (int64_t)tm * BM + row, tn * BN + h * (BN / 2), acc, out_alpha(grp, pb));
     }
   }
   fence_before();
@@ -706,8 +714,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 // chunk is below 2^-40 of the result. After each chunk the epilogue adds group 0 and 2^-8
 // group 1 into a float pair hi + lo (TwoSum) and 2^-16, 2^-24, 2^-32 times groups 2, 3, 4 into
 // lo alone (lo stays below 2^-15 of hi, so its FP32 rounding is below 2^-39 of the result),
-// and writes alpha 2^-16 (hi + lo) in FP64 at the end: no FP64 arithmetic in the k loop (a few
-// FP64 operations per clock per SM on this chip).
+// and writes alpha 2^-16 (hi + lo) in FP64 at the end (added to C when accumulating): no FP64
+// arithmetic in the k loop (a few FP64 operations per clock per SM on this chip).
 //   Tile 128 x 96 per CTA, one CTA per SM; k-blocks of 32 fp16 (64-byte swizzle), 3 stages
 //   of 10 planes (70 KB); warp 0 TMA, warp 1 MMA (15 products x 2 k-steps per k-block),
 //   warps 2..13 promotion (warp w: TMEM lane quarter w % 4, 32 of the 96 columns).
@@ -755,7 +763,8 @@ __device__ __forceinline__ void two_sum_into(float& hi, float& lo, float x) {
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     gemm_oz_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
-                   double* __restrict__ C, int64_t ldc, int M, int N, int Kp, int P, double alpha, int* status) {
+                   double* __restrict__ C, int64_t ldc, int M, int N, int Kp, int P, double alpha,
+                   const unsigned* amax_a, const unsigned* amax_b, int accumulate, int* status) {
   using CF = CfgOz;
   constexpr int STAGES = CF::STAGES, BK = CF::BK, STAGE_BYTES = CF::STAGE_BYTES, KPC = CF::KB_PER_CHUNK;
   extern __shared__ uint8_t smem_raw[];
@@ -914,10 +923,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       const int n0 = tn * OZ_BN + cpart * OZ_COLS;
       if (m < M) {
         double* crow = C + m * ldc + n0;
-        const double a16 = alpha * 1.52587890625e-05;   // alpha 2^-16
+        // alpha 2^-16, and 2^-(eA + eB) for the operands' max-norm scales
+        const int es = amax_a ? split_exponent(*amax_a, kOzTop) + split_exponent(*amax_b, kOzTop) : 0;
+        const double a16 = ldexp(alpha, -16 - es);
 #pragma unroll
         for (int j = 0; j < OZ_COLS; ++j)
-          if (n0 + j < N) crow[j] = a16 * ((double)hi[j] + (double)lo[j]);
+          if (n0 + j < N) crow[j] = a16 * ((double)hi[j] + (double)lo[j]) + (accumulate ? crow[j] : 0.0);
       }
     }
   }
@@ -1084,6 +1095,7 @@ cudaError_t launch_gemm_group(const void* Ahi, const void* Alo, const void* Bhi,
     for (int sg = 0; sg < pr.nseg; ++sg)
       if (pr.a[sg] < 0 || pr.a[sg] >= W || pr.b[sg] < 0 || pr.b[sg] >= W) return cudaErrorInvalidValue;
   }
+  if ((g.amax_a == nullptr) != (g.amax_b == nullptr) || (g.amax_a && g.per_elem < 1)) return cudaErrorInvalidValue;
   const bool f16 = variant >= 2 && variant <= 5;
   if ((kps & (variant == 5 ? 63 : (f16 ? 7 : 3))) || kps < Kp) return cudaErrorInvalidValue;
   if ((((uintptr_t)Ahi) | ((uintptr_t)Alo) | ((uintptr_t)Bhi) | ((uintptr_t)Blo)) & 15) return cudaErrorInvalidValue;
@@ -1105,7 +1117,8 @@ cudaError_t launch_gemm_group(const void* Ahi, const void* Alo, const void* Bhi,
 // FP64-grade GEMM (gemm_oz_kernel): C = alpha A B^T, A and B as kOzSlices integer planes in
 // K panels, plane p of A at A + p aps elements (B: bps); kps % 8 == 0.
 cudaError_t launch_gemm_oz(const void* A, const void* B, int64_t aps, int64_t bps, int64_t Kp, int64_t kps, int64_t P,
-                           int64_t M, int64_t N, double* C, int64_t ldc, double alpha, int* status, cudaStream_t st) {
+                           int64_t M, int64_t N, double* C, int64_t ldc, double alpha, const unsigned* amax_a,
+                           const unsigned* amax_b, bool accumulate, int* status, cudaStream_t st) {
   using namespace tc;
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (!A || !B || !C || Kp <= 0 || P <= 0 || M > 0x7fffffff || N > 0x7fffffff || Kp * P > 0x7fffffff || ldc < N ||
@@ -1120,8 +1133,9 @@ cudaError_t launch_gemm_oz(const void* A, const void* B, int64_t aps, int64_t bp
     return cudaErrorInvalidValue;
   const int64_t tiles = ((M + BM - 1) / BM) * ((N + OZ_BN - 1) / OZ_BN);
   const int grid = (int)(tiles < dv->sms ? tiles : dv->sms);
+  if ((amax_a == nullptr) != (amax_b == nullptr)) return cudaErrorInvalidValue;
   gemm_oz_kernel<<<grid, OZ_THREADS, CfgOz::SMEM_BYTES, st>>>(mA, mB, C, ldc, (int)M, (int)N, (int)Kp, (int)P, alpha,
-                                                              status);
+                                                              amax_a, amax_b, accumulate ? 1 : 0, status);
   return cudaGetLastError();
 }
 

@@ -61,6 +61,7 @@ struct StepPlan {
   int R[4];               // rows of the half-Gram per direction = D_nu D_mu
   int Rmax, nmax, nchunks;
   int batch;              // batch elements whose isometry stages run together
+  int ne;                 // batch elements contracted together (one group of launches)
   int gemm_opt;           // tensor-core GEMM pipeline option of this step (-1: the context's)
   bool tuned;             // closing direction and pipeline taken from the autotuner's cache
   double main_flops, total_flops;
@@ -101,6 +102,11 @@ struct hotrg_ctx {
   int gemm_variant = 0;
   bool use_graphs = false;
   bool autotune = false;
+  int group_max = 0;           // most temperatures contracted together (0: as many as fit)
+  int maxnorm = 1;             // FP16X3 operand scaling: a ScaleMode (0: the fixed 2^14)
+  StepPlan last_plan{};        // plan of the last step (its last block's operands stay in scratch)
+  int last_kstep = -1;         // steps done before it (-1: none since the last init)
+  int group_hist[kMaxSteps];   // temperatures contracted together at each step
   int c_hist[kMaxSteps];       // closing direction of each step
   int opt_hist[kMaxSteps];     // GEMM pipeline option of each step (-1: CUDA cores)
   int tuned_hist[kMaxSteps];   // plan from the autotuner's cache
@@ -178,7 +184,49 @@ inline cudaError_t launch_ttm_r(const R* in, const R* U, R* out, R* lo, const TT
     g_last_error = "TTM launch refused: extent outside its buffer";
     return cudaErrorInvalidValue;
   }
+  // batch elements must not overlap: each element's stride covers one element's buffer
+  if (a.nb > 1 && (a.in_bs < g_lim_in || (U && a.u_bs < g_lim_u) || a.out_bs < g_lim_out)) {
+    g_last_error = "TTM launch refused: batch stride shorter than one element's buffer";
+    return cudaErrorInvalidValue;
+  }
   return launch_ttm<R, R, R>(in, U, out, lo, a, mode, st);
+}
+
+// Per-element strides of a group of batch elements contracted together (element e of the
+// group at base + e * stride, in elements of each buffer's type; operand planes in operand
+// elements).
+struct ElemStrides {
+  int ne = 1;
+  int64_t T = 0;     // tensors (current and next buffer): the slot capacity
+  int64_t U = 0;     // isometries
+  int64_t O1 = 0;    // first half-contraction pass
+  int64_t op = 0;    // GEMM operand planes (all tensors of one element)
+  int64_t C = 0;     // GEMM outputs (all tensors of one element)
+  int64_t O3 = 0;    // first closing pass
+};
+
+// Phases of an operand build (build_A, build_B): the first half-contraction pass into O1, the
+// max pass of the second (largest |operand| into the scratch word, for max-norm scaling), the
+// second pass writing the operand planes.
+enum BuildPhase { kPass1 = 1, kPassMax = 2, kPass2 = 4 };
+
+// How an operand side's max-norm scale is found (the word amax of the side):
+//  * kScaleBound (fp16 planes): the first pass records sqrt(J) times its largest |output|,
+//    J the length of the second pass's contraction. The second pass computes A[f, r] =
+//    sum_j U[j, r] O1[f, j] with U[., r] part of a column of an isometry (norm <= 1), so by
+//    Cauchy-Schwarz |A[f, r]| <= ||O1[f, .]||_2 <= sqrt(J) max |O1|: a bound of the operand's
+//    largest magnitude at no extra pass, at most log2(sqrt(J)) bits above it;
+//  * kScaleExact (FP64-grade integer slices, whose precision is fixed-point relative to the
+//    scale): a max pass computes the second pass's outputs once more and records their
+//    exact largest magnitude.
+enum ScaleMode { kScaleNone = 0, kScaleBound = 1, kScaleExact = 2 };
+
+inline TTMArgs batched(TTMArgs t, int ne, int64_t in_bs, int64_t u_bs, int64_t out_bs) {
+  t.nb = ne;
+  t.in_bs = in_bs;
+  t.u_bs = u_bs;
+  t.out_bs = out_bs;
+  return t;
 }
 inline void ttm_limits(int64_t in, int64_t u, int64_t out) {
   g_lim_in = in;
@@ -220,6 +268,7 @@ StepPlan make_plan(const int D[4], int mu, int dcut, int prec, int batch = 1, in
   StepPlan p{};
   p.mu = mu;
   p.batch = batch;
+  p.ne = 1;
   p.gemm_opt = -1;
   for (int n = 0; n < 4; ++n) {
     p.D[n] = D[n];
@@ -313,6 +362,8 @@ int ntensors(int impure) { return (impure & HOTRG_IMPURE_SIGMASIGMA) ? 3 : ((imp
 struct Scratch {
   size_t gpart, npart, gA, G, jwork, lam, eps, degen, Uside;
   size_t O1A, A, Alo, O1B, B, Blo, C, O3;
+  size_t amax;            // operand magnitude bounds of the current A and B per element (max-norm scaling)
+  size_t stats;           // counters of hotrg_split_stats
   size_t total;
 };
 
@@ -328,7 +379,7 @@ Scratch scratch_layout(const StepPlan& p, int xs, int xs2, int prec, int impure,
   // isometry stage: one copy per batch element (all elements run it together)
   const size_t nb = (size_t)p.batch;
   s.gpart = take(nb * kMaxGramJobs * p.nchunks * p.Rmax * p.Rmax * 8);
-  s.npart = take((size_t)kNormPartials * 8);
+  s.npart = take(nb * kNormPartials * 8);
   s.gA = take(nb * kMaxGramJobs * p.Rmax * p.Rmax * 8);
   s.G = take(nb * 6 * p.nmax * p.nmax * 8);
   s.jwork = take(p.nmax > kJacobiSmemN ? nb * 6 * 2 * p.nmax * p.nmax * 8 : 0);
@@ -340,14 +391,18 @@ Scratch scratch_layout(const StepPlan& p, int xs, int xs2, int prec, int impure,
   const int64_t rowsB = (int64_t)xs2 * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[p.mu];
   const bool split = tc_mode(prec);
   const size_t os = operand_size(prec) * (prec == HOTRG_FP64OZ ? kOzSlices : 1);   // the slices of one operand
-  s.O1A = take((size_t)xs * p.E * rs);
-  s.A = take((size_t)nt * p.P * rowsA * p.kps * os);
-  s.Alo = split ? take((size_t)nt * p.P * rowsA * p.kps * os) : 0;
-  s.O1B = take((size_t)xs2 * p.E * rs);
-  s.B = take((size_t)nt * p.P * rowsB * p.kps * os);
-  s.Blo = split ? take((size_t)nt * p.P * rowsB * p.kps * os) : 0;
-  s.C = take((size_t)nt * rowsA * rowsB * rs);
-  s.O3 = take((size_t)rowsA * rowsB / (p.D[p.c] * p.D[p.c]) * p.chi[p.c] * rs);
+  // contraction: one copy per element of a group (p.ne elements contracted together)
+  const size_t ne = (size_t)p.ne;
+  s.O1A = take(ne * nt * xs * p.E * rs);              // first pass of every tensor's A
+  s.A = take(ne * nt * p.P * rowsA * p.kps * os);
+  s.Alo = split ? take(ne * nt * p.P * rowsA * p.kps * os) : 0;
+  s.O1B = take(ne * nt * xs2 * p.E * rs);
+  s.B = take(ne * nt * p.P * rowsB * p.kps * os);
+  s.Blo = split ? take(ne * nt * p.P * rowsB * p.kps * os) : 0;
+  s.C = take(ne * nt * rowsA * rowsB * rs);
+  s.O3 = take(ne * (size_t)(rowsA * rowsB / (p.D[p.c] * p.D[p.c]) * p.chi[p.c]) * rs);
+  s.amax = take(2 * ne * sizeof(unsigned));     // A side, then B side: one word per element
+  s.stats = take(4 * 3 * sizeof(unsigned long long));   // hotrg_split_stats counters
   s.total = off;
   return s;
 }
@@ -407,6 +462,8 @@ TTMArgs make_ttm(const std::vector<Dim>& d, int J1, int64_t in_sj1, int64_t u_sj
   a.u_sj2 = u_sj2;
   a.alpha = alpha;
   a.beta = beta;
+  a.nb = 1;
+  a.amax_mul = 1.0f;
   for (int i = 0; i < a.rank; ++i) {
     a.dims[i] = d[i].n;
     a.in_st[i] = d[i].in;
@@ -464,7 +521,8 @@ void operand_strides(const StepPlan& p, const std::vector<int64_t>& rn, int64_t 
 
 template <typename R>
 hotrg_status build_A(hotrg_ctx* ctx, const StepPlan& p, const R* P, const R* Ua, const R* Ub, int x0, int xs,
-                     R* O1, R* A, R* Alo, cudaStream_t st) {
+                     R* O1, R* A, R* Alo, cudaStream_t st, const ElemStrides& es, unsigned* amax, int scale,
+                     int phases) {
   const int mu = p.mu, a = p.a, b = p.b, c = p.c;
   const int Da = p.D[a], Db = p.D[b], Dc = p.D[c], Dm = p.D[mu];
   const int ca = p.chi[a], cb = p.chi[b];
@@ -485,9 +543,14 @@ hotrg_status build_A(hotrg_ctx* ctx, const StepPlan& p, const R* P, const R* Ua,
         {Db, ts[2 * b + 1], 0, os[7]},           // b1'
         {Dm, ts[2 * mu + 1], 0, os[8]},          // k = T1.mu'
     };
-    TTMArgs t = make_ttm(d, Da, ts[2 * a], (int64_t)Da * ca, 1, 0, 0, 1.0, 0.0);
+    TTMArgs t = batched(make_ttm(d, Da, ts[2 * a], (int64_t)Da * ca, 1, 0, 0, 1.0, 0.0), es.ne, es.T, es.U, es.O1);
     ttm_limits(p.E, (int64_t)Da * Da * ca - x0, (int64_t)xs * p.E);
-    LK(1, launch_ttm_r<R>(P, Ua + x0, O1, nullptr, t, kTTMStore, st), "ttm A1");
+    const bool bound = amax && scale == kScaleBound;   // the second pass contracts b1: J = Db
+    if (bound) {
+      t.amax = amax;
+      t.amax_mul = sqrtf((float)Db);
+    }
+    if (phases & kPass1) LK(1, launch_ttm_r<R>(P, Ua + x0, O1, nullptr, t, bound ? kTTMStoreMax : kTTMStore, st), "ttm A1");
   }
   // A[(X Y c1 c1' mu1), (a2 b2 a1' b1' k)] = sum_b1 U^b[b1, b2, Y] O1[X, b1, ...]
   {
@@ -508,14 +571,19 @@ hotrg_status build_A(hotrg_ctx* ctx, const StepPlan& p, const R* P, const R* Ua,
     TTMArgs t = make_ttm(d, Db, os[1], (int64_t)Db * cb, 1, 0, 0, 1.0, 0.0);
     const int mode = !Alo ? kTTMStore : split_mode(ctx->prec);
     ttm_limits((int64_t)xs * p.E, (int64_t)Db * Db * cb, p.P * ((int64_t)xs * cb * Dc * Dc * Dm) * p.kps);
-    LK(1, launch_ttm_r<R>(O1, Ub, A, Alo, t, mode, st), "ttm A2");
+    t = batched(t, es.ne, es.O1, es.U, es.op);
+    t.amax = amax;   // max-norm scaling (nullptr: none): the max pass writes it, the split reads it
+    if ((phases & kPassMax) && amax && scale == kScaleExact)
+      LK(1, launch_ttm_r<R>(O1, Ub, A, Alo, t, kTTMMaxAbs, st), "ttm A max");
+    if (phases & kPass2) LK(1, launch_ttm_r<R>(O1, Ub, A, Alo, t, mode, st), "ttm A2");
   }
   return HOTRG_OK;
 }
 
 template <typename R>
 hotrg_status build_B(hotrg_ctx* ctx, const StepPlan& p, const R* Q, const R* Ua, const R* Ub, int x0, int xs,
-                     R* O1, R* B, R* Blo, cudaStream_t st) {
+                     R* O1, R* B, R* Blo, cudaStream_t st, const ElemStrides& es, unsigned* amax, int scale,
+                     int phases) {
   const int mu = p.mu, a = p.a, b = p.b, c = p.c;
   const int Da = p.D[a], Db = p.D[b], Dc = p.D[c], Dm = p.D[mu];
   const int ca = p.chi[a], cb = p.chi[b];
@@ -536,9 +604,14 @@ hotrg_status build_B(hotrg_ctx* ctx, const StepPlan& p, const R* Q, const R* Ua,
         {Da, 0, (int64_t)Da * ca, os[7]},        // a1'
         {Dm, ts[2 * mu], 0, os[8]},              // k = T2.mu
     };
-    TTMArgs t = make_ttm(d, Da, ts[2 * a + 1], ca, 1, 0, 0, 1.0, 0.0);
+    TTMArgs t = batched(make_ttm(d, Da, ts[2 * a + 1], ca, 1, 0, 0, 1.0, 0.0), es.ne, es.T, es.U, es.O1);
     ttm_limits(p.E, (int64_t)Da * Da * ca - x0, (int64_t)xs * p.E);
-    LK(1, launch_ttm_r<R>(Q, Ua + x0, O1, nullptr, t, kTTMStore, st), "ttm B1");
+    const bool bound = amax && scale == kScaleBound;   // the second pass contracts b1': J = Db
+    if (bound) {
+      t.amax = amax;
+      t.amax_mul = sqrtf((float)Db);
+    }
+    if (phases & kPass1) LK(1, launch_ttm_r<R>(Q, Ua + x0, O1, nullptr, t, bound ? kTTMStoreMax : kTTMStore, st), "ttm B1");
   }
   {
     int64_t o[10];
@@ -558,7 +631,11 @@ hotrg_status build_B(hotrg_ctx* ctx, const StepPlan& p, const R* Q, const R* Ua,
     TTMArgs t = make_ttm(d, Db, os[1], cb, 1, 0, 0, 1.0, 0.0);
     const int mode = !Blo ? kTTMStore : split_mode(ctx->prec);
     ttm_limits((int64_t)xs * p.E, (int64_t)Db * Db * cb, p.P * ((int64_t)xs * cb * Dc * Dc * Dm) * p.kps);
-    LK(1, launch_ttm_r<R>(O1, Ub, B, Blo, t, mode, st), "ttm B2");
+    t = batched(t, es.ne, es.O1, es.U, es.op);
+    t.amax = amax;   // max-norm scaling (nullptr: none): the max pass writes it, the split reads it
+    if ((phases & kPassMax) && amax && scale == kScaleExact)
+      LK(1, launch_ttm_r<R>(O1, Ub, B, Blo, t, kTTMMaxAbs, st), "ttm B max");
+    if (phases & kPass2) LK(1, launch_ttm_r<R>(O1, Ub, B, Blo, t, mode, st), "ttm B2");
   }
   return HOTRG_OK;
 }
@@ -566,7 +643,7 @@ hotrg_status build_B(hotrg_ctx* ctx, const StepPlan& p, const R* Q, const R* Ua,
 // T'[slice] = C x_{(c1 c2)} U^c x_{(c1' c2')} U^c, written into the canonical layout.
 template <typename R>
 hotrg_status close_C(hotrg_ctx* ctx, const StepPlan& p, const R* C, const R* Uc, int x0, int xs, int x20, int xs2,
-                     R* O3, R* Tn, cudaStream_t st) {
+                     R* O3, R* Tn, cudaStream_t st, const ElemStrides& es) {
   const int mu = p.mu, a = p.a, b = p.b, c = p.c;
   const int Dc = p.D[c], Dm = p.D[mu];
   const int cb = p.chi[b], cc = p.chi[c];
@@ -594,7 +671,7 @@ hotrg_status close_C(hotrg_ctx* ctx, const StepPlan& p, const R* C, const R* Uc,
     };
     TTMArgs t = make_ttm(d, Dc, ms[2] * N, (int64_t)Dc * cc, Dc, ns[2], cc, 1.0, 0.0);
     ttm_limits((int64_t)xs * cb * Dc * Dc * Dm * N, (int64_t)Dc * Dc * cc, on[0] * os[0]);
-    LK(1, launch_ttm_r<R>(C, Uc, O3, nullptr, t, kTTMStore, st), "ttm close1");
+    LK(1, launch_ttm_r<R>(C, Uc, O3, nullptr, batched(t, es.ne, es.C, es.U, es.O3), kTTMStore, st), "ttm close1");
   }
   {
     int64_t tn[8];
@@ -631,7 +708,7 @@ hotrg_status close_C(hotrg_ctx* ctx, const StepPlan& p, const R* C, const R* Uc,
     TTMArgs t = make_ttm(d, Dc, os[3], (int64_t)Dc * cc, Dc, os[7], cc, 1.0, 0.0);
     R* out = Tn + (int64_t)x0 * tn[2 * a] + (int64_t)x20 * tn[2 * a + 1];
     ttm_limits(on[0] * os[0], (int64_t)Dc * Dc * cc, p.Enew - (int64_t)x0 * tn[2 * a] - (int64_t)x20 * tn[2 * a + 1]);
-    LK(1, launch_ttm_r<R>(O3, Uc, out, nullptr, t, kTTMStore, st), "ttm close2");
+    LK(1, launch_ttm_r<R>(O3, Uc, out, nullptr, batched(t, es.ne, es.O3, es.U, es.T), kTTMStore, st), "ttm close2");
   }
   return HOTRG_OK;
 }
@@ -836,12 +913,14 @@ struct Probe {
   int64_t gemm_rows = 0;
 };
 
-// Step 3 for batch element bidx: the half contractions, the grouped block-spin GEMM and the
-// closing isometries, slice block by slice block, into the element's next tensors (not
-// yet normalised). Reads the element's isometries from its persistent slot.
+// Step 3 for the ne batch elements e0 .. e0 + ne - 1 together: the half contractions, the
+// block-spin GEMM and the closing isometries, slice block by slice block, into the elements'
+// next tensors (not yet normalised), every launch covering the whole group (the tensor passes
+// index the element by blockIdx.y, the tensor-core GEMM takes every (element, tensor) output
+// as one problem of its group). Reads each element's isometries from its persistent slot.
 template <typename R>
-hotrg_status contract_element(hotrg_ctx* ctx, const StepPlan& p, int bidx, cudaStream_t st,
-                              const Probe& pr = Probe()) {
+hotrg_status contract_group(hotrg_ctx* ctx, const StepPlan& p, int e0, int ne, cudaStream_t st,
+                            const Probe& pr = Probe()) {
   const Scratch sc = scratch_layout(p, p.xs, p.xs2, ctx->prec, ctx->impure_active, ctx->rsize);
   char* sb = ctx->ws + ctx->L.persistent_end;
   const int mu = p.mu;
@@ -853,8 +932,9 @@ hotrg_status contract_element(hotrg_ctx* ctx, const StepPlan& p, int bidx, cudaS
   const int64_t rowsB = (int64_t)p.xs2 * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[mu];
   const int ca = p.chi[p.a];
   const bool b_sliced = p.xs2 < ca;
+  if (ne < 1 || ne > p.ne || nt * ne > kMaxGemmProblems) return HOTRG_EINVAL;
   {
-    R* Ur = (R*)(ctx->ws + ctx->L.Ur) + (int64_t)bidx * 4 * kMaxGramN * kMaxLeg;
+    R* Ur = (R*)(ctx->ws + ctx->L.Ur) + (int64_t)e0 * 4 * kMaxGramN * kMaxLeg;
     const R* Ua = Ur + (int64_t)p.a * kMaxGramN * kMaxLeg;
     const R* Ub = Ur + (int64_t)p.b * kMaxGramN * kMaxLeg;
     const R* Uc = Ur + (int64_t)p.c * kMaxGramN * kMaxLeg;
@@ -875,16 +955,45 @@ hotrg_status contract_element(hotrg_ctx* ctx, const StepPlan& p, int bidx, cudaS
     const R* src[3];
     R* dst[3];
     for (int w = 0; w < nt; ++w) {
-      src[w] = tensor_ptr<R>(ctx, w, ctx->cur, bidx);
-      dst[w] = tensor_ptr<R>(ctx, w, 1 - ctx->cur, bidx);
+      src[w] = tensor_ptr<R>(ctx, w, ctx->cur, e0);
+      dst[w] = tensor_ptr<R>(ctx, w, 1 - ctx->cur, e0);
     }
+    // element strides of the group (the scratch holds p.ne copies of every contraction buffer)
+    const int64_t planes = oz ? kOzSlices : 1;
+    ElemStrides esA, esB, esC;
+    esA.ne = esB.ne = esC.ne = ne;
+    esA.T = esB.T = esC.T = ctx->L.cap;
+    esA.U = esB.U = esC.U = 4 * (int64_t)kMaxGramN * kMaxLeg;
+    const int64_t O1Asz = (int64_t)p.xs * p.E, O1Bsz = (int64_t)p.xs2 * p.E;   // one tensor's first pass
+    esA.O1 = nt * O1Asz;
+    esB.O1 = nt * O1Bsz;
+    // max-norm scaling of the fp16 planes and of the integer slices: one magnitude bound per
+    // operand side over every tensor of the group (the segments of an output share 2^(eA+eB))
+    const int scale = ctx->prec == HOTRG_FP16X3 ? ctx->maxnorm : (oz ? kScaleExact : kScaleNone);
+    // (one word per element: an element's scales do not depend on the group it runs in)
+    unsigned* amaxA = scale != kScaleNone ? (unsigned*)(sb + sc.amax) : nullptr;
+    unsigned* amaxB = scale != kScaleNone ? amaxA + p.ne : nullptr;
+    // the first step's M operands are never read (M_1 = A(S) B(S)^T): not built
+    const int nbuild = (kstep == 0 && nt >= 3) ? 2 : nt;
+    esA.op = nt * Asz * planes;
+    esB.op = nt * Bsz * planes;
+    esC.C = nt * Csz;
+    esC.O3 = rowsA * rowsB / ((int64_t)p.D[p.c] * p.D[p.c]) * p.chi[p.c];
     // Padding columns of a panel (kin >= Kp) are never read: the tensor maps stop at Kp and
     // the CUDA-core GEMM at K, so the operand buffers need no clearing.
+    // every tensor's first pass, then (exact scaling) the max pass of every tensor, then the
+    // second passes, which read the side's bound; the bound starts from zero before the
+    // passes that record it
+    auto clear_phase = [&](int ph) { return ph == (scale == kScaleBound ? kPass1 : kPassMax); };
     auto buildB = [&](int x20, int xs2) -> hotrg_status {
-      for (int w = 0; w < nt; ++w) {
-        hotrg_status s = build_B<R>(ctx, p, src[w], Ua, Ub, x20, xs2, O1B, opnd(Bbuf, w * Bsz),
-                                    opnd(Blob, w * Bsz), st);
-        if (s != HOTRG_OK) return s;
+      for (int ph : {kPass1, kPassMax, kPass2}) {
+        if (ph == kPassMax && scale != kScaleExact) continue;
+        if (amaxB && clear_phase(ph)) CK(cudaMemsetAsync(amaxB, 0, ne * sizeof(unsigned), st), "amax clear");
+        for (int w = 0; w < nbuild; ++w) {
+          hotrg_status s = build_B<R>(ctx, p, src[w], Ua, Ub, x20, xs2, O1B + w * O1Bsz, opnd(Bbuf, w * Bsz * planes),
+                                      opnd(Blob, w * Bsz * planes), st, esB, amaxB, scale, ph);
+          if (s != HOTRG_OK) return s;
+        }
       }
       return HOTRG_OK;
     };
@@ -898,10 +1007,15 @@ hotrg_status contract_element(hotrg_ctx* ctx, const StepPlan& p, int bidx, cudaS
       const int xs = std::min(p.xs, ca - x0);
       const int64_t rA_full = (int64_t)xs * p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[mu];
       const int64_t rA = pr.gemm_rows > 0 ? std::min(rA_full, pr.gemm_rows) : rA_full;
-      for (int w = 0; w < nt && pr.ttm; ++w) {
-        hotrg_status s = build_A<R>(ctx, p, src[w], Ua, Ub, x0, xs, O1A, opnd(Abuf, w * Asz),
-                                    opnd(Alob, w * Asz), st);
-        if (s != HOTRG_OK) return s;
+      for (int ph : {kPass1, kPassMax, kPass2}) {
+        if (!pr.ttm) break;
+        if (ph == kPassMax && scale != kScaleExact) continue;
+        if (amaxA && clear_phase(ph)) CK(cudaMemsetAsync(amaxA, 0, ne * sizeof(unsigned), st), "amax clear");
+        for (int w = 0; w < nbuild; ++w) {
+          hotrg_status s = build_A<R>(ctx, p, src[w], Ua, Ub, x0, xs, O1A + w * O1Asz, opnd(Abuf, w * Asz * planes),
+                                      opnd(Alob, w * Asz * planes), st, esA, amaxA, scale, ph);
+          if (s != HOTRG_OK) return s;
+        }
       }
       for (int x20 = 0; x20 < x2end; x20 += p.xs2) {
         const int xs2 = std::min(p.xs2, ca - x20);
@@ -910,33 +1024,67 @@ hotrg_status contract_element(hotrg_ctx* ctx, const StepPlan& p, int bidx, cudaS
           hotrg_status s = buildB(x20, xs2);
           if (s != HOTRG_OK) return s;
         }
-        hotrg_status s;
+        hotrg_status s = HOTRG_OK;
         if (!pr.gemm) {
           // tensor-pass probe: no product
         } else if (split) {
           // every output of the block in one launch: C_T = A_T B_T^T, C_S = (A_S B_T^T + A_T B_S^T) / 2,
           // and M_1 = A_S B_S^T (the nearest-neighbour pair inside the first block) or
-          // C_M = (A_M B_T^T + A_T B_M^T) / 2; fp16 operands carry the factor 2^14 each
-          const double un = ctx->prec == HOTRG_FP16X3 ? 1.0 / ((double)kF16Scale * kF16Scale) : 1.0;
+          // C_M = (A_M B_T^T + A_T B_M^T) / 2; operand tensor (e, w) of the group is tensor
+          // e nt + w of the launch
+          // fp16 operands carry 2^(eA + eB), which the epilogue removes (amax_a, amax_b), or,
+          // without max-norm scaling, the fixed 2^14 each
+          const double un = (ctx->prec == HOTRG_FP16X3 && !amaxA) ? 1.0 / ((double)kF16Scale * kF16Scale) : 1.0;
           GemmGroup g{};
-          g.nprob = nt;
-          g.p[0] = GemmProblem{(float*)Cbuf, (float)un, 1, {0, 0}, {0, 0}};
-          if (nt >= 2) g.p[1] = GemmProblem{(float*)(Cbuf + Csz), (float)(0.5 * un), 2, {1, 0}, {0, 1}};
-          if (nt >= 3)
-            g.p[2] = kstep == 0 ? GemmProblem{(float*)(Cbuf + 2 * Csz), (float)un, 1, {1, 0}, {1, 0}}
-                                : GemmProblem{(float*)(Cbuf + 2 * Csz), (float)(0.5 * un), 2, {2, 0}, {0, 2}};
-          s = gemm_tc(ctx, Abuf, Alob, Bbuf, Blob, nt, Asz, Bsz, p, g, rA, rB, st);
+          g.amax_a = amaxA;
+          g.amax_b = amaxB;
+          g.per_elem = nt;
+          g.nprob = nt * ne;
+          for (int e = 0; e < ne; ++e) {
+            const int w0 = e * nt;
+            R* Ce = Cbuf + (int64_t)w0 * Csz;
+            g.p[w0] = GemmProblem{(float*)Ce, (float)un, 1, {w0, 0}, {w0, 0}};
+            if (nt >= 2) g.p[w0 + 1] = GemmProblem{(float*)(Ce + Csz), (float)(0.5 * un), 2, {w0 + 1, w0}, {w0, w0 + 1}};
+            if (nt >= 3)
+              g.p[w0 + 2] = kstep == 0
+                                ? GemmProblem{(float*)(Ce + 2 * Csz), (float)un, 1, {w0 + 1, 0}, {w0 + 1, 0}}
+                                : GemmProblem{(float*)(Ce + 2 * Csz), (float)(0.5 * un), 2, {w0 + 2, w0}, {w0, w0 + 2}};
+          }
+          s = gemm_tc(ctx, Abuf, Alob, Bbuf, Blob, nt * ne, Asz, Bsz, p, g, rA, rB, st);
           if (s != HOTRG_OK) return s;
-        } else if (oz) {   // pure tensor only: C_T = A_T B_T^T in FP64 accuracy
-          GemmTimer tm{ctx, st};
-          if ((s = tm.start()) != HOTRG_OK) return s;
-          CK(launch_gemm_oz(Abuf, Bbuf, Asz, Bsz, p.Kp, p.kps, p.P, rA, rB, (double*)Cbuf, rB, 1.0,
-                            (int*)(ctx->ws + ctx->L.status), st),
-             "gemm oz");
-          if ((s = tm.stop(2.0 * (double)rA * (double)rB * (double)p.K)) != HOTRG_OK) return s;
-        } else {
-          auto Ap = [&](int w) { return opnd(Abuf, w * Asz); };
-          auto Bp = [&](int w) { return opnd(Bbuf, w * Bsz); };
+        } else if (oz) {   // FP64 accuracy, element by element, one product per launch
+          for (int e = 0; e < ne && s == HOTRG_OK; ++e) {
+            // operand tensor w of element e: its kOzSlices planes, Asz (Bsz) values each
+            auto prod = [&](int wa, int wb, int out, double alpha, bool acc) -> hotrg_status {
+              GemmTimer tm{ctx, st};
+              hotrg_status r = tm.start();
+              if (r != HOTRG_OK) return r;
+              CK(launch_gemm_oz(Abuf + (e * esA.op + wa * Asz * planes) * (int64_t)osz,
+                                Bbuf + (e * esB.op + wb * Bsz * planes) * (int64_t)osz, Asz, Bsz, p.Kp, p.kps, p.P,
+                                rA, rB, (double*)(Cbuf + e * esC.C + out * Csz), rB, alpha, amaxA + e, amaxB + e,
+                                acc, (int*)(ctx->ws + ctx->L.status), st),
+                 "gemm oz");
+              return tm.stop(2.0 * (double)rA * (double)rB * (double)p.K);
+            };
+            s = prod(0, 0, 0, 1.0, false);                                    // C_T
+            if (s == HOTRG_OK && nt >= 2) {                                    // C_S
+              s = prod(1, 0, 1, 0.5, false);
+              if (s == HOTRG_OK) s = prod(0, 1, 1, 0.5, true);
+            }
+            if (s == HOTRG_OK && nt >= 3) {
+              if (kstep == 0) {
+                s = prod(1, 1, 2, 1.0, false);                                 // M_1 = A(S) B(S)^T
+              } else {                                                         // C_M
+                s = prod(2, 0, 2, 0.5, false);
+                if (s == HOTRG_OK) s = prod(0, 2, 2, 0.5, true);
+              }
+            }
+          }
+          if (s != HOTRG_OK) return s;
+        } else for (int e = 0; e < ne; ++e) {
+          R* Cbuf = (R*)(sb + sc.C) + e * esC.C;     // this element's outputs
+          auto Ap = [&](int w) { return opnd(Abuf, e * esA.op + w * Asz); };
+          auto Bp = [&](int w) { return opnd(Bbuf, e * esB.op + w * Bsz); };
           // C_T = A(T) B(T)^T
           s = gemm_simt<R>(ctx, Ap(0), Bp(0), p, Cbuf, rA, rB, 1.0, 0.0, st);
           if (s != HOTRG_OK) return s;
@@ -959,7 +1107,7 @@ hotrg_status contract_element(hotrg_ctx* ctx, const StepPlan& p, int bidx, cudaS
           }
         }
         for (int w = 0; w < nt && pr.ttm; ++w) {
-          s = close_C<R>(ctx, p, Cbuf + w * Csz, Uc, x0, xs, x20, xs2, O3, dst[w], st);
+          s = close_C<R>(ctx, p, Cbuf + w * Csz, Uc, x0, xs, x20, xs2, O3, dst[w], st, esC);
           if (s != HOTRG_OK) return s;
         }
       }
@@ -978,18 +1126,20 @@ hotrg_status do_step(hotrg_ctx* ctx, const StepPlan& p) {
   const int* dstep = (const int*)(ctx->ws + ctx->L.step);
   hotrg_status s = isometry_stage<R>(ctx, p, sc, sb, st);
   if (s != HOTRG_OK) return s;
-  for (int bidx = 0; bidx < ctx->batch; ++bidx) {
-    s = contract_element<R>(ctx, p, bidx, st);
+  for (int e0 = 0; e0 < ctx->batch; e0 += p.ne) {
+    s = contract_group<R>(ctx, p, e0, std::min(p.ne, ctx->batch - e0), st);
     if (s != HOTRG_OK) return s;
-    // ---------------------------------------------------------------- 4. normalise
-    DevRecord* rec_b = (DevRecord*)(ctx->ws + ctx->L.rec) + (int64_t)bidx * kMaxSteps;
-    R* dst[3];
-    for (int w = 0; w < nt; ++w) dst[w] = tensor_ptr<R>(ctx, w, 1 - ctx->cur, bidx);
-    double* lnz = (double*)(ctx->ws + ctx->L.lnz) + bidx;
-    double* cval = (double*)(ctx->ws + ctx->L.cval) + bidx;
-    LK(2, launch_norm<R>(dst[0], p.Enew, (double*)(sb + sc.npart), dstep, cval, lnz, rec_b, status, st), "norm");
-    for (int w = 0; w < nt; ++w) LK(1, launch_scale<R>(dst[w], p.Enew, cval, st), "scale");
   }
+  // ---------------------------------------------------------------- 4. normalise (every element)
+  DevRecord* rec = (DevRecord*)(ctx->ws + ctx->L.rec);
+  double* lnz = (double*)(ctx->ws + ctx->L.lnz);
+  double* cval = (double*)(ctx->ws + ctx->L.cval);
+  const int64_t cap = ctx->L.cap;
+  LK(2, launch_norm<R>(tensor_ptr<R>(ctx, 0, 1 - ctx->cur, 0), p.Enew, ctx->batch, cap, (double*)(sb + sc.npart), dstep,
+                       cval, lnz, rec, status, st),
+     "norm");
+  for (int w = 0; w < nt; ++w)
+    LK(1, launch_scale<R>(tensor_ptr<R>(ctx, w, 1 - ctx->cur, 0), p.Enew, ctx->batch, cap, cval, st), "scale");
   LK(1, launch_step_end((int*)(ctx->ws + ctx->L.step), st), "step end");
   return HOTRG_OK;
 }
@@ -1012,16 +1162,24 @@ hotrg_status sync_and_status(hotrg_ctx* ctx) {
   return ctx->sticky ? (hotrg_status)ctx->sticky : HOTRG_OK;
 }
 
-// Slice sizes (X for A and C rows, X' for B rows and C columns): the pair that fits the
-// workspace with the fewest GEMM blocks, then the largest X' slice. False if none fits.
+// Group size and slice sizes (X for A and C rows, X' for B rows and C columns). Per element
+// (one temperature at a time): the slice pair that fits the workspace with the fewest GEMM
+// blocks, then the largest X' slice. Grouped (ne >= 2 temperatures contracted together, each
+// launch of the contraction covering the whole group): B unsliced and the largest X slice
+// that fits. The plan with fewer groups x blocks (launches of the contraction) wins, ties to
+// the larger group; a group holds at most kMaxGemmProblems / tensors temperatures (the
+// outputs of one grouped GEMM launch). False if nothing fits.
 bool choose_slices(const hotrg_ctx* ctx, StepPlan& p) {
   const size_t avail = ctx->ws_bytes - ctx->L.persistent_end;
   const int ca = p.chi[p.a];
+  const int nt = ntensors(ctx->impure_active);
+  StepPlan q = p;
+  q.ne = 1;
   int best_xs = 0, best_xs2 = 0;
   int64_t best_blocks = -1;
   for (int xs = ca; xs >= 1; --xs) {
     for (int xs2 = ca; xs2 >= 1; --xs2) {
-      if (scratch_layout(p, xs, xs2, ctx->prec, ctx->impure_active, ctx->rsize).total > avail) continue;
+      if (scratch_layout(q, xs, xs2, ctx->prec, ctx->impure_active, ctx->rsize).total > avail) continue;
       const int64_t blocks = (int64_t)((ca + xs - 1) / xs) * ((ca + xs2 - 1) / xs2);
       if (best_blocks < 0 || blocks < best_blocks || (blocks == best_blocks && xs2 > best_xs2)) {
         best_blocks = blocks;
@@ -1031,7 +1189,26 @@ bool choose_slices(const hotrg_ctx* ctx, StepPlan& p) {
       break;  // smaller xs2 only adds blocks for this xs
     }
   }
-  if (best_blocks < 0) return false;
+  int best_ne = 1;
+  int64_t best_cost = best_blocks < 0 ? -1 : (int64_t)ctx->batch * best_blocks;
+  int ne_max = std::min(ctx->batch, kMaxGemmProblems / nt);
+  if (ctx->group_max > 0) ne_max = std::min(ne_max, ctx->group_max);
+  for (int ne = 2; ne <= ne_max; ++ne) {
+    q.ne = ne;
+    for (int xs = ca; xs >= 1; --xs) {
+      if (scratch_layout(q, xs, ca, ctx->prec, ctx->impure_active, ctx->rsize).total > avail) continue;
+      const int64_t cost = (int64_t)((ctx->batch + ne - 1) / ne) * ((ca + xs - 1) / xs);
+      if (best_cost < 0 || cost <= best_cost) {
+        best_cost = cost;
+        best_ne = ne;
+        best_xs = xs;
+        best_xs2 = ca;
+      }
+      break;
+    }
+  }
+  if (best_cost < 0) return false;
+  p.ne = best_ne;
   p.xs = best_xs;
   p.xs2 = best_xs2;
   return true;
@@ -1099,7 +1276,7 @@ hotrg_status tune_step(hotrg_ctx* ctx, int dir, int dcut, TuneChoice* best_out) 
   auto timed = [&](const StepPlan& pl, const Probe& pr, float* ms) -> hotrg_status {
     cudaError_t e = cudaEventRecord(e0, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tune timing");
-    hotrg_status r = contract_element<R>(ctx, pl, 0, st, pr);
+    hotrg_status r = contract_group<R>(ctx, pl, 0, 1, st, pr);
     if (r != HOTRG_OK) return r;
     e = cudaEventRecord(e1, st);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -1208,11 +1385,6 @@ hotrg_status hotrg_create(hotrg_ctx** out, int batch, int dcut_max, int prec, in
   if (prec != HOTRG_FP64 && prec != HOTRG_FP32 && prec != HOTRG_TF32X3 && prec != HOTRG_FP16X3 &&
       prec != HOTRG_FP64OZ)
     return HOTRG_EINVAL;
-  if (prec == HOTRG_FP64OZ && impure_mask != 0) {
-    // the integer slices assume |x| <= 1, which the normalised pure tensor's operands meet
-    set_last_error("HOTRG_FP64OZ propagates the pure tensor only (impure tensors: HOTRG_FP64)");
-    return HOTRG_EINVAL;
-  }
   if (impure_mask < 0 || impure_mask > 3 || impure_mask == HOTRG_IMPURE_SIGMASIGMA) return HOTRG_EINVAL;
   hotrg_ctx* c = new hotrg_ctx();
   c->batch = batch;
@@ -1241,15 +1413,21 @@ hotrg_status hotrg_workspace_size(hotrg_ctx* ctx, int nsteps, const int* dirs, c
     }
   size_t scratch = 0;
   int64_t cap = tensor_elems(D);
+  // room for the largest useful group of temperatures contracted together (unsliced); a
+  // smaller workspace makes the planner take smaller groups or slices
+  int ne_full = std::min(ctx->batch, kMaxGemmProblems / ntensors(ctx->impure));
+  if (ctx->group_max > 0) ne_full = std::min(ne_full, ctx->group_max);
   if (nsteps == 0) {
     int Dm[4] = {ctx->dcut_max, ctx->dcut_max, ctx->dcut_max, ctx->dcut_max};
     StepPlan p = make_plan(Dm, 0, ctx->dcut_max, ctx->prec, ctx->batch);
+    p.ne = ne_full;
     scratch = scratch_layout(p, p.xs, p.xs2, ctx->prec, ctx->impure, ctx->rsize).total;
     cap = std::max(cap, tensor_elems(Dm));
   } else {
     for (int i = 0; i < nsteps; ++i) {
       if (dirs[i] < 0 || dirs[i] > 3 || dcuts[i] < 1 || dcuts[i] > ctx->dcut_max) return HOTRG_EINVAL;
       StepPlan p = make_plan(D, dirs[i], dcuts[i], ctx->prec, ctx->batch);
+      p.ne = ne_full;
       scratch = std::max(scratch, scratch_layout(p, p.xs, p.xs2, ctx->prec, ctx->impure, ctx->rsize).total);
       for (int n = 0; n < 4; ++n) {
         D[n] = p.newD[n];
@@ -1324,6 +1502,7 @@ hotrg_status hotrg_init_tensor(hotrg_ctx* ctx, const double* beta, const double*
   ctx->sticky = 0;
   ctx->initialised = true;
   ctx->last_mu = -1;
+  ctx->last_kstep = -1;
   return HOTRG_OK;
 }
 
@@ -1368,6 +1547,7 @@ hotrg_status hotrg_set_tensor(hotrg_ctx* ctx, int b, const int dims[4], const do
   ctx->sticky = 0;
   ctx->initialised = true;
   ctx->last_mu = -1;
+  ctx->last_kstep = -1;
   ctx->h_host.assign(ctx->batch, 0.0);
   return HOTRG_OK;
 }
@@ -1411,9 +1591,9 @@ hotrg_status hotrg_step(hotrg_ctx* ctx, int dir, int dcut) {
     // which buffer holds the tensors, whether it is the first step (M_1 = C(S,S)) and the
     // impure tensors in use. ln c / 2^k and the record slot come from the device counter.
     char key[256];
-    snprintf(key, sizeof(key), "%d %d %d %d %d %d %d %d %d %d %d %d %d %d", dir, dcut, ctx->dims[0], ctx->dims[1],
-             ctx->dims[2], ctx->dims[3], ctx->cur, ctx->k == 0, ctx->impure_active, p.xs, p.xs2, ctx->batch, p.c,
-             p.gemm_opt);
+    snprintf(key, sizeof(key), "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d", dir, dcut, ctx->dims[0],
+             ctx->dims[1], ctx->dims[2], ctx->dims[3], ctx->cur, ctx->k == 0, ctx->impure_active, p.xs, p.xs2,
+             ctx->batch, p.c, p.gemm_opt, p.ne);
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
       const uint64_t l0 = ctx->launches;
@@ -1436,10 +1616,13 @@ hotrg_status hotrg_step(hotrg_ctx* ctx, int dir, int dcut) {
     CK(cudaGraphLaunch(it->second.exec, ctx->stream), "graph launch");
     ctx->launches += it->second.launches;
   }
+  ctx->last_plan = p;
+  ctx->last_kstep = ctx->k;
   ctx->mu_hist[ctx->k] = dir;
   ctx->c_hist[ctx->k] = p.c;
   ctx->opt_hist[ctx->k] = tc_mode(ctx->prec) ? (p.gemm_opt >= 0 ? p.gemm_opt : ctx->gemm_variant) : -1;
   ctx->tuned_hist[ctx->k] = p.tuned ? 1 : 0;
+  ctx->group_hist[ctx->k] = p.ne;
   ctx->slices_hist[ctx->k][0] = (p.chi[p.a] + p.xs - 1) / p.xs;
   ctx->slices_hist[ctx->k][1] = (p.chi[p.a] + p.xs2 - 1) / p.xs2;
   for (int n = 0; n < 4; ++n) {
@@ -1566,6 +1749,7 @@ hotrg_status hotrg_step_info(hotrg_ctx* ctx, int b, int step, hotrg_step_record*
   rec->closing = ctx->c_hist[step - 1];
   rec->gemm_option = ctx->opt_hist[step - 1];
   rec->tuned = ctx->tuned_hist[step - 1];
+  rec->group = ctx->group_hist[step - 1];
   return HOTRG_OK;
 }
 
@@ -1633,9 +1817,66 @@ hotrg_status hotrg_set_option(hotrg_ctx* ctx, int option, int value) {
       if (value < 0 || value > 1) return HOTRG_EINVAL;
       ctx->autotune = value != 0;
       return HOTRG_OK;
+    case HOTRG_OPT_GROUP:
+      if (value < 0 || value > kMaxGemmProblems) return HOTRG_EINVAL;
+      ctx->group_max = value;
+      return HOTRG_OK;
+    case HOTRG_OPT_MAXNORM:
+      if (value < kScaleNone || value > kScaleExact) return HOTRG_EINVAL;
+      ctx->maxnorm = value;
+      ctx->drop_graphs();
+      return HOTRG_OK;
     default:
       return HOTRG_EINVAL;
   }
+}
+
+hotrg_status hotrg_split_stats(hotrg_ctx* ctx, hotrg_split_counts* out) {
+  hotrg_status r = check_ready(ctx);
+  if (r != HOTRG_OK) return r;
+  if (!out) return HOTRG_EINVAL;
+  if (ctx->prec != HOTRG_FP16X3) return HOTRG_EUNSUPPORTED;
+  if (!ctx->initialised || ctx->last_kstep < 0) return HOTRG_ESTATE;
+  const StepPlan& p = ctx->last_plan;
+  const int nt = ntensors(ctx->impure_active);
+  const int nbuild = (ctx->last_kstep == 0 && nt >= 3) ? 2 : nt;
+  const Scratch sc = scratch_layout(p, p.xs, p.xs2, ctx->prec, ctx->impure_active, ctx->rsize);
+  char* sb = ctx->ws + ctx->L.persistent_end;
+  // the last group, the last slice block of A and (sliced) of B
+  const int ca = p.chi[p.a];
+  const int ne = ctx->batch - (ctx->batch - 1) / p.ne * p.ne;
+  const int xs = ca - (ca - 1) / p.xs * p.xs, xs2 = ca - (ca - 1) / p.xs2 * p.xs2;
+  const int64_t per_x = (int64_t)p.chi[p.b] * p.D[p.c] * p.D[p.c] * p.D[p.mu];
+  const int64_t rowsA = (int64_t)p.xs * per_x, rowsB = (int64_t)p.xs2 * per_x;
+  const int64_t Asz = p.P * rowsA * p.kps, Bsz = p.P * rowsB * p.kps;   // fp16 values per operand tensor
+  unsigned long long* cnt = (unsigned long long*)(sb + sc.stats);   // [A hi, A lo, B hi, B lo][3]
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemsetAsync(cnt, 0, 12 * sizeof(unsigned long long), st), "stats clear");
+  for (int e = 0; e < ne; ++e)
+    for (int w = 0; w < nbuild; ++w) {
+      const int64_t ta = (int64_t)(e * nt + w) * Asz * 2, tb = (int64_t)(e * nt + w) * Bsz * 2;   // bytes
+      CK(launch_plane_stats(sb + sc.A + ta, p.P * xs * per_x, p.Kp, p.kps, cnt + 0, st), "stats");
+      CK(launch_plane_stats(sb + sc.Alo + ta, p.P * xs * per_x, p.Kp, p.kps, cnt + 3, st), "stats");
+      CK(launch_plane_stats(sb + sc.B + tb, p.P * xs2 * per_x, p.Kp, p.kps, cnt + 6, st), "stats");
+      CK(launch_plane_stats(sb + sc.Blo + tb, p.P * xs2 * per_x, p.Kp, p.kps, cnt + 9, st), "stats");
+    }
+  unsigned long long h[12];
+  CK(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st), "stats read");
+  CK(cudaStreamSynchronize(st), "stats sync");
+  const uint64_t nA = (uint64_t)ne * nbuild * p.P * xs * per_x * p.Kp;
+  const uint64_t nB = (uint64_t)ne * nbuild * p.P * xs2 * per_x * p.Kp;
+  auto half_value = [](unsigned long long bits) {   // magnitude bits of a finite fp16
+    const int ex = (int)(bits >> 10) & 31, m = (int)(bits & 1023);
+    return ex == 0 ? ldexp((double)m, -24) : ldexp(1.0 + m / 1024.0, ex - 15);
+  };
+  out->entries = nA + nB;
+  out->hi_zero = h[0] + h[6];
+  out->hi_subnormal = h[1] + h[7];
+  out->lo_zero = h[3] + h[9];
+  out->lo_subnormal = h[4] + h[10];
+  out->hi_max[0] = half_value(h[2]);
+  out->hi_max[1] = half_value(h[8]);
+  return HOTRG_OK;
 }
 
 hotrg_status hotrg_autotune(hotrg_ctx* ctx, int dir, int dcut) {

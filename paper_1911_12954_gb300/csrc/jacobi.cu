@@ -264,11 +264,13 @@ __global__ void __launch_bounds__(kJT) jacobi_kernel(const __grid_constant__ Eig
   for (int i = tid; i < n; i += kJT) nrm[i] = A[i * n + i];
   __syncthreads();
   for (int i = tid; i < n; i += kJT) {
-    const double li = nrm[i];
+    // ranked by (value, index) with a NaN taken as -inf: a strict total order, so perm is a
+    // permutation whatever the input (a non-finite tensor is reported by the normalisation)
+    const double li = nrm[i], ki = li == li ? li : -INFINITY;
     int rank = 0;
     for (int j = 0; j < n; ++j) {
-      const double lj = nrm[j];
-      rank += (lj > li) || (lj == li && j < i);
+      const double lj = nrm[j], kj = lj == lj ? lj : -INFINITY;
+      rank += (kj > ki) || (kj == ki && j < i);
     }
     perm[rank] = i;
     lam[rank] = li;

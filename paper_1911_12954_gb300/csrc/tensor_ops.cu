@@ -14,6 +14,7 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
@@ -39,11 +40,46 @@ __device__ __forceinline__ void oz_store(__half* out, int64_t plane, int64_t o, 
   }
 }
 
+// Power-of-two scale of a split pass: from the operand's largest magnitude (a max pass of the
+// same contraction wrote it to amax) or, without one, the fixed 2^14 of the fp16 planes.
+template <int MODE>
+__device__ __forceinline__ double split_scale(const unsigned* amax) {
+  if (MODE == kTTMSplitF16) return amax ? ldexp(1.0, split_exponent(*amax, kF16Top)) : (double)kF16Scale;
+  if (MODE == kTTMSplitOz) return amax ? ldexp(1.0, split_exponent(*amax, kOzTop)) : 1.0;
+  return 1.0;
+}
+
+// Largest magnitude seen by the threads of a block, times mul, merged into *amax (bits of a
+// non-negative float, rounded up, so that the recorded value bounds mul times every output).
+__device__ __forceinline__ void merge_max(unsigned* amax, double m, float mul) {
+  float f = __double2float_ru(m * (double)mul);
+  for (int off = 16; off > 0; off >>= 1) f = fmaxf(f, __shfl_down_sync(0xffffffffu, f, off));
+  if ((threadIdx.x & 31) == 0 && f > 0.f && amax) atomicMax(amax, __float_as_uint(f));
+}
+
+// Output pointer of batch element e: the split modes write fp16 planes, whose strides count
+// fp16 values; the others count elements of the output type.
+template <typename TO, int MODE>
+__device__ __forceinline__ TO* elem_out(TO* p, int64_t off) {
+  if (!p) return p;
+  if (MODE == kTTMSplitF16 || MODE == kTTMSplitOz) return (TO*)((__half*)p + off);
+  return p + off;
+}
+
 template <typename TI, typename TU, typename TO, int MODE>
 __global__ void __launch_bounds__(256) ttm_kernel(const TI* __restrict__ in, const TU* __restrict__ U,
                                                   TO* __restrict__ out, TO* __restrict__ out_lo,
                                                   TTMArgs a) {
   using Acc = typename std::conditional<sizeof(TI) == 8, double, float>::type;
+  const int64_t eb = blockIdx.y;               // batch element
+  unsigned* amax = a.amax ? a.amax + eb : nullptr;
+  const Acc sscale = (Acc)split_scale<MODE>(amax);
+  Acc tmax = 0;                                // largest |output| of this thread (max modes), in the
+                                               // accumulator type: no FP64 work for FP32 data
+  in += eb * a.in_bs;
+  if (U) U += eb * a.u_bs;
+  out = elem_out<TO, MODE>(out, eb * a.out_bs);
+  out_lo = elem_out<TO, MODE>(out_lo, eb * a.out_bs);
   const int outer_dims = a.rank - a.rin;
   for (int64_t row = blockIdx.x; row < a.outer; row += gridDim.x) {
     int64_t r = row, in0 = 0, u0 = 0, o0 = 0;
@@ -78,18 +114,20 @@ __global__ void __launch_bounds__(256) ttm_kernel(const TI* __restrict__ in, con
         }
       }
       acc *= (Acc)a.alpha;
-      if (MODE == kTTMSplitTF32) {
+      if (MODE == kTTMMaxAbs || MODE == kTTMStoreMax) tmax = fmax(tmax, fabs(acc));
+      if (MODE == kTTMMaxAbs) {
+      } else if (MODE == kTTMSplitTF32) {
         const float v = (float)acc;
         const float hi = tf32_round(v);
         out[o1] = (TO)hi;
         out_lo[o1] = (TO)tf32_round(v - hi);
       } else if (MODE == kTTMSplitF16) {
-        const float v = (float)acc * kF16Scale;
+        const float v = (float)(acc * sscale);
         const __half hi = __float2half_rn(v);
         ((__half*)out)[o1] = hi;
         ((__half*)out_lo)[o1] = __float2half_rn(v - __half2float(hi));
       } else if (MODE == kTTMSplitOz) {
-        oz_store((__half*)out, (__half*)out_lo - (__half*)out, o1, (double)acc);
+        oz_store((__half*)out, (__half*)out_lo - (__half*)out, o1, (double)acc * (double)sscale);
       } else if (MODE == kTTMAccumulate) {
         out[o1] = (TO)(acc + (Acc)a.beta * (Acc)out[o1]);
       } else {
@@ -97,6 +135,7 @@ __global__ void __launch_bounds__(256) ttm_kernel(const TI* __restrict__ in, con
       }
     }
   }
+  if (MODE == kTTMMaxAbs || MODE == kTTMStoreMax) merge_max(amax, (double)tmax, a.amax_mul);   // every thread gets here
 }
 
 // ---------------------------------------------------------------------------- fiber form
@@ -116,6 +155,10 @@ struct FiberArgs {
   int J1, J2;                   // contracted dims
   int64_t ji1, ji2, ju1, ju2;   // their input and U-row strides
   double alpha;
+  int nb;                       // batch elements (blockIdx.y), strides as in TTMArgs
+  int64_t in_bs, u_bs, out_bs;
+  unsigned* amax;               // as in TTMArgs
+  float amax_mul;
 };
 
 constexpr int kShortJ = 16;     // longest contraction of the short form
@@ -137,7 +180,7 @@ __device__ __forceinline__ void fiber_offsets(const FiberArgs& a, uint32_t f, in
   }
 }
 
-// acc already carries the 2^14 factor in kTTMSplitF16 mode (folded into U by the caller)
+// acc already carries the split pass's power-of-two scale (folded into U by the caller)
 template <typename R, int MODE>
 __device__ __forceinline__ void fiber_store(R* out, R* out_lo, int64_t o, R acc) {
   if (MODE == kTTMSplitTF32) {
@@ -146,7 +189,7 @@ __device__ __forceinline__ void fiber_store(R* out, R* out_lo, int64_t o, R acc)
     out[o] = (R)hi;
     out_lo[o] = (R)tf32_round(v - hi);
   } else if (MODE == kTTMSplitF16) {
-    // fp16 hi + lo of 2^14 x: the pair keeps 22 significant bits
+    // fp16 hi + lo of 2^e x: the pair keeps 22 significant bits
     const float v = (float)acc;
     const __half hi = __float2half_rn(v);
     ((__half*)out)[o] = hi;
@@ -164,14 +207,20 @@ __device__ __forceinline__ void fiber_store(R* out, R* out_lo, int64_t o, R acc)
 template <typename R, int MODE>
 __global__ void __launch_bounds__(256) ttm_short_kernel(const R* __restrict__ in, const R* __restrict__ U,
                                                         R* __restrict__ out, R* __restrict__ out_lo, FiberArgs a) {
+  in += blockIdx.y * a.in_bs;                  // batch element blockIdx.y
+  U += blockIdx.y * a.u_bs;
+  out = elem_out<R, MODE>(out, blockIdx.y * a.out_bs);
+  out_lo = elem_out<R, MODE>(out_lo, blockIdx.y * a.out_bs);
   extern __shared__ __align__(16) unsigned char fsm[];
   const int J = a.J1 * a.J2, Rn = a.R1 * a.R2;
   const int Rp = (Rn + kShortRB - 1) / kShortRB * kShortRB;
   R* Us = (R*)fsm;                                       // [J][Rp], zero past Rn
   int64_t* roff = (int64_t*)(fsm + (size_t)J * Rp * sizeof(R));   // [Rp] output offset of r
   int64_t* joff = roff + Rp;                             // [J] input offset of j
-  // the fp16 split's 2^14 (exact, a power of two) is folded into U
-  const R uscale = MODE == kTTMSplitF16 ? (R)kF16Scale : (R)1;
+  // the split's power-of-two scale (exact) is folded into U
+  unsigned* amax = a.amax ? a.amax + blockIdx.y : nullptr;
+  const R uscale = (R)split_scale<MODE>(amax);
+  R tmax = 0;                                            // max modes: largest |output| (type R)
   for (int e = threadIdx.x; e < J * Rp; e += blockDim.x) {
     const int j = e / Rp, r = e % Rp;
     R v = 0;
@@ -221,23 +270,36 @@ __global__ void __launch_bounds__(256) ttm_short_kernel(const R* __restrict__ in
       }
 #pragma unroll
       for (int i = 0; i < kShortRB; ++i)
-        if (rb + i < Rn) fiber_store<R, MODE>(out, out_lo, oo + roff[rb + i], scaled ? acc[i] * alpha : acc[i]);
+        if (rb + i < Rn) {
+          const R v = scaled ? acc[i] * alpha : acc[i];
+          if (MODE == kTTMMaxAbs || MODE == kTTMStoreMax) tmax = fmax(tmax, fabs(v));
+          if (MODE != kTTMMaxAbs) fiber_store<R, MODE>(out, out_lo, oo + roff[rb + i], v);
+        }
     }
   }
+  if (MODE == kTTMMaxAbs || MODE == kTTMStoreMax) merge_max(amax, (double)tmax, a.amax_mul);   // every thread gets here
 }
 
 // The fp16 split of a short contraction, two fibres per thread: when the innermost fibre leg
 // has output stride 1 and an even extent (and every other output stride is even), fibres
 // 2f and 2f + 1 are neighbours in the output, so their hi (and lo) values go out as one
 // 4-byte half2: a warp store fills a 128-byte line and each U row read serves two fibres.
-template <typename R>
+// MAXONLY: the max pass of the same contraction (kTTMMaxAbs: nothing written, the largest
+// |output| times a.amax_mul merged into a.amax[element]).
+template <typename R, bool MAXONLY>
 __global__ void __launch_bounds__(256) ttm_pair_f16_kernel(const R* __restrict__ in, const R* __restrict__ U,
                                                            R* __restrict__ out, R* __restrict__ out_lo, FiberArgs a) {
   constexpr int RB = 16;
+  unsigned* amax = a.amax ? a.amax + blockIdx.y : nullptr;
+  float tmax = 0.f;                            // MAXONLY: largest |output| of this thread
+  in += blockIdx.y * a.in_bs;                  // batch element blockIdx.y
+  U += blockIdx.y * a.u_bs;
+  out = elem_out<R, kTTMSplitF16>(out, blockIdx.y * a.out_bs);
+  out_lo = elem_out<R, kTTMSplitF16>(out_lo, blockIdx.y * a.out_bs);
   extern __shared__ __align__(16) unsigned char fsm[];
   const int J = a.J1 * a.J2, Rn = a.R1 * a.R2;
   const int Rp = (Rn + kShortRB - 1) / kShortRB * kShortRB;
-  R* Us = (R*)fsm;                                       // [J][Rp], zero past Rn, times 2^14
+  R* Us = (R*)fsm;                                       // [J][Rp], zero past Rn, times the split scale
   int64_t* roff = (int64_t*)(fsm + (size_t)J * Rp * sizeof(R));
   int64_t* joff = roff + Rp;
   for (int e = threadIdx.x; e < J * Rp; e += blockDim.x) {
@@ -245,7 +307,7 @@ __global__ void __launch_bounds__(256) ttm_pair_f16_kernel(const R* __restrict__
     R v = 0;
     if (r < Rn) {
       const int j1 = j / a.J2, j2 = j % a.J2, r1 = r / a.R2, r2 = r % a.R2;
-      v = U[j1 * a.ju1 + j2 * a.ju2 + r1 * a.ru1 + r2 * a.ru2] * (R)kF16Scale;
+      v = U[j1 * a.ju1 + j2 * a.ju2 + r1 * a.ru1 + r2 * a.ru2] * (R)(MAXONLY ? 1.0 : split_scale<kTTMSplitF16>(amax));
     }
     Us[e] = v;
   }
@@ -289,7 +351,9 @@ __global__ void __launch_bounds__(256) ttm_pair_f16_kernel(const R* __restrict__
       }
 #pragma unroll
       for (int i = 0; i < RB; ++i) {
-        if (rb + i < Rn) {
+        if (MAXONLY) {
+          if (rb + i < Rn) tmax = fmaxf(tmax, fmaxf(fabsf(a0[i]), fabsf(a1[i])));
+        } else if (rb + i < Rn) {
           const int64_t o = oo + roff[rb + i];
           const __half h0 = __float2half_rn(a0[i]), h1 = __float2half_rn(a1[i]);
           const __half l0 = __float2half_rn(a0[i] - __half2float(h0));
@@ -300,6 +364,7 @@ __global__ void __launch_bounds__(256) ttm_pair_f16_kernel(const R* __restrict__
       }
     }
   }
+  if (MAXONLY) merge_max(amax, (double)tmax, a.amax_mul);   // every thread of the block gets here
 }
 
 // Long contractions (J > 16 with a short new index, Rn <= 16: the closing passes with U^c).
@@ -308,6 +373,9 @@ __global__ void __launch_bounds__(256) ttm_pair_f16_kernel(const R* __restrict__
 template <typename R, int RB>
 __global__ void __launch_bounds__(256) ttm_long_kernel(const R* __restrict__ in, const R* __restrict__ U,
                                                        R* __restrict__ out, FiberArgs a) {
+  in += blockIdx.y * a.in_bs;                  // batch element blockIdx.y
+  U += blockIdx.y * a.u_bs;
+  out += blockIdx.y * a.out_bs;
   extern __shared__ __align__(16) unsigned char fsm[];
   const int J = a.J1 * a.J2, Rn = a.R1 * a.R2;
   R* Us = (R*)fsm;                                       // [J][RB], zero past Rn
@@ -365,6 +433,9 @@ __global__ void __launch_bounds__(256) ttm_long_kernel(const R* __restrict__ in,
 template <int RB>
 __global__ void __launch_bounds__(256) ttm_long4_kernel(const float* __restrict__ in, const float* __restrict__ U,
                                                         float* __restrict__ out, FiberArgs a) {
+  in += blockIdx.y * a.in_bs;                  // batch element blockIdx.y
+  U += blockIdx.y * a.u_bs;
+  out += blockIdx.y * a.out_bs;
   extern __shared__ __align__(16) unsigned char fsm[];
   const int J = a.J1 * a.J2, Rn = a.R1 * a.R2;
   float* Us = (float*)fsm;                               // [J][RB], zero past Rn
@@ -436,6 +507,7 @@ inline bool quadable(const FiberArgs& f, const void* in, const void* out) {
   for (int d = 0; d < f.nf - 1; ++d)
     if ((f.fin[d] & 3) || (f.fout[d] & 3)) return false;
   if ((f.ji1 & 3) || (f.ji2 & 3) || (f.ro1 & 3) || (f.ro2 & 3)) return false;
+  if (f.nb > 1 && ((f.in_bs & 3) || (f.out_bs & 3))) return false;     // every element 16-byte aligned
   return ((((uintptr_t)in) | ((uintptr_t)out)) & 15) == 0;
 }
 
@@ -484,6 +556,12 @@ bool to_fiber(const TTMArgs& a, size_t rsize, FiberArgs& f) {
   f.ju1 = a.u_sj1;
   f.ju2 = a.u_sj2;
   f.alpha = a.alpha;
+  f.nb = a.nb;
+  f.in_bs = a.in_bs;
+  f.u_bs = a.u_bs;
+  f.out_bs = a.out_bs;
+  f.amax = a.amax;
+  f.amax_mul = a.amax_mul;
   const int J = a.J1 * a.J2, Rn = f.R1 * f.R2;
   if (f.nf == 0 || f.nfib > 0x7fffffffLL) return false;   // fibre index decoded in 32 bits
   if (J <= kShortJ) return Rn <= 256 && short_smem(J, Rn, rsize) <= kFiberSmemMax;
@@ -497,24 +575,28 @@ inline bool pairable(const FiberArgs& f, const void* out, const void* out_lo) {
   for (int d = 0; d < f.nf - 1; ++d)
     if (f.fout[d] & 1) return false;
   if ((f.ro1 & 1) || (f.ro2 & 1)) return false;
+  if (f.nb > 1 && (f.out_bs & 1)) return false;                       // every element's half2 slots aligned
   return ((((uintptr_t)out) | ((uintptr_t)out_lo)) & 3) == 0;
 }
 
 template <typename R>
 cudaError_t launch_fiber(const R* in, const R* U, R* out, R* out_lo, const FiberArgs& f, int mode, cudaStream_t st) {
   const int J = f.J1 * f.J2, Rn = f.R1 * f.R2;
+  // blocks per batch element: the whole launch stays near 16 blocks per SM
+  const int64_t cap = std::max<int64_t>(8, 152 * 16 / f.nb);
   int64_t blocks = (f.nfib + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  const unsigned g = (unsigned)blocks;
+  if (blocks > cap) blocks = cap;
+  const dim3 g((unsigned)blocks, f.nb);
   if (J > kShortJ) {               // long form (plain store only)
     if (mode != kTTMStore) return cudaErrorInvalidValue;
     const size_t smem = long_smem(J, Rn, sizeof(R));
     if constexpr (sizeof(R) == 4) {
       if (quadable(f, in, out)) {
         int64_t qblocks = (f.nfib / 4 + 255) / 256;
-        if (qblocks > 152 * 16) qblocks = 152 * 16;
-        if (long_rb(Rn) == 8) ttm_long4_kernel<8><<<(unsigned)qblocks, 256, smem, st>>>(in, U, out, f);
-        else ttm_long4_kernel<kLongRMax><<<(unsigned)qblocks, 256, smem, st>>>(in, U, out, f);
+        if (qblocks > cap) qblocks = cap;
+        const dim3 gq((unsigned)qblocks, f.nb);
+        if (long_rb(Rn) == 8) ttm_long4_kernel<8><<<gq, 256, smem, st>>>(in, U, out, f);
+        else ttm_long4_kernel<kLongRMax><<<gq, 256, smem, st>>>(in, U, out, f);
         return cudaGetLastError();
       }
     }
@@ -524,16 +606,22 @@ cudaError_t launch_fiber(const R* in, const R* U, R* out, R* out_lo, const Fiber
   }
   const size_t smem = short_smem(J, Rn, sizeof(R));
   if constexpr (sizeof(R) == 4) {
-    if (mode == kTTMSplitF16 && f.alpha == 1.0 && pairable(f, out, out_lo)) {
+    // the fp16 split, and its max pass, two fibres per thread (the max pass writes nothing:
+    // the split's output layout decides, so that both passes take the same kernel)
+    if ((mode == kTTMSplitF16 || (mode == kTTMMaxAbs && f.amax)) && f.alpha == 1.0 && pairable(f, out, out_lo)) {
       int64_t pblocks = (f.nfib / 2 + 255) / 256;
-      if (pblocks > 152 * 16) pblocks = 152 * 16;
-      ttm_pair_f16_kernel<R><<<(unsigned)pblocks, 256, smem, st>>>(in, U, out, out_lo, f);
+      if (pblocks > cap) pblocks = cap;
+      const dim3 gp((unsigned)pblocks, f.nb);
+      if (mode == kTTMMaxAbs) ttm_pair_f16_kernel<R, true><<<gp, 256, smem, st>>>(in, U, out, out_lo, f);
+      else ttm_pair_f16_kernel<R, false><<<gp, 256, smem, st>>>(in, U, out, out_lo, f);
       return cudaGetLastError();
     }
   }
   if (mode == kTTMSplitTF32) ttm_short_kernel<R, kTTMSplitTF32><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
   else if (mode == kTTMSplitF16) ttm_short_kernel<R, kTTMSplitF16><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
   else if (mode == kTTMSplitOz) ttm_short_kernel<R, kTTMSplitOz><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
+  else if (mode == kTTMMaxAbs) ttm_short_kernel<R, kTTMMaxAbs><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
+  else if (mode == kTTMStoreMax) ttm_short_kernel<R, kTTMStoreMax><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
   else ttm_short_kernel<R, kTTMStore><<<g, 256, smem, st>>>(in, U, out, out_lo, f);
   return cudaGetLastError();
 }
@@ -549,23 +637,31 @@ cudaError_t launch_ttm(const TI* in, const TU* U, TO* out, TO* out_lo, const TTM
         (f.J1 * f.J2 <= kShortJ || mode == kTTMStore))
       return launch_fiber<TI>(in, U, out, out_lo, f, mode, st);
   }
-  const int64_t blocks = a.outer < 152 * 64 ? a.outer : 152 * 64;
+  if (a.nb < 1) return cudaErrorInvalidValue;
+  const int64_t bcap = std::max<int64_t>(8, 152 * 64 / a.nb);
+  const dim3 blocks((unsigned)(a.outer < bcap ? a.outer : bcap), a.nb);
   const int threads = a.inner >= 256 ? 256 : (int)((a.inner + 31) / 32 * 32);
   switch (mode) {
     case kTTMStore:
-      ttm_kernel<TI, TU, TO, kTTMStore><<<(unsigned)blocks, threads, 0, st>>>(in, U, out, out_lo, a);
+      ttm_kernel<TI, TU, TO, kTTMStore><<<blocks, threads, 0, st>>>(in, U, out, out_lo, a);
       break;
     case kTTMSplitTF32:
-      ttm_kernel<TI, TU, TO, kTTMSplitTF32><<<(unsigned)blocks, threads, 0, st>>>(in, U, out, out_lo, a);
+      ttm_kernel<TI, TU, TO, kTTMSplitTF32><<<blocks, threads, 0, st>>>(in, U, out, out_lo, a);
       break;
     case kTTMSplitF16:
-      ttm_kernel<TI, TU, TO, kTTMSplitF16><<<(unsigned)blocks, threads, 0, st>>>(in, U, out, out_lo, a);
+      ttm_kernel<TI, TU, TO, kTTMSplitF16><<<blocks, threads, 0, st>>>(in, U, out, out_lo, a);
       break;
     case kTTMSplitOz:
-      ttm_kernel<TI, TU, TO, kTTMSplitOz><<<(unsigned)blocks, threads, 0, st>>>(in, U, out, out_lo, a);
+      ttm_kernel<TI, TU, TO, kTTMSplitOz><<<blocks, threads, 0, st>>>(in, U, out, out_lo, a);
+      break;
+    case kTTMMaxAbs:
+      ttm_kernel<TI, TU, TO, kTTMMaxAbs><<<blocks, threads, 0, st>>>(in, U, out, out_lo, a);
+      break;
+    case kTTMStoreMax:
+      ttm_kernel<TI, TU, TO, kTTMStoreMax><<<blocks, threads, 0, st>>>(in, U, out, out_lo, a);
       break;
     default:
-      ttm_kernel<TI, TU, TO, kTTMAccumulate><<<(unsigned)blocks, threads, 0, st>>>(in, U, out, out_lo, a);
+      ttm_kernel<TI, TU, TO, kTTMAccumulate><<<blocks, threads, 0, st>>>(in, U, out, out_lo, a);
   }
   return cudaGetLastError();
 }
@@ -632,7 +728,10 @@ template cudaError_t launch_init<float>(const double*, const double*, float*, fl
 constexpr int kNormBlocks = kNormPartials;
 
 template <typename R>
-__global__ void __launch_bounds__(256) sumsq_kernel(const R* __restrict__ x, int64_t n, double* partial) {
+__global__ void __launch_bounds__(256) sumsq_kernel(const R* __restrict__ x, int64_t n, int64_t xstride,
+                                                    double* partial) {
+  x += blockIdx.y * xstride;                   // batch element blockIdx.y
+  partial += blockIdx.y * gridDim.x;
   double acc = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double v = (double)x[i];
@@ -654,6 +753,11 @@ __global__ void __launch_bounds__(256) sumsq_kernel(const R* __restrict__ x, int
 // device, so a captured step replays correctly at any k).
 __global__ void norm_finish_kernel(const double* __restrict__ partial, int np, const int* __restrict__ step,
                                    double* c_out, double* lnz_acc, DevRecord* rec_b, int* status) {
+  // batch element blockIdx.x
+  partial += blockIdx.x * np;
+  c_out += blockIdx.x;
+  lnz_acc += blockIdx.x;
+  rec_b += blockIdx.x * kMaxSteps;
   __shared__ double red[256];
   double s = 0;
   for (int i = threadIdx.x; i < np; i += blockDim.x) s += partial[i];
@@ -679,6 +783,41 @@ __global__ void norm_finish_kernel(const double* __restrict__ partial, int np, c
   }
 }
 
+// ---------------------------------------------------------------------------- split statistics
+__global__ void __launch_bounds__(256) plane_stats_kernel(const __half* __restrict__ p, int64_t nrows, int64_t Kp,
+                                                          int64_t kps, unsigned long long* out) {
+  unsigned long long nz = 0, ns = 0;
+  unsigned mx = 0;
+  const int64_t n = nrows * Kp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / Kp;
+    const unsigned a = __half_as_ushort(p[r * kps + (i - r * Kp)]) & 0x7fffu;   // magnitude bits
+    nz += a == 0u;
+    ns += (a != 0u && a < 0x0400u);
+    mx = max(mx, a);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    nz += __shfl_down_sync(0xffffffffu, nz, off);
+    ns += __shfl_down_sync(0xffffffffu, ns, off);
+    mx = max(mx, __shfl_down_sync(0xffffffffu, mx, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&out[0], nz);
+    atomicAdd(&out[1], ns);
+    atomicMax(&out[2], (unsigned long long)mx);
+  }
+}
+
+cudaError_t launch_plane_stats(const void* plane, int64_t nrows, int64_t Kp, int64_t kps, unsigned long long* out,
+                               cudaStream_t st) {
+  if (nrows <= 0 || Kp <= 0) return cudaSuccess;
+  if (Kp > kps) return cudaErrorInvalidValue;
+  int64_t blocks = (nrows * Kp + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  plane_stats_kernel<<<(unsigned)blocks, 256, 0, st>>>((const __half*)plane, nrows, Kp, kps, out);
+  return cudaGetLastError();
+}
+
 // Advances the device step counter at the end of a step.
 __global__ void step_end_kernel(int* step) {
   if (threadIdx.x == 0) *step += 1;
@@ -690,33 +829,35 @@ cudaError_t launch_step_end(int* step, cudaStream_t st) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) scale_kernel(R* __restrict__ x, int64_t n, const double* __restrict__ c) {
-  const R inv = (R)(1.0 / *c);
+__global__ void __launch_bounds__(256) scale_kernel(R* __restrict__ x, int64_t n, int64_t xstride,
+                                                    const double* __restrict__ c) {
+  x += blockIdx.y * xstride;                   // batch element blockIdx.y
+  const R inv = (R)(1.0 / c[blockIdx.y]);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] *= inv;
 }
 
 template <typename R>
-cudaError_t launch_norm(const R* x, int64_t n, double* partial, const int* step, double* c_out, double* lnz_acc,
-                        DevRecord* rec_b, int* status, cudaStream_t st) {
-  sumsq_kernel<R><<<kNormBlocks, 256, 0, st>>>(x, n, partial);
-  norm_finish_kernel<<<1, 256, 0, st>>>(partial, kNormBlocks, step, c_out, lnz_acc, rec_b, status);
+cudaError_t launch_norm(const R* x, int64_t n, int nb, int64_t xstride, double* partial, const int* step,
+                        double* c_out, double* lnz_acc, DevRecord* rec_b, int* status, cudaStream_t st) {
+  sumsq_kernel<R><<<dim3(kNormBlocks, nb), 256, 0, st>>>(x, n, xstride, partial);
+  norm_finish_kernel<<<nb, 256, 0, st>>>(partial, kNormBlocks, step, c_out, lnz_acc, rec_b, status);
   return cudaGetLastError();
 }
 template <typename R>
-cudaError_t launch_scale(R* x, int64_t n, const double* c, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
+cudaError_t launch_scale(R* x, int64_t n, int nb, int64_t xstride, const double* c, cudaStream_t st) {
+  if (n <= 0 || nb <= 0) return cudaSuccess;
   int64_t blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  scale_kernel<R><<<(unsigned)blocks, 256, 0, st>>>(x, n, c);
+  scale_kernel<R><<<dim3((unsigned)blocks, nb), 256, 0, st>>>(x, n, xstride, c);
   return cudaGetLastError();
 }
-template cudaError_t launch_norm<double>(const double*, int64_t, double*, const int*, double*, double*, DevRecord*,
-                                         int*, cudaStream_t);
-template cudaError_t launch_norm<float>(const float*, int64_t, double*, const int*, double*, double*, DevRecord*,
-                                        int*, cudaStream_t);
-template cudaError_t launch_scale<double>(double*, int64_t, const double*, cudaStream_t);
-template cudaError_t launch_scale<float>(float*, int64_t, const double*, cudaStream_t);
+template cudaError_t launch_norm<double>(const double*, int64_t, int, int64_t, double*, const int*, double*, double*,
+                                         DevRecord*, int*, cudaStream_t);
+template cudaError_t launch_norm<float>(const float*, int64_t, int, int64_t, double*, const int*, double*, double*,
+                                        DevRecord*, int*, cudaStream_t);
+template cudaError_t launch_scale<double>(double*, int64_t, int, int64_t, const double*, cudaStream_t);
+template cudaError_t launch_scale<float>(float*, int64_t, int, int64_t, const double*, cudaStream_t);
 
 // ---------------------------------------------------------------------------- trace
 // Tr T = sum_{x,y,z,t} T[x,x,y,y,z,z,t,t] in FP64; one block per batch element.

@@ -18,7 +18,7 @@ from . import build as _build
 FP64, FP32, TF32X3, FP16X3, FP64OZ = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32x3": TF32X3, "fp16x3": FP16X3, "fp64oz": FP64OZ}
 IMPURE_NONE, IMPURE_SIGMA, IMPURE_SIGMASIGMA = 0, 1, 2
-OPT_JACOBI_SWEEPS, OPT_GEMM_VARIANT, OPT_GRAPHS, OPT_AUTOTUNE = 1, 2, 3, 4
+OPT_JACOBI_SWEEPS, OPT_GEMM_VARIANT, OPT_GRAPHS, OPT_AUTOTUNE, OPT_GROUP, OPT_MAXNORM = 1, 2, 3, 4, 5, 6
 
 STATUS = {0: "ok", -1: "EINVAL", -2: "EWORKSPACE", -3: "ECUDA", -4: "ENOCONV", -5: "ENONFINITE",
           -6: "ETIMEOUT", -7: "ESTATE", -8: "EUNSUPPORTED"}
@@ -37,7 +37,7 @@ class StepRecord(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_int), ("dims", ctypes.c_int * 4), ("primed", ctypes.c_int * 4),
                 ("eps", (ctypes.c_double * 2) * 4), ("ln_c", ctypes.c_double),
                 ("degenerate", ctypes.c_int * 4), ("slices", ctypes.c_int * 2), ("closing", ctypes.c_int),
-                ("gemm_option", ctypes.c_int), ("tuned", ctypes.c_int)]
+                ("gemm_option", ctypes.c_int), ("tuned", ctypes.c_int), ("group", ctypes.c_int)]
 
 
 class Profile(ctypes.Structure):
@@ -45,12 +45,17 @@ class Profile(ctypes.Structure):
                 ("gemm_flops", ctypes.c_double)]
 
 
+class SplitStats(ctypes.Structure):
+    _fields_ = [("entries", ctypes.c_uint64), ("hi_zero", ctypes.c_uint64), ("hi_subnormal", ctypes.c_uint64),
+                ("lo_zero", ctypes.c_uint64), ("lo_subnormal", ctypes.c_uint64), ("hi_max", ctypes.c_double * 2)]
+
+
 _LIB = None
 SYMBOLS = ["hotrg_create", "hotrg_destroy", "hotrg_workspace_size", "hotrg_set_workspace", "hotrg_set_stream",
            "hotrg_init_tensor", "hotrg_set_tensor", "hotrg_step", "hotrg_lnZ", "hotrg_impure_magnetization",
            "hotrg_impure_energy", "hotrg_x_indicator", "hotrg_step_info", "hotrg_state", "hotrg_copy_tensor",
            "hotrg_copy_isometry", "hotrg_step_flops", "hotrg_set_option", "hotrg_selftest_wait", "hotrg_profile_enable",
-           "hotrg_profile_read", "hotrg_isometry_noalloc", "hotrg_autotune", "hotrg_tune_stats",
+           "hotrg_profile_read", "hotrg_isometry_noalloc", "hotrg_autotune", "hotrg_tune_stats", "hotrg_split_stats",
            "hotrg_status_string", "hotrg_last_error"]
 
 
@@ -93,6 +98,7 @@ def _lib():
                                            c_void_p]),
         "hotrg_autotune": (c_int, [c_void_p, c_int, c_int]),
         "hotrg_tune_stats": (c_int, [c_void_p, P(ctypes.c_uint64), P(ctypes.c_uint64)]),
+        "hotrg_split_stats": (c_int, [c_void_p, P(SplitStats)]),
         "hotrg_status_string": (ctypes.c_char_p, [c_int]),
         "hotrg_last_error": (ctypes.c_char_p, []),
     }
@@ -133,10 +139,15 @@ class HOTRG:
     graphs : capture each distinct step into a CUDA graph and replay it (own stream).
     autotune : take each step's closing direction and GEMM pipeline from the autotuner
         (timing new step shapes first; see autotune()).
+    group : most temperatures contracted together (0: the planner's choice; 1: one at a time).
+    maxnorm : FP16X3 operand scaling: 1 (or True, the default) max-norm scaling from the bound
+        the first pass records, 2 from the exact largest magnitude (a max pass), 0 (False) the
+        fixed 2^14.
     """
 
     def __init__(self, batch=1, dcut_max=4, precision="fp64", impure=0, schedule=None, dims0=None,
-                 workspace_bytes=None, device=None, stream=None, graphs=False, autotune=False):
+                 workspace_bytes=None, device=None, stream=None, graphs=False, autotune=False, group=0,
+                 maxnorm=True):
         import torch
 
         if not torch.cuda.is_available():
@@ -150,6 +161,10 @@ class HOTRG:
         ctx = ctypes.c_void_p()
         _check(self.lib.hotrg_create(ctypes.byref(ctx), batch, dcut_max, self.precision, impure), "create")
         self.ctx = ctx
+        if group:
+            _check(self.lib.hotrg_set_option(self.ctx, OPT_GROUP, int(group)), "set_option(group)")
+        if int(maxnorm) != 1:
+            _check(self.lib.hotrg_set_option(self.ctx, OPT_MAXNORM, int(maxnorm)), "set_option(maxnorm)")
         nbytes = self.workspace_size(schedule, dims0)
         if workspace_bytes is not None:
             nbytes = int(workspace_bytes)
@@ -238,7 +253,7 @@ class HOTRG:
         return dict(mu=r.mu, dims=tuple(r.dims), primed=tuple(r.primed),
                     eps=tuple(tuple(r.eps[n]) for n in range(4)), ln_c=r.ln_c,
                     degenerate=tuple(r.degenerate), slices=tuple(r.slices), closing=r.closing,
-                    gemm_option=r.gemm_option, tuned=bool(r.tuned))
+                    gemm_option=r.gemm_option, tuned=bool(r.tuned), group=r.group)
 
     def tensor(self, which: int = 0, b: int = 0) -> np.ndarray:
         _, dims = self.state()
@@ -261,6 +276,14 @@ class HOTRG:
         t, h = ctypes.c_uint64(), ctypes.c_uint64()
         _check(self.lib.hotrg_tune_stats(self.ctx, ctypes.byref(t), ctypes.byref(h)), "tune_stats")
         return dict(timed=t.value, hits=h.value)
+
+    def split_stats(self) -> dict:
+        """FP16X3 split of the last step's operands: entries, zero and subnormal hi / lo counts,
+        largest |hi| of A and B (hotrg_split_stats)."""
+        st = SplitStats()
+        _check(self.lib.hotrg_split_stats(self.ctx, ctypes.byref(st)), "split_stats")
+        return dict(entries=st.entries, hi_zero=st.hi_zero, hi_subnormal=st.hi_subnormal, lo_zero=st.lo_zero,
+                    lo_subnormal=st.lo_subnormal, hi_max=(st.hi_max[0], st.hi_max[1]))
 
     def set_option(self, option: int, value: int):
         _check(self.lib.hotrg_set_option(self.ctx, option, value), "set_option")

@@ -52,8 +52,8 @@ def test_host_argument_checks(lib):
     assert lib.hotrg_create(ctypes.byref(ctx), 1, 17, 0, 0) == -1         # dcut_max too big
     assert lib.hotrg_create(ctypes.byref(ctx), 1, 4, 7, 0) == -1          # bad precision
     assert lib.hotrg_create(ctypes.byref(ctx), 1, 4, 0, 2) == -1          # sigma-sigma needs sigma
-    assert lib.hotrg_create(ctypes.byref(ctx), 1, 4, 4, 1) == -1          # FP64OZ: pure tensor only
-    assert b"pure tensor only" in lib.hotrg_last_error()
+    assert lib.hotrg_create(ctypes.byref(ctx), 1, 4, 4, 3) == 0           # FP64OZ with impure tensors
+    assert lib.hotrg_destroy(ctx) == 0
     assert lib.hotrg_create(ctypes.byref(ctx), 2, 8, 2, 3) == 0
     size = ctypes.c_size_t()
     assert lib.hotrg_workspace_size(ctx, 0, None, None, None, ctypes.byref(size)) == 0
