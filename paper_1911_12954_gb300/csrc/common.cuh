@@ -41,9 +41,10 @@ struct TTMArgs {
   // split modes: an upper bound of the operand's magnitudes (bits of a non-negative float)
   // that sets its power-of-two scale (nullptr: the fixed scale); kTTMMaxAbs and kTTMStoreMax:
   // where the pass accumulates amax_mul times its largest |output| (atomicMax, rounded up).
-  // One word per batch element: element e uses amax[e].
+  // One word per batch element: element e uses amax[e amax_bs].
   unsigned* amax;
   float amax_mul;
+  int amax_bs;
 };
 
 enum TTMMode {
@@ -68,10 +69,11 @@ __host__ __device__ inline int split_exponent(unsigned mbits, int top) {
 }
 constexpr int kF16Top = 15;
 constexpr int kOzTop = 0;
-// FP64-grade tensor-core mode (Ozaki-type splitting): an FP64 operand x with |x| <= 1 is
-// stored as kOzSlices fp16 planes of integers v_i, x = sum_i v_i 2^(-8 (i + 1)) up to
-// 2^-41; |v_0| <= 256, |v_i| <= 128 for i >= 1. Plane p of an operand starts p times the
-// plane size after plane 0 (the split pass takes the plane size as out_lo - out).
+// FP64-grade tensor-core mode (Ozaki-type splitting): an FP64 operand x with |x| < 1 (after
+// its max-norm scale) is stored as kOzSlices fp16 planes of integers v_i, x = sum_i v_i
+// 2^(-8 (i + 1)) up to 2^-41; |v_0| <= 256, |v_i| <= 128 for i >= 1. Plane p of an operand
+// starts p times the plane size after plane 0 (the split pass takes the plane size as
+// out_lo - out).
 constexpr int kOzSlices = 5;
 // Scale applied to operands stored as fp16 hi/lo pairs: |x| <= 1 (normalised tensors
 // contracted with isometries) becomes <= 2^14, inside fp16's normal range with room for

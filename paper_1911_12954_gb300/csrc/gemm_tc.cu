@@ -706,16 +706,17 @@ __global__ void __launch_bounds__(THREADS, 1)
 // gemm_oz_kernel: C = alpha A B^T in FP64 accuracy on the fp16 tensor cores (an Ozaki-type
 // splitting; Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59 (2012), here with fixed-point
 // slices). Each operand is given as kOzSlices = 5 planes of integers, x = sum_i v_i 2^-8(i+1)
-// (|v_0| <= 256, |v_i| <= 128), so x_A x_B = sum_{i,j} v_i w_j 2^-8(i+j+2). The products with
-// i + j <= 4 (15 of the 25; the rest lie below 2^-40 of the leading one) are formed, one TMEM
-// accumulator per group g = i + j (5 x 96 columns). Within a chunk of 256 k the sums of groups
-// 0 and 1 are integers below 2^24, exact in FP32 whatever order and truncation the tensor
-// cores use; groups 2..4 lie below 2^-16 of the leading group, where one FP32 rounding per
-// chunk is below 2^-40 of the result. After each chunk the epilogue adds group 0 and 2^-8
-// group 1 into a float pair hi + lo (TwoSum) and 2^-16, 2^-24, 2^-32 times groups 2, 3, 4 into
-// lo alone (lo stays below 2^-15 of hi, so its FP32 rounding is below 2^-39 of the result),
-// and writes alpha 2^-16 (hi + lo) in FP64 at the end (added to C when accumulating): no FP64
-// arithmetic in the k loop (a few FP64 operations per clock per SM on this chip).
+// (|v_0| <= 256, |v_i| <= 128: |x| < 1 after the max-norm scale), so x_A x_B = sum_{i,j}
+// v_i w_j 2^-8(i+j+2). The products with i + j <= 4 (15 of the 25; the rest lie below 2^-40 of
+// the leading one) are formed, one TMEM accumulator per group g = i + j (5 x 96 columns).
+// Within a chunk of 256 k the sums of groups 0 and 1 are integers below 2^24, exact in FP32
+// whatever order and truncation the tensor cores use; group 2 lies below 2^-16 of the leading
+// group (one FP32 rounding per chunk below 2^-40 of it, and only when its sum passes 2^24),
+// groups 3 and 4 below 2^-24. After each chunk the epilogue adds groups 0..2 (times 1, 2^-8,
+// 2^-16) into a float pair hi + lo (TwoSum), 2^-24 and 2^-32 times groups 3 and 4 into lo, and
+// renormalises the pair; at the end it writes alpha 2^-(16 + eA + eB) (hi + lo) in FP64 (added
+// to C when accumulating): no FP64 arithmetic in the k loop (a few FP64 operations per clock
+// per SM on this chip).
 //   Tile 128 x 96 per CTA, one CTA per SM; k-blocks of 32 fp16 (64-byte swizzle), 3 stages
 //   of 10 planes (70 KB); warp 0 TMA, warp 1 MMA (15 products x 2 k-steps per k-block),
 //   warps 2..13 promotion (warp w: TMEM lane quarter w % 4, 32 of the 96 columns).
@@ -743,14 +744,17 @@ struct CfgOz {
   static constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(OZ_BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 };
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // hi + lo += x (Knuth's TwoSum; the error of the sum goes into lo)
@@ -904,15 +908,23 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           // 2^-8g: exact scalings of exact (groups 0, 1) or nearly exact (2..4) chunk sums
           const float sc = g == 0 ? 1.f : (g == 1 ? 0x1p-8f : (g == 2 ? 0x1p-16f : (g == 3 ? 0x1p-24f : 0x1p-32f)));
 #pragma unroll
-          for (int c8 = 0; c8 < OZ_COLS; c8 += 8) {
-            float v[8];
-            tmem_ld8(tmem + lane_base + (uint32_t)(g * OZ_BN + cpart * OZ_COLS + c8), v);
+          for (int c16 = 0; c16 < OZ_COLS; c16 += 16) {
+            float v[16];
+            tmem_ld16(tmem + lane_base + (uint32_t)(g * OZ_BN + cpart * OZ_COLS + c16), v);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              if (g < 2) two_sum_into(hi[c8 + j], lo[c8 + j], v[j] * sc);
-              else lo[c8 + j] = fmaf(v[j], sc, lo[c8 + j]);
+            for (int j = 0; j < 16; ++j) {
+              if (g < 3) two_sum_into(hi[c16 + j], lo[c16 + j], v[j] * sc);
+              else lo[c16 + j] = fmaf(v[j], sc, lo[c16 + j]);
             }
           }
+        }
+        // renormalise each pair (FastTwoSum: |lo| back to half an ulp of hi), so that lo's own
+        // roundings stay near 2^-48 of the sum over the whole k loop
+#pragma unroll
+        for (int j = 0; j < OZ_COLS; ++j) {
+          const float s = hi[j] + lo[j];
+          lo[j] = lo[j] - (s - hi[j]);
+          hi[j] = s;
         }
         fence_before();
         mbar_arrive(cempty);

@@ -401,7 +401,7 @@ Scratch scratch_layout(const StepPlan& p, int xs, int xs2, int prec, int impure,
   s.Blo = split ? take(ne * nt * p.P * rowsB * p.kps * os) : 0;
   s.C = take(ne * nt * rowsA * rowsB * rs);
   s.O3 = take(ne * (size_t)(rowsA * rowsB / (p.D[p.c] * p.D[p.c]) * p.chi[p.c]) * rs);
-  s.amax = take(2 * ne * sizeof(unsigned));     // A side, then B side: one word per element
+  s.amax = take(2 * ne * nt * sizeof(unsigned));   // A side, then B side: per element (and tensor)
   s.stats = take(4 * 3 * sizeof(unsigned long long));   // hotrg_split_stats counters
   s.total = off;
   return s;
@@ -464,6 +464,7 @@ TTMArgs make_ttm(const std::vector<Dim>& d, int J1, int64_t in_sj1, int64_t u_sj
   a.beta = beta;
   a.nb = 1;
   a.amax_mul = 1.0f;
+  a.amax_bs = 1;
   for (int i = 0; i < a.rank; ++i) {
     a.dims[i] = d[i].n;
     a.in_st[i] = d[i].in;
@@ -521,8 +522,8 @@ void operand_strides(const StepPlan& p, const std::vector<int64_t>& rn, int64_t 
 
 template <typename R>
 hotrg_status build_A(hotrg_ctx* ctx, const StepPlan& p, const R* P, const R* Ua, const R* Ub, int x0, int xs,
-                     R* O1, R* A, R* Alo, cudaStream_t st, const ElemStrides& es, unsigned* amax, int scale,
-                     int phases) {
+                     R* O1, R* A, R* Alo, cudaStream_t st, const ElemStrides& es, unsigned* amax, int amax_bs,
+                     int scale, int phases) {
   const int mu = p.mu, a = p.a, b = p.b, c = p.c;
   const int Da = p.D[a], Db = p.D[b], Dc = p.D[c], Dm = p.D[mu];
   const int ca = p.chi[a], cb = p.chi[b];
@@ -549,6 +550,7 @@ hotrg_status build_A(hotrg_ctx* ctx, const StepPlan& p, const R* P, const R* Ua,
     if (bound) {
       t.amax = amax;
       t.amax_mul = sqrtf((float)Db);
+      t.amax_bs = amax_bs;
     }
     if (phases & kPass1) LK(1, launch_ttm_r<R>(P, Ua + x0, O1, nullptr, t, bound ? kTTMStoreMax : kTTMStore, st), "ttm A1");
   }
@@ -573,6 +575,7 @@ hotrg_status build_A(hotrg_ctx* ctx, const StepPlan& p, const R* P, const R* Ua,
     ttm_limits((int64_t)xs * p.E, (int64_t)Db * Db * cb, p.P * ((int64_t)xs * cb * Dc * Dc * Dm) * p.kps);
     t = batched(t, es.ne, es.O1, es.U, es.op);
     t.amax = amax;   // max-norm scaling (nullptr: none): the max pass writes it, the split reads it
+    t.amax_bs = amax_bs;
     if ((phases & kPassMax) && amax && scale == kScaleExact)
       LK(1, launch_ttm_r<R>(O1, Ub, A, Alo, t, kTTMMaxAbs, st), "ttm A max");
     if (phases & kPass2) LK(1, launch_ttm_r<R>(O1, Ub, A, Alo, t, mode, st), "ttm A2");
@@ -582,8 +585,8 @@ hotrg_status build_A(hotrg_ctx* ctx, const StepPlan& p, const R* P, const R* Ua,
 
 template <typename R>
 hotrg_status build_B(hotrg_ctx* ctx, const StepPlan& p, const R* Q, const R* Ua, const R* Ub, int x0, int xs,
-                     R* O1, R* B, R* Blo, cudaStream_t st, const ElemStrides& es, unsigned* amax, int scale,
-                     int phases) {
+                     R* O1, R* B, R* Blo, cudaStream_t st, const ElemStrides& es, unsigned* amax, int amax_bs,
+                     int scale, int phases) {
   const int mu = p.mu, a = p.a, b = p.b, c = p.c;
   const int Da = p.D[a], Db = p.D[b], Dc = p.D[c], Dm = p.D[mu];
   const int ca = p.chi[a], cb = p.chi[b];
@@ -610,6 +613,7 @@ hotrg_status build_B(hotrg_ctx* ctx, const StepPlan& p, const R* Q, const R* Ua,
     if (bound) {
       t.amax = amax;
       t.amax_mul = sqrtf((float)Db);
+      t.amax_bs = amax_bs;
     }
     if (phases & kPass1) LK(1, launch_ttm_r<R>(Q, Ua + x0, O1, nullptr, t, bound ? kTTMStoreMax : kTTMStore, st), "ttm B1");
   }
@@ -633,6 +637,7 @@ hotrg_status build_B(hotrg_ctx* ctx, const StepPlan& p, const R* Q, const R* Ua,
     ttm_limits((int64_t)xs * p.E, (int64_t)Db * Db * cb, p.P * ((int64_t)xs * cb * Dc * Dc * Dm) * p.kps);
     t = batched(t, es.ne, es.O1, es.U, es.op);
     t.amax = amax;   // max-norm scaling (nullptr: none): the max pass writes it, the split reads it
+    t.amax_bs = amax_bs;
     if ((phases & kPassMax) && amax && scale == kScaleExact)
       LK(1, launch_ttm_r<R>(O1, Ub, B, Blo, t, kTTMMaxAbs, st), "ttm B max");
     if (phases & kPass2) LK(1, launch_ttm_r<R>(O1, Ub, B, Blo, t, mode, st), "ttm B2");
@@ -970,9 +975,12 @@ hotrg_status contract_group(hotrg_ctx* ctx, const StepPlan& p, int e0, int ne, c
     // max-norm scaling of the fp16 planes and of the integer slices: one magnitude bound per
     // operand side over every tensor of the group (the segments of an output share 2^(eA+eB))
     const int scale = ctx->prec == HOTRG_FP16X3 ? ctx->maxnorm : (oz ? kScaleExact : kScaleNone);
-    // (one word per element: an element's scales do not depend on the group it runs in)
+    // (one word per element, so an element's scales do not depend on the group it runs in;
+    // FP64OZ: one per element and tensor, each product being its own launch, so that the
+    // impure tensors' slices keep their own precision)
+    const int tw = oz ? nt : 1;               // words per element and side
     unsigned* amaxA = scale != kScaleNone ? (unsigned*)(sb + sc.amax) : nullptr;
-    unsigned* amaxB = scale != kScaleNone ? amaxA + p.ne : nullptr;
+    unsigned* amaxB = scale != kScaleNone ? amaxA + p.ne * tw : nullptr;
     // the first step's M operands are never read (M_1 = A(S) B(S)^T): not built
     const int nbuild = (kstep == 0 && nt >= 3) ? 2 : nt;
     esA.op = nt * Asz * planes;
@@ -988,10 +996,11 @@ hotrg_status contract_group(hotrg_ctx* ctx, const StepPlan& p, int e0, int ne, c
     auto buildB = [&](int x20, int xs2) -> hotrg_status {
       for (int ph : {kPass1, kPassMax, kPass2}) {
         if (ph == kPassMax && scale != kScaleExact) continue;
-        if (amaxB && clear_phase(ph)) CK(cudaMemsetAsync(amaxB, 0, ne * sizeof(unsigned), st), "amax clear");
+        if (amaxB && clear_phase(ph)) CK(cudaMemsetAsync(amaxB, 0, ne * tw * sizeof(unsigned), st), "amax clear");
         for (int w = 0; w < nbuild; ++w) {
           hotrg_status s = build_B<R>(ctx, p, src[w], Ua, Ub, x20, xs2, O1B + w * O1Bsz, opnd(Bbuf, w * Bsz * planes),
-                                      opnd(Blob, w * Bsz * planes), st, esB, amaxB, scale, ph);
+                                      opnd(Blob, w * Bsz * planes), st, esB, amaxB ? amaxB + (tw > 1 ? w : 0) : nullptr,
+                                      tw, scale, ph);
           if (s != HOTRG_OK) return s;
         }
       }
@@ -1010,10 +1019,11 @@ hotrg_status contract_group(hotrg_ctx* ctx, const StepPlan& p, int e0, int ne, c
       for (int ph : {kPass1, kPassMax, kPass2}) {
         if (!pr.ttm) break;
         if (ph == kPassMax && scale != kScaleExact) continue;
-        if (amaxA && clear_phase(ph)) CK(cudaMemsetAsync(amaxA, 0, ne * sizeof(unsigned), st), "amax clear");
+        if (amaxA && clear_phase(ph)) CK(cudaMemsetAsync(amaxA, 0, ne * tw * sizeof(unsigned), st), "amax clear");
         for (int w = 0; w < nbuild; ++w) {
           hotrg_status s = build_A<R>(ctx, p, src[w], Ua, Ub, x0, xs, O1A + w * O1Asz, opnd(Abuf, w * Asz * planes),
-                                      opnd(Alob, w * Asz * planes), st, esA, amaxA, scale, ph);
+                                      opnd(Alob, w * Asz * planes), st, esA, amaxA ? amaxA + (tw > 1 ? w : 0) : nullptr,
+                                      tw, scale, ph);
           if (s != HOTRG_OK) return s;
         }
       }
@@ -1061,7 +1071,8 @@ hotrg_status contract_group(hotrg_ctx* ctx, const StepPlan& p, int e0, int ne, c
               if (r != HOTRG_OK) return r;
               CK(launch_gemm_oz(Abuf + (e * esA.op + wa * Asz * planes) * (int64_t)osz,
                                 Bbuf + (e * esB.op + wb * Bsz * planes) * (int64_t)osz, Asz, Bsz, p.Kp, p.kps, p.P,
-                                rA, rB, (double*)(Cbuf + e * esC.C + out * Csz), rB, alpha, amaxA + e, amaxB + e,
+                                rA, rB, (double*)(Cbuf + e * esC.C + out * Csz), rB, alpha, amaxA + e * tw + wa,
+                                amaxB + e * tw + wb,
                                 acc, (int*)(ctx->ws + ctx->L.status), st),
                  "gemm oz");
               return tm.stop(2.0 * (double)rA * (double)rB * (double)p.K);

@@ -27,7 +27,7 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
-// Exact 8-bit slices of x (|x| <= 1, FP64): r <- 256 r, v = rint(r), r <- r - v, five times;
+// Exact 8-bit slices of x (|x| < 1, FP64): r <- 256 r, v = rint(r), r <- r - v, five times;
 // every step is exact in FP64 and every v an integer fp16 holds exactly (|v| <= 256).
 __device__ __forceinline__ void oz_store(__half* out, int64_t plane, int64_t o, double x) {
   double r = x;
@@ -45,7 +45,7 @@ __device__ __forceinline__ void oz_store(__half* out, int64_t plane, int64_t o, 
 template <int MODE>
 __device__ __forceinline__ double split_scale(const unsigned* amax) {
   if (MODE == kTTMSplitF16) return amax ? ldexp(1.0, split_exponent(*amax, kF16Top)) : (double)kF16Scale;
-  if (MODE == kTTMSplitOz) return amax ? ldexp(1.0, split_exponent(*amax, kOzTop)) : 1.0;
+  if (MODE == kTTMSplitOz) return ldexp(1.0, amax ? split_exponent(*amax, kOzTop) : kOzTop);
   return 1.0;
 }
 
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256) ttm_kernel(const TI* __restrict__ in, con
                                                   TTMArgs a) {
   using Acc = typename std::conditional<sizeof(TI) == 8, double, float>::type;
   const int64_t eb = blockIdx.y;               // batch element
-  unsigned* amax = a.amax ? a.amax + eb : nullptr;
+  unsigned* amax = a.amax ? a.amax + eb * a.amax_bs : nullptr;
   const Acc sscale = (Acc)split_scale<MODE>(amax);
   Acc tmax = 0;                                // largest |output| of this thread (max modes), in the
                                                // accumulator type: no FP64 work for FP32 data
@@ -159,6 +159,7 @@ struct FiberArgs {
   int64_t in_bs, u_bs, out_bs;
   unsigned* amax;               // as in TTMArgs
   float amax_mul;
+  int amax_bs;
 };
 
 constexpr int kShortJ = 16;     // longest contraction of the short form
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(256) ttm_short_kernel(const R* __restrict__ in
   int64_t* roff = (int64_t*)(fsm + (size_t)J * Rp * sizeof(R));   // [Rp] output offset of r
   int64_t* joff = roff + Rp;                             // [J] input offset of j
   // the split's power-of-two scale (exact) is folded into U
-  unsigned* amax = a.amax ? a.amax + blockIdx.y : nullptr;
+  unsigned* amax = a.amax ? a.amax + blockIdx.y * a.amax_bs : nullptr;
   const R uscale = (R)split_scale<MODE>(amax);
   R tmax = 0;                                            // max modes: largest |output| (type R)
   for (int e = threadIdx.x; e < J * Rp; e += blockDim.x) {
@@ -290,7 +291,7 @@ template <typename R, bool MAXONLY>
 __global__ void __launch_bounds__(256) ttm_pair_f16_kernel(const R* __restrict__ in, const R* __restrict__ U,
                                                            R* __restrict__ out, R* __restrict__ out_lo, FiberArgs a) {
   constexpr int RB = 16;
-  unsigned* amax = a.amax ? a.amax + blockIdx.y : nullptr;
+  unsigned* amax = a.amax ? a.amax + blockIdx.y * a.amax_bs : nullptr;
   float tmax = 0.f;                            // MAXONLY: largest |output| of this thread
   in += blockIdx.y * a.in_bs;                  // batch element blockIdx.y
   U += blockIdx.y * a.u_bs;
@@ -562,6 +563,7 @@ bool to_fiber(const TTMArgs& a, size_t rsize, FiberArgs& f) {
   f.out_bs = a.out_bs;
   f.amax = a.amax;
   f.amax_mul = a.amax_mul;
+  f.amax_bs = a.amax_bs;
   const int J = a.J1 * a.J2, Rn = f.R1 * f.R2;
   if (f.nf == 0 || f.nfib > 0x7fffffffLL) return false;   // fibre index decoded in 32 bits
   if (J <= kShortJ) return Rn <= 256 && short_smem(J, Rn, rsize) <= kFiberSmemMax;
