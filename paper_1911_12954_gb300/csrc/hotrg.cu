@@ -908,7 +908,7 @@ hotrg_status isometry_stage(hotrg_ctx* ctx, const StepPlan& p, const Scratch& sc
   return HOTRG_OK;
 }
 
-// What one contract_element call runs: the whole contraction (default), or a timing probe of
+// What one contract_group call runs: the whole contraction (default), or a timing probe of
 // the first slice block only: its tensor passes without the GEMM, or its GEMM alone on the
 // first gemm_rows rows (operands left in place by a tensor-pass probe of the same plan).
 struct Probe {

@@ -131,7 +131,7 @@ class HOTRG:
     batch : number of independent runs (temperatures).
     dcut_max : largest bond dimension (2..16).
     precision : "fp64", "fp32", "tf32x3", "fp16x3" (the fastest mixed mode) or "fp64oz" (FP64-grade
-        product on the tensor cores; pure tensor only).
+        product on the tensor cores, from integer slices).
     impure : 0, IMPURE_SIGMA or IMPURE_SIGMA | IMPURE_SIGMASIGMA.
     schedule : list of (dir, dcut) used to size the workspace (None: steady state at
         dcut_max), dims0 : starting bond dimensions for set_tensor runs.
