@@ -31,7 +31,7 @@
 
 namespace hotrg {
 
-constexpr int kJT = 256;            // threads per Jacobi CTA
+constexpr int kJT = 512;            // threads per Jacobi CTA (16 warps: latency, not FP64 throughput, bounds a round)
 constexpr int kSmemJacobiN = kJacobiSmemN;    // A and V in shared memory up to this n
 
 __device__ __forceinline__ void rr_pair(int r, int i, int m, int& p, int& q) {
