@@ -69,6 +69,14 @@ def test_host_argument_checks(lib):
     t, h = ctypes.c_uint64(), ctypes.c_uint64()
     assert lib.hotrg_tune_stats(ctx, ctypes.byref(t), ctypes.byref(h)) == 0 and (t.value, h.value) == (0, 0)
     assert lib.hotrg_tune_stats(None, None, None) == -1
+    # operand scaling: 0 fixed 2^14, 1 first-pass bound, 2 exact max pass; others refused
+    for v, st in ((-1, -1), (3, -1), (0, 0), (2, 0), (1, 0)):
+        assert lib.hotrg_set_option(ctx, HB.OPT_MAXNORM, v) == st, v
+    assert lib.hotrg_set_option(ctx, HB.OPT_GROUP, 97) == -1               # at most 96 outputs per GEMM
+    assert lib.hotrg_set_option(ctx, HB.OPT_GROUP, 3) == 0
+    counts = HB.SplitStats()
+    assert lib.hotrg_split_stats(ctx, ctypes.byref(counts)) == -2          # no workspace yet
+    assert lib.hotrg_split_stats(None, ctypes.byref(counts)) == -1
     assert lib.hotrg_destroy(ctx) == 0
 
 
